@@ -1,0 +1,33 @@
+"""Compile the CPU oracle (test infrastructure) into oracle/_build/libcupso_oracle.so.
+
+Plain gcc, no fast-math, no FP contraction: every float operation in the oracle
+is a single binary32 operation rounded to nearest. Portable C only, so the same
+source gives the same bits on x86-64 and on aarch64.
+"""
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "cupso_oracle.c")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libcupso_oracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+          "-Wall", "-Wextra", "-D_DEFAULT_SOURCE"]
+
+
+def build_oracle(force: bool = False) -> str:
+    os.makedirs(OUT_DIR, exist_ok=True)
+    deps = [SRC, os.path.join(HERE, "cupso_oracle.h"), __file__]
+    if not force and os.path.exists(LIB):
+        if os.path.getmtime(LIB) >= max(os.path.getmtime(p) for p in deps):
+            return LIB
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", *CFLAGS, SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build_oracle(force=True))

@@ -1,0 +1,381 @@
+/*
+ * cupso_oracle.c -- CPU oracle for the PSO iteration (TEST INFRASTRUCTURE ONLY).
+ *
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg use this
+ * file. It follows the paper step by step:
+ *   Step 1 (init)          Alg. 1, Sec. 2.1, "initialize ... uniformly distributed"
+ *   Step 2 (v and pos)     Eq. 1 and Eq. 2, clamps of Alg. 1 ("keep in range")
+ *   Step 3 (fitness)       Sec. 2.1 step (3); Eq. 3 for the paper's cubic
+ *   Step 4 (pbest)         Alg. 1, "if fit_i better than pbest_fit_i"
+ *   Step 5 (gbest)         Alg. 1, "if pbest_fit_i better than gbest_fit"
+ * Random numbers (Sec. 4.4: r1, r2 uniform, cuRAND's (0,1] range) come from a
+ * counter-based Philox4x32-10 written from its published definition.
+ *
+ * Readings where the paper is silent (each also recorded in the design notes):
+ *  - minimisation (the paper maximises its cubic; we minimise -f);
+ *  - r1, r2 drawn fresh per (iteration, particle, dimension);
+ *  - v0 ~ U(-max_v, max_v], pos0 ~ U(min_pos, max_pos];
+ *  - closed clamps written as comparisons (NaN passes through unchanged);
+ *  - synchronous gbest: iteration t uses the gbest at the end of t-1;
+ *  - ties: strict "<" for pbest, lowest index among equal pbest_fit for gbest.
+ *
+ * Compile with -O2 -ffp-contract=off and no fast-math: every float operation
+ * below is one IEEE-754 binary32 operation rounded to nearest.
+ */
+#include "cupso_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon et al., SC'11)                                      */
+/* ------------------------------------------------------------------------- */
+
+/* Multipliers and Weyl key increments as published with the generator. */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+float ora_u01(uint32_t w)
+{
+    /* (w >> 8) + 1 is an integer in [1, 2^24]: exact in binary32, and so is
+     * its product with 2^-24. */
+    return (float)((w >> 8) + 1u) * 0x1p-24f;
+}
+
+/* Counter of one draw: (dimension pair, particle, iteration, swarm). One
+ * Philox call serves dimensions 2g and 2g+1 of one particle: words 0,1 are
+ * (r1, r2) of dimension 2g, words 2,3 those of dimension 2g+1. At t = 0 the
+ * same words give the initial (pos, v). */
+static void draw_words(const ora_params* p, uint32_t t, int i, int d, uint32_t* wa, uint32_t* wb)
+{
+    uint32_t ctr[4] = {(uint32_t)(d >> 1), (uint32_t)i, t, p->swarm};
+    uint32_t key[2] = {(uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32)};
+    uint32_t out[4];
+    ora_philox4x32_10(ctr, key, out);
+    if ((d & 1) == 0) {
+        *wa = out[0];
+        *wb = out[1];
+    } else {
+        *wa = out[2];
+        *wb = out[3];
+    }
+}
+
+void ora_draw_r(const ora_params* p, uint32_t t, int i, int d, float* r1, float* r2)
+{
+    uint32_t a, b;
+    draw_words(p, t, i, d, &a, &b);
+    *r1 = ora_u01(a);
+    *r2 = ora_u01(b);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Own cos(2*pi*x) and exp(y)                                                */
+/* ------------------------------------------------------------------------- */
+/* cos(2*pi*a) = sum_j (-1)^j (2*pi)^(2j) / (2j)! * a^(2j): Taylor series of
+ * cosine, truncated after j = 7 (the j = 8 term is below 7e-11 for |a| <= 1/4).
+ * exp(r) = sum_k r^k / k!, k <= 8, after Cody-Waite reduction y = n*ln2 + r.
+ * The coefficients are computed here, in double, and rounded once to float. */
+
+static float g_cos_c[8];
+static float g_exp_c[9];
+static float g_log2e, g_ln2_hi, g_ln2_lo;
+static int g_consts_ready = 0;
+
+static void init_consts(void)
+{
+    if (g_consts_ready) return;
+    const double two_pi = 2.0 * M_PI;
+    double term = 1.0; /* (2*pi)^(2j) / (2j)! */
+    for (int j = 0; j < 8; ++j) {
+        if (j > 0) term *= (two_pi * two_pi) / ((double)(2 * j - 1) * (double)(2 * j));
+        g_cos_c[j] = (float)((j & 1) ? -term : term);
+    }
+    double fact = 1.0;
+    for (int k = 0; k < 9; ++k) {
+        if (k > 0) fact *= (double)k;
+        g_exp_c[k] = (float)(1.0 / fact);
+    }
+    g_log2e = (float)(1.0 / M_LN2);
+    /* ln2 cut to 16 significant bits, so n * ln2_hi is exact for |n| < 2^8. */
+    double hi = ldexp(floor(ldexp(M_LN2, 16)), -16);
+    g_ln2_hi = (float)hi;
+    g_ln2_lo = (float)(M_LN2 - hi);
+    g_consts_ready = 1;
+}
+
+void ora_cos2pi_coeffs(float out[8])
+{
+    init_consts();
+    memcpy(out, g_cos_c, sizeof(g_cos_c));
+}
+
+void ora_exp_coeffs(float out[9], float* log2e, float* ln2_hi, float* ln2_lo)
+{
+    init_consts();
+    memcpy(out, g_exp_c, sizeof(g_exp_c));
+    *log2e = g_log2e;
+    *ln2_hi = g_ln2_hi;
+    *ln2_lo = g_ln2_lo;
+}
+
+/* cos(2*pi*a), 0 <= a <= 1/4, as the polynomial in z = a*a (Horner, fmaf). */
+static float cos2pi_poly(float a)
+{
+    float z = a * a;
+    float q = g_cos_c[7];
+    for (int j = 6; j >= 0; --j) q = fmaf(q, z, g_cos_c[j]);
+    return q;
+}
+
+float ora_cos2pi(float x)
+{
+    init_consts();
+    if (isnan(x) || isinf(x)) return NAN;
+    /* x - rint(x) is exact: for |x| >= 2^23 x is an integer (r = 0); below
+     * that, x and rint(x) share the binade bounds and r fits in x's bits. */
+    float r = x - rintf(x);
+    float a = fabsf(r);                 /* cosine is even: 0 <= a <= 1/2 */
+    if (a > 0.25f) {
+        float b = 0.5f - a;             /* exact (Sterbenz): 0 <= b < 1/4 */
+        return -cos2pi_poly(b);         /* cos(pi - t) = -cos(t) */
+    }
+    return cos2pi_poly(a);
+}
+
+float ora_exp(float y)
+{
+    init_consts();
+    if (isnan(y)) return y;
+    if (y > 88.8f) return INFINITY;
+    if (y < -104.0f) return 0.0f;
+    float n = rintf(y * g_log2e);
+    float r = fmaf(-n, g_ln2_hi, y);
+    r = fmaf(-n, g_ln2_lo, r);
+    float q = g_exp_c[8];
+    for (int k = 7; k >= 0; --k) q = fmaf(q, r, g_exp_c[k]);
+    /* q * 2^n, in two factors so that each power of two is a normal float. */
+    int ni = (int)n;
+    int n1 = ni / 2;
+    int n2 = ni - n1;
+    return (q * ldexpf(1.0f, n1)) * ldexpf(1.0f, n2);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Fitness functions (Step 3). Sequential over d, accumulator starts at 0.  */
+/* ------------------------------------------------------------------------- */
+
+float ora_fitness(int fitness, const float* x, int D)
+{
+    init_consts();
+    float acc = 0.0f;
+    switch (fitness) {
+    case ORA_SPHERE: /* sum x_d^2 */
+        for (int d = 0; d < D; ++d) acc = fmaf(x[d], x[d], acc);
+        return acc;
+    case ORA_RASTRIGIN: /* sum (x_d^2 + 10 - 10 cos(2 pi x_d)) = 10 D + sum(...) */
+        for (int d = 0; d < D; ++d) {
+            float ten_minus = fmaf(-10.0f, ora_cos2pi(x[d]), 10.0f);
+            acc = acc + fmaf(x[d], x[d], ten_minus);
+        }
+        return acc;
+    case ORA_ACKLEY: { /* -20 exp(-0.2 sqrt(mean x^2)) - exp(mean cos 2 pi x) + 20 + e */
+        float s1 = 0.0f, s2 = 0.0f;
+        for (int d = 0; d < D; ++d) {
+            s1 = fmaf(x[d], x[d], s1);
+            s2 = s2 + ora_cos2pi(x[d]);
+        }
+        float m1 = s1 / (float)D;
+        float m2 = s2 / (float)D;
+        float e1 = ora_exp(-0.2f * sqrtf(m1));
+        float part1 = 20.0f - 20.0f * e1;
+        float part2 = ora_exp(1.0f) - ora_exp(m2);
+        return part1 + part2;
+    }
+    case ORA_ROSENBROCK: /* sum_{d<D-1} 100 (x_{d+1} - x_d^2)^2 + (1 - x_d)^2 */
+        for (int d = 0; d + 1 < D; ++d) {
+            float p = fmaf(-x[d], x[d], x[d + 1]);
+            float q = 1.0f - x[d];
+            acc = acc + fmaf(100.0f * p, p, q * q);
+        }
+        return acc;
+    case ORA_CUBIC_MAX: /* Eq. 3, maximised: return -sum (x^3 - 0.8 x^2 - 1000 x + 8000) */
+        for (int d = 0; d < D; ++d) {
+            float h = fmaf(fmaf(x[d] - 0.8f, x[d], -1000.0f), x[d], 8000.0f);
+            acc = acc + h;
+        }
+        return -acc;
+    default:
+        return NAN;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Ordering of fitness values                                                */
+/* ------------------------------------------------------------------------- */
+
+uint32_t ora_fit_key(float f)
+{
+    if (isnan(f)) return 0xFFFFFFFFu;
+    if (f == 0.0f) f = 0.0f; /* -0 and +0 are the same fitness */
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+/* a ranks strictly before b: by fitness (NaN last), then by index. */
+static int better(float fa, int64_t ia, float fb, int64_t ib)
+{
+    uint32_t ka = ora_fit_key(fa), kb = ora_fit_key(fb);
+    if (ka != kb) return ka < kb;
+    return ia < ib;
+}
+
+int64_t ora_argmin_pbest(const ora_params* p, const ora_state* s)
+{
+    int64_t g = 0;
+    for (int64_t i = 1; i < p->N; ++i)
+        if (better(s->pbest_fit[i], i, s->pbest_fit[g], g)) g = i;
+    return g;
+}
+
+static void take_gbest(const ora_params* p, ora_state* s, int64_t g)
+{
+    s->gbest_idx = g;
+    s->gbest_fit = s->pbest_fit[g];
+    memcpy(s->gbest_pos, s->pbest_pos + (size_t)g * p->D, sizeof(float) * (size_t)p->D);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Step 1: initialisation                                                    */
+/* ------------------------------------------------------------------------- */
+
+static float clampf(float a, float lo, float hi)
+{
+    return a < lo ? lo : (a > hi ? hi : a);
+}
+
+static int check_params(const ora_params* p)
+{
+    if (p->N <= 0 || p->D <= 0) return -1;
+    if (!(p->min_pos < p->max_pos) || !(p->max_v > 0.0f)) return -1;
+    if (p->fitness < ORA_SPHERE || p->fitness > ORA_CUBIC_MAX) return -1;
+    return 0;
+}
+
+int ora_init(const ora_params* p, ora_state* s)
+{
+    if (check_params(p)) return -1;
+    const int N = p->N, D = p->D;
+    const float span = p->max_pos - p->min_pos;
+    const float vspan = 2.0f * p->max_v;
+    for (int i = 0; i < N; ++i) {
+        float* pos = s->pos + (size_t)i * D;
+        float* v = s->v + (size_t)i * D;
+        for (int d = 0; d < D; ++d) {
+            uint32_t wx, wv;
+            draw_words(p, 0u, i, d, &wx, &wv);
+            pos[d] = clampf(fmaf(ora_u01(wx), span, p->min_pos), p->min_pos, p->max_pos);
+            v[d] = clampf(fmaf(ora_u01(wv), vspan, -p->max_v), -p->max_v, p->max_v);
+        }
+        s->fit[i] = ora_fitness(p->fitness, pos, D);
+        s->pbest_fit[i] = s->fit[i];
+        memcpy(s->pbest_pos + (size_t)i * D, pos, sizeof(float) * (size_t)D);
+    }
+    s->t = 0;
+    take_gbest(p, s, ora_argmin_pbest(p, s));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Steps 2-5                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Steps 2-4 for particle i at iteration t: Eq. 1 with the clamp to
+ * [-max_v, max_v], Eq. 2 with the clamp to [min_pos, max_pos], fitness, and the
+ * personal-best update. gbest_pos is read, never written. */
+static void move_particle(const ora_params* p, ora_state* s, uint32_t t, int i,
+                          const float* r_iter /* null or [N][D][2] */)
+{
+    const int D = p->D;
+    float* pos = s->pos + (size_t)i * D;
+    float* v = s->v + (size_t)i * D;
+    float* pbest = s->pbest_pos + (size_t)i * D;
+    for (int d = 0; d < D; ++d) {
+        float r1, r2;
+        if (r_iter) {
+            r1 = r_iter[((size_t)i * D + d) * 2 + 0];
+            r2 = r_iter[((size_t)i * D + d) * 2 + 1];
+        } else {
+            ora_draw_r(p, t, i, d, &r1, &r2);
+        }
+        /* Eq. 1: v <- w v + c1 r1 (pbest - pos) + c2 r2 (gbest - pos) */
+        float cognitive = pbest[d] - pos[d];
+        float social = s->gbest_pos[d] - pos[d];
+        float vel = p->w * v[d];
+        vel = fmaf(p->c1 * r1, cognitive, vel);
+        vel = fmaf(p->c2 * r2, social, vel);
+        v[d] = clampf(vel, -p->max_v, p->max_v);
+        /* Eq. 2: pos <- pos + v */
+        pos[d] = clampf(pos[d] + v[d], p->min_pos, p->max_pos);
+    }
+    s->fit[i] = ora_fitness(p->fitness, pos, D);          /* Step 3 */
+    if (s->fit[i] < s->pbest_fit[i]) {                      /* Step 4 */
+        s->pbest_fit[i] = s->fit[i];
+        memcpy(pbest, pos, sizeof(float) * (size_t)D);
+    }
+}
+
+int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_override)
+{
+    if (check_params(p) || iters < 0) return -1;
+    for (int k = 0; k < iters; ++k) {
+        uint32_t t = s->t + 1;
+        const float* r_iter = r_override ? r_override + (size_t)k * p->N * p->D * 2 : NULL;
+        for (int i = 0; i < p->N; ++i) move_particle(p, s, t, i, r_iter);
+        take_gbest(p, s, ora_argmin_pbest(p, s));           /* Step 5 */
+        s->t = t;
+    }
+    return 0;
+}
+
+int ora_step_serial(const ora_params* p, ora_state* s, int iters, const float* r_override)
+{
+    if (check_params(p) || iters < 0) return -1;
+    for (int k = 0; k < iters; ++k) {
+        uint32_t t = s->t + 1;
+        const float* r_iter = r_override ? r_override + (size_t)k * p->N * p->D * 2 : NULL;
+        for (int i = 0; i < p->N; ++i) {
+            move_particle(p, s, t, i, r_iter);
+            if (better(s->pbest_fit[i], i, s->gbest_fit, s->gbest_idx)) /* Step 5 in-loop */
+                take_gbest(p, s, i);
+        }
+        s->t = t;
+    }
+    return 0;
+}

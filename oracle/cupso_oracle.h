@@ -1,0 +1,101 @@
+/*
+ * cupso_oracle.h -- plain, slow, single-threaded CPU oracle of one PSO run.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path links, loads or calls
+ * this code: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark do. It shares no source, header, table or constant with the CUDA
+ * library; every constant below is derived at run time from its mathematical
+ * definition.
+ *
+ * What it computes: the Standard PSO of Alg. 1 (Sec. 2.1) with the velocity
+ * update of Eq. 1 and the position update of Eq. 2, parameters as in Table 1,
+ * in FP32 with every operation rounded to nearest and in a fixed order, so that
+ * a GPU implementation of the same reading can match it bit for bit. The
+ * library minimises; the paper's maximised cubic (Eq. 3) is minimised as -f.
+ *
+ * State layout (oracle-private): particle-major, pos[i*D + d].
+ */
+#ifndef CUPSO_ORACLE_H
+#define CUPSO_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    ORA_SPHERE = 0,
+    ORA_RASTRIGIN = 1,
+    ORA_ACKLEY = 2,
+    ORA_ROSENBROCK = 3,
+    ORA_CUBIC_MAX = 4
+};
+
+typedef struct {
+    int N;          /* particle_cnt */
+    int D;          /* dimensions */
+    float min_pos;  /* Table 1 */
+    float max_pos;
+    float max_v;    /* min_v = -max_v */
+    float w, c1, c2;
+    int fitness;    /* ORA_* */
+    uint64_t seed;  /* Philox key */
+    uint32_t swarm; /* fourth Philox counter word */
+} ora_params;
+
+typedef struct {
+    float *pos;        /* [N][D] */
+    float *v;          /* [N][D] */
+    float *pbest_pos;  /* [N][D] */
+    float *pbest_fit;  /* [N]    */
+    float *fit;        /* [N]    fitness of the current position */
+    float *gbest_pos;  /* [D]    */
+    float gbest_fit;
+    int64_t gbest_idx;
+    uint32_t t;        /* iterations completed */
+} ora_state;
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): 10 rounds of the 4x32 bijection keyed by key[2]. */
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* One 32-bit word -> uniform in (0,1]: ((w >> 8) + 1) * 2^-24. */
+float ora_u01(uint32_t w);
+
+/* The two uniforms (r1, r2) of particle i, dimension d, iteration t. */
+void ora_draw_r(const ora_params* p, uint32_t t, int i, int d, float* r1, float* r2);
+
+/* Own cos(2*pi*x) and exp(y) in FP32 (range reduction + Taylor polynomial). */
+float ora_cos2pi(float x);
+float ora_exp(float y);
+/* The polynomial coefficients those use, as computed here (for the pins). */
+void ora_cos2pi_coeffs(float out[8]);
+void ora_exp_coeffs(float out[9], float* log2e, float* ln2_hi, float* ln2_lo);
+
+/* Fitness of one position (D contiguous floats); lower is better. */
+float ora_fitness(int fitness, const float* x, int D);
+
+/* Order-preserving 32-bit key of a fitness value (NaN -> 0xFFFFFFFF). */
+uint32_t ora_fit_key(float f);
+
+/* Step 1 of Alg. 1 (t = 0). Arrays must be allocated by the caller. */
+int ora_init(const ora_params* p, ora_state* s);
+
+/* `iters` iterations of Steps 2-5 with synchronous gbest: every particle of
+ * iteration t uses the gbest from the end of iteration t-1. If r_override is
+ * non-null it holds r1,r2 for every (iteration, particle, dim):
+ * r_override[((k*N + i)*D + d)*2 + {0,1}] for k < iters. */
+int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_override);
+
+/* The same, but with gbest updated inside the particle loop exactly as the
+ * sequential Alg. 1 writes it (a later particle sees an earlier one's gbest). */
+int ora_step_serial(const ora_params* p, ora_state* s, int iters, const float* r_override);
+
+/* Lexicographic argmin over (pbest_fit[i], i); NaN ranks last. */
+int64_t ora_argmin_pbest(const ora_params* p, const ora_state* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,197 @@
+"""Python view of the CPU oracle (ctypes over oracle/_build/libcupso_oracle.so).
+
+TEST INFRASTRUCTURE ONLY: used by tests, the smoke check and the benchmark's
+CPU-baseline leg. The library never imports this module.
+
+State arrays are particle-major numpy float32 arrays, shape (N, D).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import build_oracle
+
+SPHERE, RASTRIGIN, ACKLEY, ROSENBROCK, CUBIC_MAX = 0, 1, 2, 3, 4
+
+_lib = None
+
+
+class _Params(C.Structure):
+    _fields_ = [("N", C.c_int), ("D", C.c_int),
+                ("min_pos", C.c_float), ("max_pos", C.c_float), ("max_v", C.c_float),
+                ("w", C.c_float), ("c1", C.c_float), ("c2", C.c_float),
+                ("fitness", C.c_int), ("seed", C.c_uint64), ("swarm", C.c_uint32)]
+
+
+class _State(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("v", C.c_void_p), ("pbest_pos", C.c_void_p),
+                ("pbest_fit", C.c_void_p), ("fit", C.c_void_p), ("gbest_pos", C.c_void_p),
+                ("gbest_fit", C.c_float), ("gbest_idx", C.c_int64), ("t", C.c_uint32)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build_oracle()
+        L = C.CDLL(path)
+        f32p = C.POINTER(C.c_float)
+        L.ora_philox4x32_10.argtypes = [C.POINTER(C.c_uint32)] * 3
+        L.ora_u01.argtypes = [C.c_uint32]
+        L.ora_u01.restype = C.c_float
+        L.ora_draw_r.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_int, C.c_int, f32p, f32p]
+        L.ora_cos2pi.argtypes = [C.c_float]
+        L.ora_cos2pi.restype = C.c_float
+        L.ora_exp.argtypes = [C.c_float]
+        L.ora_exp.restype = C.c_float
+        L.ora_cos2pi_coeffs.argtypes = [f32p]
+        L.ora_exp_coeffs.argtypes = [f32p, f32p, f32p, f32p]
+        L.ora_fitness.argtypes = [C.c_int, f32p, C.c_int]
+        L.ora_fitness.restype = C.c_float
+        L.ora_fit_key.argtypes = [C.c_float]
+        L.ora_fit_key.restype = C.c_uint32
+        for name in ("ora_init",):
+            getattr(L, name).argtypes = [C.POINTER(_Params), C.POINTER(_State)]
+            getattr(L, name).restype = C.c_int
+        for name in ("ora_step_sync", "ora_step_serial"):
+            getattr(L, name).argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int, f32p]
+            getattr(L, name).restype = C.c_int
+        L.ora_argmin_pbest.argtypes = [C.POINTER(_Params), C.POINTER(_State)]
+        L.ora_argmin_pbest.restype = C.c_int64
+        _lib = L
+    return _lib
+
+
+def _f32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (C.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (C.c_uint32 * 4)()
+    lib().ora_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def u01(w):
+    return np.float32(lib().ora_u01(int(w) & 0xFFFFFFFF))
+
+
+def cos2pi(x):
+    return np.float32(lib().ora_cos2pi(float(np.float32(x))))
+
+
+def exp(y):
+    return np.float32(lib().ora_exp(float(np.float32(y))))
+
+
+def cos2pi_coeffs():
+    out = np.zeros(8, np.float32)
+    lib().ora_cos2pi_coeffs(_f32p(out))
+    return out
+
+
+def exp_coeffs():
+    out = np.zeros(9, np.float32)
+    a, b, c = C.c_float(), C.c_float(), C.c_float()
+    lib().ora_exp_coeffs(_f32p(out), C.byref(a), C.byref(b), C.byref(c))
+    return out, np.float32(a.value), np.float32(b.value), np.float32(c.value)
+
+
+def fitness(fid, x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    return np.float32(lib().ora_fitness(int(fid), _f32p(x), int(x.shape[-1])))
+
+
+def fit_key(f):
+    return int(lib().ora_fit_key(float(np.float32(f))))
+
+
+class Swarm:
+    """One swarm as the oracle holds it. Fields mirror Table 1 of the paper."""
+
+    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0):
+        self.p = _Params(int(N), int(D), float(np.float32(min_pos)), float(np.float32(max_pos)),
+                         float(np.float32(max_v)), float(np.float32(w)), float(np.float32(c1)),
+                         float(np.float32(c2)), int(fitness), int(seed), int(swarm))
+        self.N, self.D = int(N), int(D)
+        self.pos = np.zeros((N, D), np.float32)
+        self.v = np.zeros((N, D), np.float32)
+        self.pbest_pos = np.zeros((N, D), np.float32)
+        self.pbest_fit = np.zeros(N, np.float32)
+        self.fit = np.zeros(N, np.float32)
+        self.gbest_pos = np.zeros(D, np.float32)
+        self.s = _State()
+        self._bind()
+
+    def _bind(self):
+        s = self.s
+        s.pos = self.pos.ctypes.data
+        s.v = self.v.ctypes.data
+        s.pbest_pos = self.pbest_pos.ctypes.data
+        s.pbest_fit = self.pbest_fit.ctypes.data
+        s.fit = self.fit.ctypes.data
+        s.gbest_pos = self.gbest_pos.ctypes.data
+
+    @property
+    def t(self):
+        return int(self.s.t)
+
+    @property
+    def gbest_fit(self):
+        return np.float32(self.s.gbest_fit)
+
+    @property
+    def gbest_idx(self):
+        return int(self.s.gbest_idx)
+
+    def init(self):
+        rc = lib().ora_init(C.byref(self.p), C.byref(self.s))
+        if rc != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def set_state(self, pos, v, pbest_pos, pbest_fit, t):
+        """Load a state; gbest is recomputed from pbest (Step 5)."""
+        self.pos[...] = pos
+        self.v[...] = v
+        self.pbest_pos[...] = pbest_pos
+        self.pbest_fit[...] = pbest_fit
+        self.s.t = int(t)
+        g = int(lib().ora_argmin_pbest(C.byref(self.p), C.byref(self.s)))
+        self.s.gbest_idx = g
+        self.s.gbest_fit = float(self.pbest_fit[g])
+        self.gbest_pos[...] = self.pbest_pos[g]
+        return self
+
+    def _r(self, r_override, iters):
+        if r_override is None:
+            return None
+        r = np.ascontiguousarray(r_override, dtype=np.float32)
+        assert r.size == iters * self.N * self.D * 2
+        return r
+
+    def step_sync(self, iters=1, r_override=None):
+        r = self._r(r_override, iters)
+        rc = lib().ora_step_sync(C.byref(self.p), C.byref(self.s), int(iters),
+                                 _f32p(r) if r is not None else None)
+        if rc != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def step_serial(self, iters=1, r_override=None):
+        r = self._r(r_override, iters)
+        rc = lib().ora_step_serial(C.byref(self.p), C.byref(self.s), int(iters),
+                                   _f32p(r) if r is not None else None)
+        if rc != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def draw_r(self, t, i, d):
+        r1, r2 = C.c_float(), C.c_float()
+        lib().ora_draw_r(C.byref(self.p), int(t), int(i), int(d), C.byref(r1), C.byref(r2))
+        return np.float32(r1.value), np.float32(r2.value)
+
+    def argmin_pbest(self):
+        return int(lib().ora_argmin_pbest(C.byref(self.p), C.byref(self.s)))

@@ -1,0 +1,328 @@
+"""Benchmark: particle-dimension updates per second of the fused PSO iteration.
+
+Workload (default): Rosenbrock, N = 2^20 particles, D = 64, the synchronous
+fused iteration (update + fitness + pbest + atomic gbest in one kernel), FP32.
+One step = one PSO iteration over the whole swarm. The swarm state (805 MB)
+is larger than L2 (129 MB), so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). `--impl reference` times the CPU oracle (the
+paper's serial Alg. 1 baseline, Sec. 5.1) on a bounded sample of the same
+workload. Under torchrun with N > 1 every rank runs an independent replica of
+the swarm (no collective on the data path; the barrier and the max-over-ranks
+timing use torch.distributed).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2205_01313_gb300 import workloads  # noqa: E402
+
+METRIC = "particle·dim updates/s per fused iter vs HBM roofline; batched & BF16 vs plain"
+UNIT = "particle-dim updates/s"
+DEFAULT_WORKLOAD = "rosenbrock_1048576x64"
+FALLBACK_HBM_GBS = 6800.0
+KERNEL_SOURCES = ["paper_2205_01313_gb300/csrc/kernels_stream.cu", "paper_2205_01313_gb300/csrc/cupso_device.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_sync_step_kernel.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
+    ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- #
+# distributed plumbing (replicas only)                                        #
+# --------------------------------------------------------------------------- #
+
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------- #
+# clocks (nvidia-smi sampled during the timed region)                          #
+# --------------------------------------------------------------------------- #
+
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 9]
+        self.file.close()
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        smax = [float(r[3]) for r in rows if r[3].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[6 + k] and "Not" not in r[6 + k]})
+        loaded = [x for x in sm if smax and x > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- #
+# roofline inputs                                                              #
+# --------------------------------------------------------------------------- #
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch from the last ncu capture, if the kernel source is unchanged since."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_sha") != kernel_source_sha() or rec.get("workload") != workload:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(N, D):
+    """Compulsory DRAM bytes of one fused iteration: read pos, v, pbest_pos and
+    write pos, v (5 x 4 B per particle-dimension), read pbest_fit (4 B per
+    particle). pbest writes of improving particles are extra and not counted."""
+    return 20 * N * D + 4 * N
+
+
+# --------------------------------------------------------------------------- #
+# our arm                                                                      #
+# --------------------------------------------------------------------------- #
+
+def run_ours(a):
+    import torch
+
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    from paper_2205_01313_gb300 import build as B
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    barrier(world)
+    from paper_2205_01313_gb300 import cupso as P
+
+    cfg = workloads.config(a.workload)
+    N, D, fid = cfg["N"], cfg["D"], cfg["fitness_id"]
+    stream = torch.cuda.Stream()
+    sw = P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], fid, cfg["seed"] + rank,
+                 mode=a.mode, stream=stream.cuda_stream)
+    sw.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)   # one kernel per step: events bracket that launch
+    mode_used = {v: k for k, v in P.MODES.items()}[sw.info()["mode"]]
+
+    for _ in range(a.warmup):
+        sw.step(1)
+    torch.cuda.synchronize()
+
+    K = a.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(K):
+        starts[k].record(stream)
+        sw.step(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = starts[0].elapsed_time(ends[-1])
+    per_launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = max_over_ranks(total_ms, world, device="cuda")
+
+    # End to end through the public API: each step queues one iteration and
+    # reads the step's result (gbest fitness, index, position, status) back
+    # into host memory, waiting for it. The API takes no per-step input data.
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        sw.step(1)
+        rc, fit, idx, pos = sw.gbest()
+    e2e_s = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    e2e_s = max_over_ranks(e2e_s, world, device="cuda")
+    rc, fit, idx, pos = sw.gbest()
+    sw.close()
+
+    work = float(N) * D * K * world
+    value = work / (total_ms / 1e3)
+    bpl = algorithmic_bytes(N, D)
+    achieved = bpl / (per_launch_ms / 1e3) / 1e9
+    peak, peak_src = hbm_peak()
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": a.warmup,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": a.workload, "fitness": workloads.FITNESS_NAMES[fid], "N": N, "D": D,
+                   "mode": mode_used, "step": "one PSO iteration over the whole swarm",
+                   "l2": "inputs larger than L2 (%.0f MB swarm state vs 129 MB L2), no flush"
+                         % (3 * 4 * N * D / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 4 + 8 + 4 * D + 4,
+                "api": "cupso_step(h, 1) + cupso_get_gbest(h, host buffers) per step"},
+        "gpu_launches": K,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": measured_traffic(a.workload),
+                     "kernel": "sync_step_kernel", "algorithmic_bytes_per_launch": bpl,
+                     "launch_ms": per_launch_ms, "peak_source": peak_src},
+        "clocks": clk,
+        "result": {"gbest_fit": float(fit), "gbest_idx": idx, "status": rc},
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, a.cpu_iters)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(cfg, iters):
+    """The oracle as it stands, single-threaded, on the full swarm: init
+    (untimed), then `iters` timed iterations."""
+    from oracle import oracle as O
+    lo, hi, vmax = cfg["bounds"]
+    s = O.Swarm(cfg["N"], cfg["D"], lo, hi, vmax, cfg["w"], cfg["c1"], cfg["c2"], cfg["fitness_id"], cfg["seed"])
+    s.init()
+    t0 = time.perf_counter()
+    s.step_sync(iters)
+    dt = time.perf_counter() - t0
+    return {"value": cfg["N"] * cfg["D"] * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d iterations of the full %s swarm (N=%d, D=%d) after an untimed init; %.1f s"
+                      % (iters, cfg["name"], cfg["N"], cfg["D"], dt),
+            "host_cores_available": len(os.sched_getaffinity(0))}
+
+
+# --------------------------------------------------------------------------- #
+# reference arm: the CPU oracle                                                #
+# --------------------------------------------------------------------------- #
+
+REF_SAMPLE_N = 1 << 14
+
+
+def run_reference(a):
+    world, rank, _ = dist_setup("gloo")
+    if rank != 0:
+        return
+    from oracle import build as OB
+    OB.build_oracle()
+    from oracle import oracle as O
+    cfg = workloads.config(a.workload)
+    n = min(cfg["N"], REF_SAMPLE_N)
+    lo, hi, vmax = cfg["bounds"]
+    s = O.Swarm(n, cfg["D"], lo, hi, vmax, cfg["w"], cfg["c1"], cfg["c2"], cfg["fitness_id"], cfg["seed"]).init()
+    for _ in range(a.warmup):
+        s.step_sync(1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        s.step_sync(1)
+    dt = time.perf_counter() - t0
+    value = n * cfg["D"] * a.steps / dt
+    sample = ("each step: one synchronous iteration of the oracle over a %d-particle sub-swarm of %s "
+              "(D=%d, same bounds, seed and parameters)" % (n, cfg["name"], cfg["D"]))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": a.workload, "fitness": workloads.FITNESS_NAMES[cfg["fitness_id"]], "N": cfg["N"],
+                   "D": cfg["D"], "mode": "oracle (serial synchronous PSO, Alg. 1)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

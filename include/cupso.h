@@ -1,0 +1,194 @@
+/*
+ * cupso.h -- C ABI of the GB300 particle swarm optimizer (libcupso.so).
+ *
+ * The library runs the Standard PSO of Alg. 1 (Sec. 2.1 of "cuPSO: GPU
+ * Parallelization for Particle Swarm Optimization Algorithms") on one GPU:
+ * velocity update (Eq. 1) and position update (Eq. 2) with the clamps of
+ * Alg. 1, fitness of every particle, personal-best update, and the global-best
+ * aggregation of Sec. 3 (conditional atomic update instead of a tree
+ * reduction; synchronous and asynchronous lock-protected forms). The
+ * parameters are those of Table 1 (w, c1, c2, min/max_pos, max_v, particle
+ * count); min_v = -max_v.
+ *
+ * Conventions for every function:
+ *  - Return value: CUPSO_OK (0) or a negative cupso_status. No exception or
+ *    abort crosses the ABI. Arguments are checked on the host before any GPU
+ *    work; an invalid argument changes nothing.
+ *  - Host pointers are host memory owned by the caller. The library owns all
+ *    device memory of a handle and frees it in cupso_destroy.
+ *  - Work is queued on the handle's stream (cupso_set_stream; default: a
+ *    non-blocking stream the handle creates). Only cupso_get_gbest,
+ *    cupso_get_state, cupso_set_state, cupso_create and cupso_destroy wait
+ *    for it. A device-side error (timeout of a bounded wait, NaN fitness)
+ *    sets a sticky status that the next waiting call returns.
+ *  - One handle must not be used from two host threads at once.
+ *  - Random numbers: Philox4x32-10 keyed by the 64-bit seed with the counter
+ *    (d >> 1, particle, iteration, swarm id), so results are reproducible
+ *    and independent of how the work is scheduled (Sec. 4.4 draws r1, r2
+ *    uniformly; here they lie in (0, 1]).
+ *  - The optimizer minimises. CUPSO_CUBIC_MAX is the paper's Eq. 3, which the
+ *    paper maximises, minimised as its negation; its reported fitness is -f.
+ */
+#ifndef CUPSO_H
+#define CUPSO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUPSO_VERSION 1
+
+/* Symbols of the library's ABI (everything else in libcupso.so is hidden). */
+#if defined(__GNUC__)
+#define CUPSO_API __attribute__((visibility("default")))
+#else
+#define CUPSO_API
+#endif
+
+typedef struct cupso_swarm* cupso_handle; /* opaque, owned by the library */
+
+/* Search box, the same for every dimension (Table 1): positions are clamped
+ * to [min_pos, max_pos], velocities to [-max_v, max_v]. Requires
+ * min_pos < max_pos and max_v > 0, all finite. */
+typedef struct {
+    float min_pos;
+    float max_pos;
+    float max_v;
+} cupso_bounds;
+
+typedef enum {
+    CUPSO_SPHERE = 0,     /* sum x^2                                   */
+    CUPSO_RASTRIGIN = 1,  /* 10 D + sum (x^2 - 10 cos 2 pi x)          */
+    CUPSO_ACKLEY = 2,     /* -20 e^{-0.2 sqrt(mean x^2)} - e^{mean cos 2 pi x} + 20 + e */
+    CUPSO_ROSENBROCK = 3, /* sum 100 (x_{d+1} - x_d^2)^2 + (1 - x_d)^2 */
+    CUPSO_CUBIC_MAX = 4   /* Eq. 3: maximise sum x^3 - 0.8 x^2 - 1000 x + 8000 */
+} cupso_fitness;
+
+typedef enum {
+    CUPSO_OK = 0,
+    CUPSO_ERR_INVALID_ARG = -1,
+    CUPSO_ERR_OOM = -2,
+    CUPSO_ERR_CUDA = -3,
+    CUPSO_ERR_DEVICE_TIMEOUT = -4, /* a bounded device-side wait expired */
+    CUPSO_ERR_NAN = -5,            /* a fitness evaluated to NaN          */
+    CUPSO_ERR_UNSUPPORTED = -6
+} cupso_status;
+
+/* How the global best is aggregated (cupso_set_option(CUPSO_OPT_MODE)). */
+typedef enum {
+    CUPSO_MODE_AUTO = 0,   /* ONCHIP when the swarm fits, else SYNC                        */
+    CUPSO_MODE_SYNC = 1,   /* fused kernel, conditional atomicMin + last-CTA gather (Sec. 3.1) */
+    CUPSO_MODE_TREE = 2,   /* parallel-reduction baseline: two kernels per iteration (Sec. 2.2) */
+    CUPSO_MODE_TREE_UNROLLED = 3, /* the same with the unrolled reduction (Sec. 2.2)       */
+    CUPSO_MODE_ASYNC = 4,  /* persistent CTAs, no grid barrier, lock-protected gbest (Sec. 3.2) */
+    CUPSO_MODE_ONCHIP = 5  /* whole swarm in one CTA cluster's shared memory, many iterations per launch */
+} cupso_mode;
+
+typedef enum {
+    CUPSO_OPT_MODE = 1,           /* value: cupso_mode                                         */
+    CUPSO_OPT_GRAPH_CHUNK = 2,    /* iterations per captured CUDA graph (SYNC/TREE); 0 = none  */
+    CUPSO_OPT_WAIT_LIMIT_NS = 3,  /* bound of every device-side wait (default 2e9 ns)          */
+    CUPSO_OPT_CLEAR_STATUS = 4,   /* any value: clear the sticky device status                 */
+    CUPSO_OPT_GRID = 5,           /* CTAs of the persistent kernels (SYNC/ASYNC); 0 = automatic */
+    CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
+                                       lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
+} cupso_option;
+
+typedef struct {
+    int N, D;             /* particles, dimensions                   */
+    int Np;               /* N rounded up to 128 (device row stride) */
+    int mode;             /* cupso_mode the next cupso_step will use */
+    uint32_t t;           /* iterations completed                    */
+    int sync_grid;        /* CTAs of the persistent SYNC launch      */
+    int async_grid;       /* CTAs of the ASYNC launch                */
+    int onchip_cluster;   /* CTAs per cluster if ONCHIP fits, else 0 */
+    uint64_t device_bytes;/* device memory held by the handle        */
+} cupso_info;
+
+/* Create a swarm and run Step 1 of Alg. 1 (iteration t = 0) on the device:
+ * pos ~ U(min_pos, max_pos], v ~ U(-max_v, max_v], pbest = pos, gbest =
+ * lowest-index argmin of the fitness. D >= 1, N >= 1, N * D < 2^31 and
+ * N < 2^31 - 128. Waits for the initialisation. On success *out is a new
+ * handle; on error *out is set to NULL. */
+CUPSO_API int cupso_create(int D, int N, const cupso_bounds* bounds, float w, float c1, float c2,
+                 int fitness_id, uint64_t seed, cupso_handle* out);
+
+/* Queue this handle's work on `cuda_stream` (a cudaStream_t; NULL selects
+ * the handle's own non-blocking stream). Work already queued is not moved. */
+CUPSO_API int cupso_set_stream(cupso_handle h, void* cuda_stream);
+
+/* Set an option (cupso_option). Unknown keys: CUPSO_ERR_INVALID_ARG. */
+CUPSO_API int cupso_set_option(cupso_handle h, int key, long long value);
+
+/* Queue `iters` >= 0 iterations of Steps 2-5 (Alg. 1). SYNC/TREE/ONCHIP are
+ * synchronous PSO: every particle of iteration t uses the gbest from the end
+ * of iteration t-1 (Sec. 2.2, "PPSO"), and the result does not depend on the
+ * mode or the launch shape. ASYNC lets CTAs run ahead of each other, so its
+ * trajectory depends on timing (Sec. 3.2). Does not wait. */
+CUPSO_API int cupso_step(cupso_handle h, int iters);
+
+/* Wait for the handle's stream, then return gbest: *fit_out = gbest_fit,
+ * pos_out[0..D-1] = gbest_pos, *idx_out = index of the particle whose pbest
+ * it is. Any output pointer may be NULL. Returns the sticky device status
+ * (CUPSO_ERR_DEVICE_TIMEOUT or CUPSO_ERR_NAN) when one is set; the outputs
+ * are filled in that case too. */
+CUPSO_API int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx_out);
+
+/* Wait, then copy the swarm state to host arrays in particle-major layout:
+ * pos, v, pbest_pos are [N][D] (element i*D + d), pbest_fit is [N]; *t_out =
+ * iterations completed. Any pointer may be NULL. */
+CUPSO_API int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, float* pbest_fit,
+                    uint32_t* t_out);
+
+/* Load a swarm state (layout as cupso_get_state; all four arrays required)
+ * and set the iteration counter to t; gbest is recomputed on the device as
+ * the lowest-index argmin of pbest_fit. Waits for the upload. Together with
+ * cupso_get_state this is checkpoint and resume: the random draws depend only
+ * on (seed, swarm, t, particle, dimension). */
+CUPSO_API int cupso_set_state(cupso_handle h, const float* pos, const float* v, const float* pbest_pos,
+                    const float* pbest_fit, uint32_t t);
+
+/* Fill *info. */
+CUPSO_API int cupso_get_info(cupso_handle h, cupso_info* info);
+
+/* One problem of a batch: an independent swarm with its own parameters.
+ * swarm_id is the fourth word of the Philox counter. */
+typedef struct {
+    int D, N;
+    cupso_bounds bounds;
+    float w, c1, c2;
+    int fitness_id;
+    uint64_t seed;
+    uint32_t swarm_id;
+} cupso_problem;
+
+typedef struct {
+    float fit;        /* gbest_fit after `iters` iterations        */
+    int64_t idx;      /* its particle                              */
+    float* pos;       /* caller-allocated D floats, or NULL        */
+    int status;       /* cupso_status of this swarm                */
+} cupso_result;
+
+/* Solve n_swarms independent problems for `iters` iterations each (Step 1
+ * included) on `cuda_stream` (NULL: an internal stream) and wait. Each
+ * swarm's result equals what cupso_create with seed and swarm_id, then
+ * cupso_step(iters), would give. Returns CUPSO_OK if every swarm succeeded,
+ * else the first failing status; results[k].status holds each swarm's. */
+CUPSO_API int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters,
+                      cupso_result* results, void* cuda_stream);
+
+/* Wait for the handle's work and free everything it holds. NULL is a no-op. */
+CUPSO_API int cupso_destroy(cupso_handle h);
+
+/* Static description of a status code. */
+CUPSO_API const char* cupso_status_string(int status);
+
+/* Detail of the last error on the calling host thread (static storage). */
+CUPSO_API const char* cupso_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUPSO_H */

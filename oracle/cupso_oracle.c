@@ -316,27 +316,21 @@ int ora_init(const ora_params* p, ora_state* s)
 /* Steps 2-5                                                                 */
 /* ------------------------------------------------------------------------- */
 
-/* Steps 2-4 for particle i at iteration t: Eq. 1 with the clamp to
- * [-max_v, max_v], Eq. 2 with the clamp to [min_pos, max_pos], fitness, and the
- * personal-best update. gbest_pos is read, never written. */
-static void move_particle(const ora_params* p, ora_state* s, uint32_t t, int i,
-                          const float* r_iter /* null or [N][D][2] */)
+float ora_move_one(const ora_params* p, uint32_t t, int i, float* pos, float* v, float* pbest,
+                   float* pbest_fit, const float* gbest_pos, const float* r_particle)
 {
     const int D = p->D;
-    float* pos = s->pos + (size_t)i * D;
-    float* v = s->v + (size_t)i * D;
-    float* pbest = s->pbest_pos + (size_t)i * D;
     for (int d = 0; d < D; ++d) {
         float r1, r2;
-        if (r_iter) {
-            r1 = r_iter[((size_t)i * D + d) * 2 + 0];
-            r2 = r_iter[((size_t)i * D + d) * 2 + 1];
+        if (r_particle) {
+            r1 = r_particle[2 * d + 0];
+            r2 = r_particle[2 * d + 1];
         } else {
             ora_draw_r(p, t, i, d, &r1, &r2);
         }
         /* Eq. 1: v <- w v + c1 r1 (pbest - pos) + c2 r2 (gbest - pos) */
         float cognitive = pbest[d] - pos[d];
-        float social = s->gbest_pos[d] - pos[d];
+        float social = gbest_pos[d] - pos[d];
         float vel = p->w * v[d];
         vel = fmaf(p->c1 * r1, cognitive, vel);
         vel = fmaf(p->c2 * r2, social, vel);
@@ -344,11 +338,21 @@ static void move_particle(const ora_params* p, ora_state* s, uint32_t t, int i,
         /* Eq. 2: pos <- pos + v */
         pos[d] = clampf(pos[d] + v[d], p->min_pos, p->max_pos);
     }
-    s->fit[i] = ora_fitness(p->fitness, pos, D);          /* Step 3 */
-    if (s->fit[i] < s->pbest_fit[i]) {                      /* Step 4 */
-        s->pbest_fit[i] = s->fit[i];
+    float fit = ora_fitness(p->fitness, pos, D);             /* Step 3 */
+    if (fit < *pbest_fit) {                                   /* Step 4 */
+        *pbest_fit = fit;
         memcpy(pbest, pos, sizeof(float) * (size_t)D);
     }
+    return fit;
+}
+
+/* Steps 2-4 for particle i of the swarm at iteration t (gbest_pos is read). */
+static void move_particle(const ora_params* p, ora_state* s, uint32_t t, int i,
+                          const float* r_iter /* null or [N][D][2] */)
+{
+    const size_t D = (size_t)p->D;
+    s->fit[i] = ora_move_one(p, t, i, s->pos + i * D, s->v + i * D, s->pbest_pos + i * D,
+                             &s->pbest_fit[i], s->gbest_pos, r_iter ? r_iter + (size_t)i * D * 2 : NULL);
 }
 
 int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_override)

@@ -92,6 +92,14 @@ int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_o
  * sequential Alg. 1 writes it (a later particle sees an earlier one's gbest). */
 int ora_step_serial(const ora_params* p, ora_state* s, int iters, const float* r_override);
 
+/* Steps 2-4 of Alg. 1 for ONE particle with global index i at iteration t:
+ * Eq. 1 and Eq. 2 with their clamps, the fitness, and the strict pbest
+ * update, in place; gbest_pos is read only. r_particle (nullable) overrides
+ * the draws: r_particle[2d], r_particle[2d+1] = r1, r2 of dimension d.
+ * Returns the new fitness. */
+float ora_move_one(const ora_params* p, uint32_t t, int i, float* pos, float* v, float* pbest_pos,
+                   float* pbest_fit, const float* gbest_pos, const float* r_particle);
+
 /* Lexicographic argmin over (pbest_fit[i], i); NaN ranks last. */
 int64_t ora_argmin_pbest(const ora_params* p, const ora_state* s);
 

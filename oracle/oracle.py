@@ -56,6 +56,8 @@ def lib():
         for name in ("ora_step_sync", "ora_step_serial"):
             getattr(L, name).argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int, f32p]
             getattr(L, name).restype = C.c_int
+        L.ora_move_one.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_int, f32p, f32p, f32p, f32p, f32p, f32p]
+        L.ora_move_one.restype = C.c_float
         L.ora_argmin_pbest.argtypes = [C.POINTER(_Params), C.POINTER(_State)]
         L.ora_argmin_pbest.restype = C.c_int64
         _lib = L
@@ -192,6 +194,18 @@ class Swarm:
         r1, r2 = C.c_float(), C.c_float()
         lib().ora_draw_r(C.byref(self.p), int(t), int(i), int(d), C.byref(r1), C.byref(r2))
         return np.float32(r1.value), np.float32(r2.value)
+
+    def move_one(self, t, i, pos, v, pbest_pos, pbest_fit, gbest_pos):
+        """Steps 2-4 for one particle (global index i) at iteration t, on copies.
+        Returns (pos, v, pbest_pos, pbest_fit, fit)."""
+        pos = np.array(pos, np.float32)
+        v = np.array(v, np.float32)
+        pb = np.array(pbest_pos, np.float32)
+        pf = np.array([pbest_fit], np.float32)
+        g = np.ascontiguousarray(gbest_pos, np.float32)
+        f = lib().ora_move_one(C.byref(self.p), int(t), int(i), _f32p(pos), _f32p(v), _f32p(pb), _f32p(pf),
+                               _f32p(g), None)
+        return pos, v, pb, np.float32(pf[0]), np.float32(f)
 
     def argmin_pbest(self):
         return int(lib().ora_argmin_pbest(C.byref(self.p), C.byref(self.s)))

@@ -1,0 +1,483 @@
+// cupso_api.cu -- the C ABI declared in include/cupso.h.
+//
+// Host-side control only (Sec. 2.2 splits PSO into host control and device
+// work): argument checks, one device arena per swarm, stream and CUDA-graph
+// management, and the launch of the kernels of kernels_stream.cu and
+// kernels_onchip.cu. Every step of the iteration itself runs on the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cupso.h"
+#include "cupso_device.cuh"
+#include "cupso_internal.h"
+
+using namespace cupso;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int code, const char* fmt, const char* detail = "") {
+    std::snprintf(g_last_error, sizeof(g_last_error), fmt, detail);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? CUPSO_ERR_OOM : CUPSO_ERR_CUDA;
+}
+
+#define CUPSO_CUDA(call, where)                      \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct cupso_swarm {
+    SwarmDev dev{};
+    int N = 0, D = 0, Np = 0, fid = 0;
+    uint64_t seed = 0;
+    uint32_t swarm = 0;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    cudaStream_t own = nullptr;     // the handle's non-blocking stream
+    cudaStream_t stream = nullptr;  // where work is queued (own or the caller's)
+    cudaStream_t capture = nullptr; // graphs are captured here, launched on `stream`
+    int device = 0, num_sms = 1;
+    int mode = CUPSO_MODE_AUTO;
+    int graph_chunk = 16;
+    cudaGraphExec_t graph = nullptr;
+    int graph_mode = -1, graph_len = 0;
+    uint32_t t_host = 0;
+    int hold_lock = 0;
+    int grid_override = 0;
+    int onchip_cluster = 0;
+};
+
+namespace {
+
+int resolved_mode(const cupso_swarm* h) {
+    if (h->mode != CUPSO_MODE_AUTO) return h->mode;
+    return h->onchip_cluster > 0 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
+}
+
+int sync_grid(const cupso_swarm* h) {
+    const int ntiles = tiles_of(h->Np);
+    int g = h->grid_override > 0 ? h->grid_override : h->num_sms * sync_blocks_per_sm(h->fid, h->D);
+    return g < ntiles ? g : ntiles;
+}
+
+// ASYNC uses small CTAs when the swarm is small, so that it still spreads
+// over many independently running CTAs.
+int async_block(const cupso_swarm* h) {
+    return (h->Np / kTile >= 2 * h->num_sms) ? kBlock : 32;
+}
+
+int async_grid(const cupso_swarm* h) {
+    const int tile = async_block(h) * kPerThread;
+    const int ntiles = (h->Np + tile - 1) / tile;
+    const int per_sm = async_blocks_per_sm(h->fid, h->D) * (kBlock / async_block(h));
+    int g = h->grid_override > 0 ? h->grid_override : h->num_sms * per_sm;
+    return g < ntiles ? g : ntiles;
+}
+
+void drop_graph(cupso_swarm* h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+    h->graph_mode = -1;
+    h->graph_len = 0;
+}
+
+cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
+    switch (mode) {
+        case CUPSO_MODE_SYNC: return launch_sync_step(h->dev, h->fid, sync_grid(h), st);
+        case CUPSO_MODE_TREE: return launch_tree_step(h->dev, h->fid, false, st);
+        case CUPSO_MODE_TREE_UNROLLED: return launch_tree_step(h->dev, h->fid, true, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// A graph of `len` iterations. The kernels read the iteration counter from
+// device memory, so one captured graph serves every later chunk.
+int ensure_graph(cupso_swarm* h, int mode, int len) {
+    if (h->graph && h->graph_mode == mode && h->graph_len == len) return CUPSO_OK;
+    drop_graph(h);
+    if (!h->capture) CUPSO_CUDA(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "cudaStreamCreate");
+    CUPSO_CUDA(cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < len && le == cudaSuccess; ++k) le = launch_one(h, mode, h->capture);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h->capture, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "kernel launch during capture");
+    }
+    if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+    cudaError_t ie = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        h->graph = nullptr;
+        return cuda_fail(ie, "cudaGraphInstantiate");
+    }
+    h->graph_mode = mode;
+    h->graph_len = len;
+    return CUPSO_OK;
+}
+
+int check_problem(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid) {
+    if (D < 1 || N < 1) return fail(CUPSO_ERR_INVALID_ARG, "D and N must be >= 1%s");
+    if ((long long)N > (long long)0x7FFFFFFF - kPad) return fail(CUPSO_ERR_INVALID_ARG, "N too large%s");
+    const long long Np = ((long long)N + kPad - 1) / kPad * kPad;
+    if (Np * (long long)D >= (1ll << 31)) return fail(CUPSO_ERR_INVALID_ARG, "N * D must be < 2^31%s");
+    if (!b) return fail(CUPSO_ERR_INVALID_ARG, "bounds is NULL%s");
+    if (!std::isfinite(b->min_pos) || !std::isfinite(b->max_pos) || !std::isfinite(b->max_v))
+        return fail(CUPSO_ERR_INVALID_ARG, "bounds must be finite%s");
+    if (!(b->min_pos < b->max_pos)) return fail(CUPSO_ERR_INVALID_ARG, "min_pos must be < max_pos%s");
+    if (!(b->max_v > 0.0f)) return fail(CUPSO_ERR_INVALID_ARG, "max_v must be > 0%s");
+    if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
+        return fail(CUPSO_ERR_INVALID_ARG, "w, c1, c2 must be finite%s");
+    if (fid < CUPSO_SPHERE || fid > CUPSO_CUBIC_MAX) return fail(CUPSO_ERR_INVALID_ARG, "unknown fitness_id%s");
+    return CUPSO_OK;
+}
+
+int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid, uint64_t seed,
+                 uint32_t swarm, cudaStream_t user_stream, cupso_handle* out) {
+    if (!out) return fail(CUPSO_ERR_INVALID_ARG, "out is NULL%s");
+    *out = nullptr;
+    int rc = check_problem(D, N, b, w, c1, c2, fid);
+    if (rc) return rc;
+    cupso_swarm* h = new (std::nothrow) cupso_swarm();
+    if (!h) return fail(CUPSO_ERR_OOM, "host allocation failed%s");
+    h->N = N;
+    h->D = D;
+    h->Np = (N + kPad - 1) / kPad * kPad;
+    h->fid = fid;
+    h->seed = seed;
+    h->swarm = swarm;
+    auto bail = [&](int code) {
+        cupso_destroy(h);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    h->stream = user_stream ? user_stream : h->own;
+
+    // One arena: x, v, pb [D][Np]; pf [Np]; G [2][D]; Grec [D]; aux; words.
+    const size_t A = 256;
+    const size_t plane = sizeof(float) * (size_t)D * (size_t)h->Np;
+    const size_t ntiles = (size_t)tiles_of(h->Np);
+    size_t off = 0;
+    const size_t o_x = off; off = align_up(off + plane, A);
+    const size_t o_v = off; off = align_up(off + plane, A);
+    const size_t o_pb = off; off = align_up(off + plane, A);
+    const size_t o_pf = off; off = align_up(off + sizeof(float) * (size_t)h->Np, A);
+    const size_t o_G = off; off = align_up(off + sizeof(float) * 2 * (size_t)D, A);
+    const size_t o_Grec = off; off = align_up(off + sizeof(float) * (size_t)D, A);
+    const size_t o_aux = off; off = align_up(off + sizeof(unsigned long long) * ntiles, A);
+    const size_t o_words = off; off = align_up(off + 128, A);
+    h->arena_bytes = off;
+    e = cudaMalloc(&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    char* base = static_cast<char*>(h->arena);
+    SwarmDev& s = h->dev;
+    s.x = reinterpret_cast<float*>(base + o_x);
+    s.v = reinterpret_cast<float*>(base + o_v);
+    s.pb = reinterpret_cast<float*>(base + o_pb);
+    s.pf = reinterpret_cast<float*>(base + o_pf);
+    s.G = reinterpret_cast<float*>(base + o_G);
+    s.Grec = reinterpret_cast<float*>(base + o_Grec);
+    s.aux = reinterpret_cast<unsigned long long*>(base + o_aux);
+    unsigned long long* w64 = reinterpret_cast<unsigned long long*>(base + o_words);
+    s.gkey = w64;        // [2]
+    s.claim = w64 + 2;
+    s.reckey = w64 + 3;
+    unsigned int* w32 = reinterpret_cast<unsigned int*>(w64 + 4);
+    s.ticket = w32 + 0;
+    s.t_dev = w32 + 1;
+    s.status = w32 + 2;
+    s.lock = w32 + 3;
+    s.seq = w32 + 4;
+    s.N = N;
+    s.D = D;
+    s.Np = h->Np;
+    s.lo = b->min_pos;
+    s.hi = b->max_pos;
+    s.vmax = b->max_v;
+    s.w = w;
+    s.c1 = c1;
+    s.c2 = c2;
+    s.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+    s.key1 = (uint32_t)(seed >> 32);
+    s.swarm = swarm;
+    s.wait_limit_ns = 2000000000ll;
+
+    int cl = 0, per = 0;
+    h->onchip_cluster = onchip_fits(N, D, &cl, &per) ? cl : 0;
+
+    e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
+    const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
+    e = launch_init(s, fid, grid, h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "init launch"));
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "init"));
+    *out = h;
+    return CUPSO_OK;
+}
+
+int read_status(cupso_swarm* h, unsigned* st) {
+    CUPSO_CUDA(cudaMemcpyAsync(st, h->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return CUPSO_OK;
+}
+
+int status_code(unsigned st) {
+    if (st & kStatusTimeout) return CUPSO_ERR_DEVICE_TIMEOUT;
+    if (st & kStatusNaN) return CUPSO_ERR_NAN;
+    return CUPSO_OK;
+}
+
+float key_to_fit(unsigned long long key) {
+    const uint32_t k = (uint32_t)(key >> 32);
+    if (k == 0xFFFFFFFFu) return NAN;
+    const uint32_t bits = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cupso_create(int D, int N, const cupso_bounds* bounds, float w, float c1, float c2, int fitness_id,
+                 uint64_t seed, cupso_handle* out) {
+    return create_swarm(D, N, bounds, w, c1, c2, fitness_id, seed, 0u, nullptr, out);
+}
+
+int cupso_set_stream(cupso_handle h, void* cuda_stream) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    h->stream = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->own;
+    return CUPSO_OK;
+}
+
+int cupso_set_option(cupso_handle h, int key, long long value) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    switch (key) {
+        case CUPSO_OPT_MODE:
+            if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_ONCHIP)
+                return fail(CUPSO_ERR_INVALID_ARG, "unknown mode%s");
+            if (value == CUPSO_MODE_ONCHIP && h->onchip_cluster == 0)
+                return fail(CUPSO_ERR_UNSUPPORTED, "swarm does not fit in one cluster's shared memory%s");
+            h->mode = (int)value;
+            return CUPSO_OK;
+        case CUPSO_OPT_GRAPH_CHUNK:
+            if (value < 0 || value > 4096) return fail(CUPSO_ERR_INVALID_ARG, "graph chunk out of range%s");
+            h->graph_chunk = (int)value;
+            drop_graph(h);
+            return CUPSO_OK;
+        case CUPSO_OPT_WAIT_LIMIT_NS:
+            if (value < 1000 || value > 60000000000ll) return fail(CUPSO_ERR_INVALID_ARG, "wait limit out of range%s");
+            h->dev.wait_limit_ns = value;
+            drop_graph(h);
+            return CUPSO_OK;
+        case CUPSO_OPT_CLEAR_STATUS:
+            CUPSO_CUDA(cudaMemsetAsync(h->dev.status, 0, sizeof(unsigned), h->stream), "cudaMemsetAsync");
+            return CUPSO_OK;
+        case CUPSO_OPT_GRID:
+            if (value < 0 || value > (1 << 20)) return fail(CUPSO_ERR_INVALID_ARG, "grid out of range%s");
+            h->grid_override = (int)value;
+            drop_graph(h);
+            return CUPSO_OK;
+        case CUPSO_OPT_FAULT_HOLD_LOCK:
+            h->hold_lock = value ? 1 : 0;
+            return CUPSO_OK;
+        default:
+            return fail(CUPSO_ERR_INVALID_ARG, "unknown option%s");
+    }
+}
+
+int cupso_step(cupso_handle h, int iters) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (iters < 0) return fail(CUPSO_ERR_INVALID_ARG, "iters must be >= 0%s");
+    if (iters == 0) return CUPSO_OK;
+    if ((uint64_t)h->t_host + (uint64_t)iters > 0xFFFFFFFFull)
+        return fail(CUPSO_ERR_INVALID_ARG, "iteration counter would overflow%s");
+    const int mode = resolved_mode(h);
+    cudaError_t e = cudaSuccess;
+    if (mode == CUPSO_MODE_ASYNC) {
+        e = launch_async(h->dev, h->fid, async_grid(h), async_block(h), h->t_host + 1u, iters, h->hold_lock,
+                         h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "async launch");
+    } else if (mode == CUPSO_MODE_ONCHIP) {
+        e = launch_onchip(h->dev, h->fid, iters, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "on-chip launch");
+    } else {
+        int left = iters;
+        const int L = h->graph_chunk;
+        if (L > 1 && left >= L) {
+            int rc = ensure_graph(h, mode, L);
+            if (rc) return rc;
+            while (left >= L) {
+                e = cudaGraphLaunch(h->graph, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+                left -= L;
+            }
+        }
+        for (; left > 0; --left) {
+            e = launch_one(h, mode, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "step launch");
+        }
+    }
+    h->t_host += (uint32_t)iters;
+    return CUPSO_OK;
+}
+
+int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx_out) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    const int cur = (int)(h->t_host & 1u);
+    unsigned long long key = 0;
+    unsigned st = 0;
+    CUPSO_CUDA(cudaMemcpyAsync(&key, h->dev.gkey + cur, sizeof(key), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync");
+    if (pos_out)
+        CUPSO_CUDA(cudaMemcpyAsync(pos_out, h->dev.G + (size_t)cur * h->D, sizeof(float) * (size_t)h->D,
+                                   cudaMemcpyDeviceToHost, h->stream),
+                   "cudaMemcpyAsync");
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (fit_out) *fit_out = key_to_fit(key);
+    if (idx_out) *idx_out = (int64_t)(key & 0xFFFFFFFFull);
+    rc = status_code(st);
+    if (rc) fail(rc, "device status set: %s", cupso_status_string(rc));
+    return rc;
+}
+
+int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, float* pbest_fit, uint32_t* t_out) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
+    std::vector<float> stage;
+    float* outs[3] = {pos, v, pbest_pos};
+    const float* srcs[3] = {h->dev.x, h->dev.v, h->dev.pb};
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (int a = 0; a < 3; ++a) {
+        if (!outs[a]) continue;
+        stage.resize(D * Np);
+        CUPSO_CUDA(cudaMemcpy(stage.data(), srcs[a], sizeof(float) * D * Np, cudaMemcpyDeviceToHost), "cudaMemcpy");
+        for (size_t i = 0; i < N; ++i)
+            for (size_t d = 0; d < D; ++d) outs[a][i * D + d] = stage[d * Np + i];
+    }
+    if (pbest_fit)
+        CUPSO_CUDA(cudaMemcpy(pbest_fit, h->dev.pf, sizeof(float) * N, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (t_out) *t_out = h->t_host;
+    return CUPSO_OK;
+}
+
+int cupso_set_state(cupso_handle h, const float* pos, const float* v, const float* pbest_pos,
+                    const float* pbest_fit, uint32_t t) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (!pos || !v || !pbest_pos || !pbest_fit) return fail(CUPSO_ERR_INVALID_ARG, "state array is NULL%s");
+    const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    std::vector<float> stage(D * Np, 0.0f);
+    const float* ins[3] = {pos, v, pbest_pos};
+    float* dsts[3] = {h->dev.x, h->dev.v, h->dev.pb};
+    for (int a = 0; a < 3; ++a) {
+        for (size_t i = 0; i < N; ++i)
+            for (size_t d = 0; d < D; ++d) stage[d * Np + i] = ins[a][i * D + d];
+        CUPSO_CUDA(cudaMemcpy(dsts[a], stage.data(), sizeof(float) * D * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+    std::vector<float> pf(Np, INFINITY);
+    std::memcpy(pf.data(), pbest_fit, sizeof(float) * N);
+    CUPSO_CUDA(cudaMemcpy(h->dev.pf, pf.data(), sizeof(float) * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
+    CUPSO_CUDA(launch_recompute(h->dev, t, h->stream), "recompute launch");
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    h->t_host = t;
+    return CUPSO_OK;
+}
+
+int cupso_get_info(cupso_handle h, cupso_info* info) {
+    if (!h || !info) return fail(CUPSO_ERR_INVALID_ARG, "NULL argument%s");
+    info->N = h->N;
+    info->D = h->D;
+    info->Np = h->Np;
+    info->mode = resolved_mode(h);
+    info->t = h->t_host;
+    info->sync_grid = sync_grid(h);
+    info->async_grid = async_grid(h);
+    info->onchip_cluster = h->onchip_cluster;
+    info->device_bytes = (uint64_t)h->arena_bytes;
+    return CUPSO_OK;
+}
+
+int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters, cupso_result* results,
+                      void* cuda_stream) {
+    if (n_swarms < 0 || iters < 0) return fail(CUPSO_ERR_INVALID_ARG, "n_swarms and iters must be >= 0%s");
+    if (n_swarms > 0 && (!problems || !results)) return fail(CUPSO_ERR_INVALID_ARG, "NULL problems/results%s");
+    for (int k = 0; k < n_swarms; ++k) {
+        const cupso_problem& p = problems[k];
+        int rc = check_problem(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id);
+        if (rc) return rc;
+    }
+    int first = CUPSO_OK;
+    for (int k = 0; k < n_swarms; ++k) {
+        const cupso_problem& p = problems[k];
+        cupso_handle h = nullptr;
+        int rc = create_swarm(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id, p.seed, p.swarm_id,
+                              static_cast<cudaStream_t>(cuda_stream), &h);
+        if (rc == CUPSO_OK) rc = cupso_step(h, iters);
+        if (rc == CUPSO_OK) rc = cupso_get_gbest(h, &results[k].fit, results[k].pos, &results[k].idx);
+        results[k].status = rc;
+        if (h) cupso_destroy(h);
+        if (rc != CUPSO_OK && first == CUPSO_OK) first = rc;
+    }
+    return first;
+}
+
+int cupso_destroy(cupso_handle h) {
+    if (!h) return CUPSO_OK;
+    int rc = CUPSO_OK;
+    if (h->stream) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
+    }
+    drop_graph(h);
+    if (h->arena) cudaFree(h->arena);
+    if (h->capture) cudaStreamDestroy(h->capture);
+    if (h->own) cudaStreamDestroy(h->own);
+    delete h;
+    return rc;
+}
+
+const char* cupso_status_string(int status) {
+    switch (status) {
+        case CUPSO_OK: return "ok";
+        case CUPSO_ERR_INVALID_ARG: return "invalid argument";
+        case CUPSO_ERR_OOM: return "out of device memory";
+        case CUPSO_ERR_CUDA: return "CUDA error";
+        case CUPSO_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
+        case CUPSO_ERR_NAN: return "fitness evaluated to NaN";
+        case CUPSO_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char* cupso_last_error(void) { return g_last_error; }
+
+}  // extern "C"

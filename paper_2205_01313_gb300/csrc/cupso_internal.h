@@ -1,0 +1,38 @@
+// cupso_internal.h -- host-side launch wrappers shared by the C-ABI layer.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "cupso_device.cuh"
+
+namespace cupso {
+
+constexpr int kBlock = 256;             // threads per CTA of the streaming kernels
+constexpr int kPerThread = 4;           // particles per thread (one float4)
+constexpr int kTile = kBlock * kPerThread;
+constexpr int kPad = 128;               // Np = N rounded up to a multiple of this
+
+__host__ __device__ inline int tiles_of(int Np) { return (Np + kTile - 1) / kTile; }
+
+// All wrappers return a cudaError_t of the launch.
+cudaError_t launch_init(const SwarmDev& s, int fid, int grid, cudaStream_t st);
+cudaError_t launch_sync_step(const SwarmDev& s, int fid, int grid, cudaStream_t st);
+cudaError_t launch_tree_step(const SwarmDev& s, int fid, bool unrolled, cudaStream_t st);
+// ASYNC: `block` threads per CTA (a multiple of 32, <= kBlock), each CTA a
+// tile of 4 * block particles per pass.
+cudaError_t launch_async(const SwarmDev& s, int fid, int grid, int block, uint32_t t_first, int iters,
+                         int hold_lock, cudaStream_t st);
+cudaError_t launch_recompute(const SwarmDev& s, uint32_t t, cudaStream_t st);
+
+// Resident CTAs per SM of the persistent kernels (for grid sizing).
+int sync_blocks_per_sm(int fid, int D);
+int async_blocks_per_sm(int fid, int D);
+
+// On-chip variant: whole swarm in the shared memory of one thread-block
+// cluster, many iterations per launch.
+bool onchip_fits(int N, int D, int* cluster_out, int* per_cta_out);
+cudaError_t launch_onchip(const SwarmDev& s, int fid, int iters, cudaStream_t st);
+
+}  // namespace cupso

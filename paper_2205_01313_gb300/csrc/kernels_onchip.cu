@@ -1,0 +1,324 @@
+// kernels_onchip.cu -- whole swarm resident in one thread-block cluster.
+//
+// For swarms whose state fits in the shared memory of a cluster (up to 16
+// CTAs on GB300), the whole run of many iterations is one launch: x, v,
+// pbest_pos and pbest_fit stay in shared memory (Sec. 4.3 keeps the hot data
+// on chip), and the only exchange per iteration is the global best. Each CTA
+// pushes its candidate -- the lowest improved key below the current gbest,
+// with that particle's position (Sec. 4.3: index first, position after) --
+// into a slot of every CTA of the cluster through distributed shared memory,
+// then one cluster barrier replaces the paper's kernel boundary (Sec. 2.2).
+// Every CTA then reduces the same slots in the same order, so all hold the
+// same gbest. The arithmetic is that of the streaming kernels: bit-identical
+// synchronous PSO.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "cupso_device.cuh"
+#include "cupso_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace cupso {
+
+namespace {
+
+constexpr int kOnchipThreads = 256;
+constexpr int kMaxCluster = 16;
+
+struct OnchipLayout {
+    int P;            // particles per CTA (Np / cluster)
+    int C;            // CTAs in the cluster
+    size_t o_x, o_v, o_pb, o_aux, o_pf, o_fit, o_imp, o_G, o_slots, bytes;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+__host__ __device__ inline OnchipLayout onchip_layout(int Np, int D, int C) {
+    OnchipLayout L;
+    L.C = C;
+    L.P = Np / C;
+    const size_t plane = sizeof(float) * (size_t)L.P * (size_t)D;
+    size_t o = 0;
+    L.o_x = o; o = al16(o + plane);
+    L.o_v = o; o = al16(o + plane);
+    L.o_pb = o; o = al16(o + plane);
+    L.o_aux = o; o = al16(o + plane);                 // cos2pi(x') where the fitness needs it
+    L.o_pf = o; o = al16(o + sizeof(float) * L.P);
+    L.o_fit = o; o = al16(o + sizeof(float) * L.P);
+    L.o_imp = o; o = al16(o + sizeof(int) * L.P);
+    L.o_G = o; o = al16(o + sizeof(float) * D);
+    // slots[2][C]: 8-byte key then D floats, padded to 16 bytes
+    L.o_slots = o;
+    const size_t slot = al16(8 + sizeof(float) * (size_t)D);
+    o = al16(o + 2 * (size_t)C * slot);
+    L.bytes = o;
+    return L;
+}
+
+__device__ __forceinline__ size_t slot_bytes(int D) { return al16(8 + sizeof(float) * (size_t)D); }
+
+template <int FIT>
+__global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_constant__ SwarmDev s, int iters) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const int D = s.D;
+    const OnchipLayout L = onchip_layout(s.Np, D, C);
+    const int P = L.P;
+    float* x = reinterpret_cast<float*>(smem + L.o_x);     // [D][P]
+    float* v = reinterpret_cast<float*>(smem + L.o_v);
+    float* pb = reinterpret_cast<float*>(smem + L.o_pb);
+    float* caux = reinterpret_cast<float*>(smem + L.o_aux);
+    float* pf = reinterpret_cast<float*>(smem + L.o_pf);
+    float* fit = reinterpret_cast<float*>(smem + L.o_fit);
+    int* imp = reinterpret_cast<int*>(smem + L.o_imp);
+    float* G = reinterpret_cast<float*>(smem + L.o_G);
+    unsigned char* slots = smem + L.o_slots;
+    const size_t sb = slot_bytes(D);
+    __shared__ unsigned long long red[kOnchipThreads / 32];
+    __shared__ unsigned long long s_K;
+
+    const uint32_t base = (uint32_t)rank * (uint32_t)P;   // first particle of this CTA
+    const size_t Np = (size_t)s.Np;
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const int cur0 = (int)(t_prev & 1u);
+
+    // Load the CTA's particles, gbest and its key.
+    for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
+        const int d = e / P, p = e - d * P;
+        const size_t g = (size_t)d * Np + base + p;
+        x[e] = s.x[g];
+        v[e] = s.v[g];
+        pb[e] = s.pb[g];
+    }
+    for (int p = threadIdx.x; p < P; p += blockDim.x) pf[p] = s.pf[base + p];
+    for (int d = threadIdx.x; d < D; d += blockDim.x) G[d] = s.G[(size_t)cur0 * D + d];
+    if (threadIdx.x == 0) s_K = s.gkey[cur0];
+    __syncthreads();
+
+    const int npairs = (D + 1) / 2;
+    bool nan = false;
+    for (int k = 0; k < iters; ++k) {
+        const uint32_t t = t_prev + 1u + (uint32_t)k;
+        const unsigned long long K = s_K;
+        // Steps 2 (Eq. 1, Eq. 2): one Philox call per (particle, dimension pair).
+        for (int e = threadIdx.x; e < P * npairs; e += blockDim.x) {
+            const int g2 = e / P, p = e - g2 * P;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)g2, base + (uint32_t)p, t, s.swarm), s.key0, s.key1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int d = 2 * g2 + h;
+                if (d >= D) break;
+                const int idx = d * P + p;
+                const float r1 = u01(h == 0 ? r.x : r.z);
+                const float r2 = u01(h == 0 ? r.y : r.w);
+                float xx = x[idx], vv = v[idx];
+                const float cognitive = __fsub_rn(pb[idx], xx);
+                const float social = __fsub_rn(G[d], xx);
+                float vel = __fmul_rn(s.w, vv);
+                vel = __fmaf_rn(__fmul_rn(s.c1, r1), cognitive, vel);
+                vel = __fmaf_rn(__fmul_rn(s.c2, r2), social, vel);
+                vv = clampf(vel, -s.vmax, s.vmax);
+                xx = clampf(__fadd_rn(xx, vv), s.lo, s.hi);
+                x[idx] = xx;
+                v[idx] = vv;
+                if constexpr (FitAcc<FIT>::kNeedsCos) caux[idx] = cos2pi(xx);
+            }
+        }
+        __syncthreads();
+        // Step 3: fitness, sequential over d per particle.
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            FitAcc<FIT> acc;
+            for (int d = 0; d < D; ++d) acc.add_c(d, x[d * P + p], FitAcc<FIT>::kNeedsCos ? caux[d * P + p] : 0.0f);
+            fit[p] = acc.finish(D);
+        }
+        __syncthreads();
+        // Step 4 (strict improvement) and the CTA's Step-5 candidate.
+        unsigned long long cand = kKeyNone;
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const uint32_t i = base + (uint32_t)p;
+            const float f = fit[p];
+            int up = 0;
+            if (i < (uint32_t)s.N) {
+                nan |= (f != f);
+                if (f < pf[p]) {
+                    pf[p] = f;
+                    up = 1;
+                    const unsigned long long kk = pack_key(f, i);
+                    if (kk < K && kk < cand) cand = kk;
+                }
+            }
+            imp[p] = up;
+        }
+        cand = warp_min_u64(cand);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cand;
+        __syncthreads();
+        for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
+            const int p = e % P;
+            if (imp[p]) pb[e] = x[e];
+        }
+        if (threadIdx.x < 32) {
+            unsigned long long c2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : kKeyNone;
+            c2 = warp_min_u64(c2);
+            if (threadIdx.x == 0) red[0] = c2;
+        }
+        __syncthreads();
+        cand = red[0];
+        // Push the candidate into slot [k & 1][rank] of every CTA of the cluster.
+        const int par = k & 1;
+        const size_t my_slot = ((size_t)par * C + rank) * sb;
+        if (threadIdx.x < C) {
+            unsigned char* remote = cluster.map_shared_rank(slots, threadIdx.x);
+            *reinterpret_cast<unsigned long long*>(remote + my_slot) = cand;
+        }
+        if (cand != kKeyNone) {
+            const int pc = (int)((uint32_t)(cand & 0xFFFFFFFFull) - base);
+            for (int e = threadIdx.x; e < C * D; e += blockDim.x) {
+                const int r = e / D, d = e - r * D;
+                unsigned char* remote = cluster.map_shared_rank(slots, r);
+                reinterpret_cast<float*>(remote + my_slot + 8)[d] = x[d * P + pc];
+            }
+        }
+        cluster.sync();
+        // Step 5: every CTA reduces the same slots in rank order.
+        unsigned long long best = K;
+        int win = -1;
+        for (int r = 0; r < C; ++r) {
+            const unsigned long long kk = *reinterpret_cast<const unsigned long long*>(slots + ((size_t)par * C + r) * sb);
+            if (kk < best) {
+                best = kk;
+                win = r;
+            }
+        }
+        if (win >= 0) {
+            const float* row = reinterpret_cast<const float*>(slots + ((size_t)par * C + win) * sb + 8);
+            for (int d = threadIdx.x; d < D; d += blockDim.x) G[d] = row[d];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_K = best;
+        __syncthreads();
+    }
+
+    // Write the state back so that every other mode and the host see it.
+    for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
+        const int d = e / P, p = e - d * P;
+        const size_t g = (size_t)d * Np + base + p;
+        s.x[g] = x[e];
+        s.v[g] = v[e];
+        s.pb[g] = pb[e];
+    }
+    for (int p = threadIdx.x; p < P; p += blockDim.x) s.pf[base + p] = pf[p];
+    if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
+    if (rank == 0) {
+        const uint32_t t_end = t_prev + (uint32_t)iters;
+        const int cur = (int)(t_end & 1u);
+        for (int d = threadIdx.x; d < D; d += blockDim.x) s.G[(size_t)cur * D + d] = G[d];
+        if (threadIdx.x == 0) {
+            s.gkey[0] = s_K;
+            s.gkey[1] = s_K;
+            *s.t_dev = t_end;
+        }
+    }
+    // No CTA may leave while others can still read its shared memory.
+    cluster.sync();
+}
+
+int max_optin_smem() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+// The cluster can be scheduled: the device reports room for at least one.
+bool cluster_schedulable(int C, size_t smem) {
+    auto kernel = onchip_kernel<kSphere>;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return false;
+    if (C > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(kOnchipThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+}  // namespace
+
+bool onchip_fits(int N, int D, int* cluster_out, int* per_cta_out) {
+    const int Np = (N + kPad - 1) / kPad * kPad;
+    const int limit = max_optin_smem() - 2048;   // room for the static shared arrays
+    if (limit <= 0) return false;
+    // Smallest cluster that fits, then grow towards ~64 particles per CTA for
+    // parallelism; shrink again if the device cannot schedule that cluster.
+    int C = 0;
+    for (int c = 1; c <= kMaxCluster; c *= 2) {
+        if (Np % c) break;
+        if (onchip_layout(Np, D, c).bytes <= (size_t)limit) { C = c; break; }
+    }
+    if (C == 0) return false;
+    const int C_min = C;
+    while (C < kMaxCluster && Np / (2 * C) >= 64 && Np % (2 * C) == 0) C *= 2;
+    while (C >= C_min && !cluster_schedulable(C, onchip_layout(Np, D, C).bytes)) C /= 2;
+    if (C < C_min) return false;
+    if (cluster_out) *cluster_out = C;
+    if (per_cta_out) *per_cta_out = Np / C;
+    return true;
+}
+
+namespace {
+template <int FIT>
+cudaError_t launch_onchip_t(const SwarmDev& s, int iters, cudaStream_t st) {
+    int C = 0, P = 0;
+    if (!onchip_fits(s.N, s.D, &C, &P)) return cudaErrorInvalidConfiguration;
+    const OnchipLayout L = onchip_layout(s.Np, s.D, C);
+    auto kernel = onchip_kernel<FIT>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(kOnchipThreads, 1, 1);
+    cfg.dynamicSmemBytes = L.bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, s, iters);
+}
+}  // namespace
+
+cudaError_t launch_onchip(const SwarmDev& s, int fid, int iters, cudaStream_t st) {
+    switch (fid) {
+        case kSphere: return launch_onchip_t<kSphere>(s, iters, st);
+        case kRastrigin: return launch_onchip_t<kRastrigin>(s, iters, st);
+        case kAckley: return launch_onchip_t<kAckley>(s, iters, st);
+        case kRosenbrock: return launch_onchip_t<kRosenbrock>(s, iters, st);
+        case kCubicMax: return launch_onchip_t<kCubicMax>(s, iters, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace cupso

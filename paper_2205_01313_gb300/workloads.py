@@ -1,0 +1,49 @@
+"""Seeded synthetic workloads (parameters only; no PSO arithmetic here).
+
+The paper uses no dataset: its fitness functions are analytic (Sec. 5.1,
+Eq. 3). These are the five generated workloads this project measures; the
+bounds and velocity limits follow the standard ranges of each test function,
+with max_v = 0.1 (max_pos - min_pos) where no value is given. Both the
+library's tests/benchmarks and the oracle read them from here.
+"""
+import numpy as np
+
+W_STD, C_STD = 0.729, 1.49445   # inertia / acceleration constants used by every workload
+
+BOUNDS = {
+    0: (-100.0, 100.0, 20.0),        # sphere
+    1: (-5.12, 5.12, 1.024),         # Rastrigin
+    2: (-32.768, 32.768, 6.5536),    # Ackley
+    3: (-30.0, 30.0, 6.0),           # Rosenbrock
+    4: (-100.0, 100.0, 20.0),        # the paper's cubic, Eq. 3
+}
+
+# name: (fitness_id, N, D, iterations, seed)
+CONFIGS = {
+    "sphere_1024x32": (0, 1024, 32, 1000, 1),
+    "rastrigin_65536x128": (1, 65536, 128, 2000, 1),
+    "rosenbrock_1048576x64": (3, 1 << 20, 64, 1000, 1),
+}
+
+FITNESS_NAMES = {0: "sphere", 1: "rastrigin", 2: "ackley", 3: "rosenbrock", 4: "cubic_max"}
+
+
+def config(name):
+    fid, N, D, T, seed = CONFIGS[name]
+    lo, hi, vmax = BOUNDS[fid]
+    return {"name": name, "fitness_id": fid, "N": N, "D": D, "iters": T, "seed": seed,
+            "bounds": (lo, hi, vmax), "w": W_STD, "c1": C_STD, "c2": C_STD}
+
+
+def batch_problems(n_swarms=512, seed=1, n_range=(64, 8192), d_range=(8, 256)):
+    """Independent swarms of uneven size: N ~ U{64..8192}, D ~ U{8..256},
+    fitness cycling sphere / Rastrigin / Ackley / Rosenbrock, seed_s = s + 1."""
+    rng = np.random.default_rng(seed)
+    Ns = rng.integers(n_range[0], n_range[1] + 1, n_swarms)
+    Ds = rng.integers(d_range[0], d_range[1] + 1, n_swarms)
+    out = []
+    for s in range(n_swarms):
+        fid = s % 4
+        out.append({"D": int(Ds[s]), "N": int(Ns[s]), "bounds": BOUNDS[fid], "w": W_STD, "c1": C_STD,
+                    "c2": C_STD, "fitness_id": fid, "seed": s + 1, "swarm_id": s})
+    return out

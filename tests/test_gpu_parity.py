@@ -1,0 +1,199 @@
+"""Synchronous path vs the oracle, element by element (bit-exact).
+
+Sizes span several 1024-particle tiles with a ragged tail (N = 3000 -> 3 tiles,
+padded to 3072) and odd D (the last Philox call serves a single dimension).
+Every synchronous mode -- fused atomic (SYNC), tree baseline (TREE and its
+unrolled form), on-chip cluster (ONCHIP) -- must give the oracle's trajectory.
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, oracle_swarm, same_bits, ulp_distance
+
+pytestmark = pytest.mark.gpu
+
+SYNC_MODES = ["sync", "tree", "tree_unrolled", "onchip"]
+
+
+@pytest.fixture(scope="module")
+def P():
+    return load_cupso()
+
+
+def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
+    s = P.Swarm(D, N, bounds or BOUNDS[fid], w, c1, c2, fid, seed)
+    s.set_mode(mode)
+    return s
+
+
+@pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])
+@pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
+def test_init_bit_exact(P, fid, N, D):
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 11) as s:
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 11).init()
+    assert rc == P.CUPSO_OK
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+    assert st["t"] == 0
+
+
+@pytest.mark.parametrize("mode", SYNC_MODES)
+@pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
+def test_trajectory_bit_exact(P, fid, mode):
+    N, D, T = 3000, 7, 40
+    with gpu_swarm(P, fid, N, D, 3, mode) as s:
+        s.step(1)
+        s.step(16)     # one captured graph (chunk 16)
+        s.step(23)     # graph + remainder
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 3).init().step_sync(T)
+    assert rc == P.CUPSO_OK and st["t"] == T
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx, (idx, ref.gbest_idx)
+    assert same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("mode", SYNC_MODES)
+def test_single_step_from_shared_state(P, mode):
+    """One step from a state the oracle provides (not one either side reached
+    by itself): positions, velocities and pbests drawn at random."""
+    rng = np.random.default_rng(5)
+    fid, N, D = 3, 2500, 9
+    lo, hi, vmax = BOUNDS[fid]
+    pos = rng.uniform(lo, hi, (N, D)).astype(np.float32)
+    v = rng.uniform(-vmax, vmax, (N, D)).astype(np.float32)
+    pb = rng.uniform(lo, hi, (N, D)).astype(np.float32)
+    ref = oracle_swarm(fid, N, D, 8)
+    from oracle import oracle as O
+    pf = np.array([O.fitness(fid, pb[i]) for i in range(N)], np.float32)
+    ref.set_state(pos, v, pb, pf, 41)
+    with gpu_swarm(P, fid, N, D, 8, mode) as s:
+        s.set_state(pos, v, pb, pf, 41)
+        rc, fit0, idx0, _ = s.gbest()
+        assert idx0 == ref.gbest_idx and same_bits(fit0, ref.gbest_fit)
+        s.step(1)
+        st = s.state()
+        rc, fit, idx, gpos = s.gbest()
+    ref.step_sync(1)
+    for name in ("pos", "v", "pbest_pos", "pbest_fit"):
+        assert ulp_distance(st[name], getattr(ref, name)).max() <= 2, name
+    assert_state_equal(st, ref)       # the bar is 2 ulp; the arithmetic is identical, so 0
+    assert idx == ref.gbest_idx and st["t"] == 42
+
+
+def test_modes_interchangeable_mid_run(P):
+    fid, N, D = 1, 2048, 12
+    with gpu_swarm(P, fid, N, D, 21, "sync") as s:
+        s.step(7)
+        s.set_mode("tree")
+        s.step(5)
+        s.set_mode("onchip")
+        s.step(9)
+        s.set_mode("tree_unrolled")
+        s.step(3)
+        s.set_mode("sync")
+        s.step(2)
+        st = s.state()
+        _, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 21).init().step_sync(26)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("grid", [1, 2, 5])
+@pytest.mark.parametrize("chunk", [0, 4])
+def test_launch_shape_does_not_change_results(P, grid, chunk):
+    fid, N, D, T = 2, 5000, 6, 12
+    with gpu_swarm(P, fid, N, D, 4, "sync") as s:
+        s.set_option(P.CUPSO_OPT_GRID, grid)
+        s.set_option(P.CUPSO_OPT_GRAPH_CHUNK, chunk)
+        s.step(T)
+        st = s.state()
+    ref = oracle_swarm(fid, N, D, 4).init().step_sync(T)
+    assert_state_equal(st, ref)
+
+
+def test_checkpoint_resume_bit_exact(P):
+    fid, N, D = 3, 1500, 10
+    with gpu_swarm(P, fid, N, D, 6, "sync") as a:
+        a.step(10)
+        ck = a.state()
+        a.step(10)
+        full = a.state()
+    with gpu_swarm(P, fid, N, D, 6, "tree") as b:     # a fresh handle, another mode
+        b.set_state(ck["pos"], ck["v"], ck["pbest_pos"], ck["pbest_fit"], ck["t"])
+        b.step(10)
+        resumed = b.state()
+    for k in ("pos", "v", "pbest_pos", "pbest_fit"):
+        assert same_bits(resumed[k], full[k]), k
+    assert resumed["t"] == 20
+
+
+def test_gbest_ties_go_to_lowest_index(P):
+    fid, N, D = 0, 300, 2
+    pos = np.zeros((N, D), np.float32)
+    pos[:, 0] = 1.0
+    pf = np.full(N, 1.0, np.float32)
+    pf[[17, 5, 250]] = 0.25
+    pf[[9]] = -0.0
+    pf[[4]] = 0.0
+    with gpu_swarm(P, fid, N, D, 1, "sync") as s:
+        s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+        _, fit, idx, _ = s.gbest()
+    assert idx == 4 and fit == 0.0
+
+
+def test_nan_fitness_sets_status(P):
+    fid, N, D = 0, 256, 4
+    rng = np.random.default_rng(2)
+    pos = rng.uniform(-1, 1, (N, D)).astype(np.float32)
+    pos[77, 2] = np.nan
+    pf = np.full(N, np.inf, np.float32)
+    with gpu_swarm(P, fid, N, D, 1, "sync") as s:
+        s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+        s.step(1)
+        rc, fit, idx, _ = s.gbest()
+        assert rc == P.CUPSO_ERR_NAN
+        assert idx != 77
+        s.set_option(P.CUPSO_OPT_CLEAR_STATUS, 1)
+        rc, _, _, _ = s.gbest()
+        assert rc == P.CUPSO_OK
+
+
+def test_solve_batch_matches_single_swarms(P):
+    probs = []
+    for k, (fid, N, D) in enumerate([(0, 70, 8), (1, 1500, 13), (2, 333, 4), (3, 2100, 9), (4, 64, 1)]):
+        probs.append(dict(D=D, N=N, bounds=BOUNDS[fid], w=W, c1=C12, c2=C12, fitness_id=fid, seed=k + 1,
+                          swarm_id=k))
+    rc, res = P.cupso_solve_batch(probs, 30)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"]).init().step_sync(30)
+        assert res[k]["status"] == P.CUPSO_OK
+        assert res[k]["idx"] == ref.gbest_idx
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos)
+
+
+def test_onchip_selected_for_small_swarm(P):
+    with P.Swarm(32, 1024, BOUNDS[0], W, C12, C12, 0, 1) as s:
+        info = s.info()
+        assert info["mode"] == P.CUPSO_MODE_ONCHIP and info["onchip_cluster"] >= 2
+    with P.Swarm(64, 1 << 16, BOUNDS[3], W, C12, C12, 3, 1) as s:
+        assert s.info()["mode"] == P.CUPSO_MODE_SYNC
+        with pytest.raises(P.CupsoError):
+            s.set_mode("onchip")
+
+
+def test_sphere_1024x32_full_run_bit_exact(P):
+    """The 1024-particle, 32-dimension, 1000-iteration sphere workload in full."""
+    with P.Swarm(32, 1024, BOUNDS[0], W, C12, C12, 0, 1) as s:
+        s.step(1000)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(0, 1024, 32, 1).init().step_sync(1000)
+    assert rc == P.CUPSO_OK
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and float(fit) < 1e-4

@@ -23,6 +23,9 @@ CONFIGS = {
     "sphere_1024x32": (0, 1024, 32, 1000, 1),
     "rastrigin_65536x128": (1, 65536, 128, 2000, 1),
     "rosenbrock_1048576x64": (3, 1 << 20, 64, 1000, 1),
+    # a quarter of the swarm above (201 MB of state, still larger than L2): the
+    # case the detailed profiler captures run on
+    "rosenbrock_262144x64": (3, 1 << 18, 64, 1000, 1),
 }
 
 FITNESS_NAMES = {0: "sphere", 1: "rastrigin", 2: "ackley", 3: "rosenbrock", 4: "cubic_max"}

@@ -31,7 +31,10 @@ def checker(tmp_path_factory):
 def test_device_philox_equals_curand_and_oracle(checker):
     rng = np.random.default_rng(0)
     ctr = rng.integers(0, 2 ** 32, (4096, 4), dtype=np.uint64).astype(np.uint32)
-    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [5, 17, 3, 0], [1, 2, 0xFFFFFFFF, 7]]
+    # cuRAND reaches counter (c0, c1) through a 64-bit offset of 4 (c0 + 2^32 c1) words,
+    # so c1 must stay below 2^30 (the library's c1 is a particle index).
+    ctr[:, 1] &= 0x3FFFFFFF
+    ctr[:4] = [[0, 0, 0, 0], [0xFFFFFFFF, 0x3FFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF], [5, 17, 3, 0], [1, 2, 0xFFFFFFFF, 7]]
     for key in [(1, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0x89ABCDEF, 0x01234567)]:
         own = np.zeros_like(ctr)
         ref = np.zeros_like(ctr)

@@ -179,6 +179,49 @@ typedef struct {
 CUPSO_API int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters,
                       cupso_result* results, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free iteration. The paper has no counterpart: this entry point
+ * serves callers that must not allocate device memory themselves -- typically
+ * a process whose GPU memory belongs to another allocator (a serving
+ * framework's caching pool, or a budget an embedding application enforces),
+ * where a private cudaMalloc would escape that allocator's accounting or fail
+ * against its reservation. The caller keeps the swarm in its own device
+ * buffers; this call allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine).
+ *
+ * Computes iteration t (t >= 1) of synchronous PSO -- Steps 2-5 with the
+ * tree-reduction aggregation, i.e. what cupso_step gives in CUPSO_MODE_TREE
+ * for the same seed and swarm_id -- in place on:
+ *   pos, v, pbest_pos : device, [D][ld] floats (element d*ld + i), 16-byte aligned
+ *   pbest_fit         : device, [ld] floats, 16-byte aligned
+ *   ld                : row stride, a multiple of 128, >= N; columns N..ld-1
+ *                       are moved too but never win the global best
+ *   gbest_pos         : device, [D]: in = gbest after iteration t-1, out = after t
+ *   gbest_fit, gbest_idx, status_out : device, one element each, or NULL;
+ *                       status_out receives the device status bits (1 = NaN fitness)
+ * Work is queued on `cuda_stream` (a cudaStream_t, NULL = legacy default
+ * stream); the call does not wait.
+ *
+ * Working storage: a fixed device array of about 41 KB inside the library
+ * (static, one per GPU that loads the library, held until the process exits)
+ * holds the per-block keys, the double-buffered gbest position, the iteration
+ * counter and the status word. Limits: N <= CUPSO_NOALLOC_MAX_N and D <=
+ * CUPSO_NOALLOC_MAX_D; larger sizes return CUPSO_ERR_INVALID_ARG with a
+ * message in cupso_last_error(). The first call on each device looks up that
+ * array's device address (with the device current); make that first call
+ * before any stream capture. Every call on a device shares the one array and
+ * clears the counters it needs at its start: calls that overlap on the GPU
+ * (several streams, several host threads) race and give wrong results, so
+ * serialise them.
+ * ------------------------------------------------------------------------- */
+#define CUPSO_NOALLOC_MAX_N 4194304
+#define CUPSO_NOALLOC_MAX_D 1024
+CUPSO_API int cupso_tree_step_noalloc(int D, int N, const cupso_bounds* bounds, float w, float c1, float c2,
+                                      int fitness_id, uint64_t seed, uint32_t swarm_id, uint32_t t,
+                                      float* pos, float* v, float* pbest_pos, float* pbest_fit, int ld,
+                                      float* gbest_pos, float* gbest_fit, int64_t* gbest_idx,
+                                      unsigned int* status_out, void* cuda_stream);
+
 /* Wait for the handle's work and free everything it holds. NULL is a no-op. */
 CUPSO_API int cupso_destroy(cupso_handle h);
 

@@ -15,7 +15,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libcupso.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["cupso_api.cu", "kernels_stream.cu", "kernels_onchip.cu"]
+SOURCES = ["cupso_api.cu", "kernels_stream.cu", "kernels_onchip.cu", "cupso_noalloc.cu"]
 HEADERS = ["cupso_device.cuh", "cupso_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -43,6 +43,8 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+void cupso::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 struct cupso_swarm {
     SwarmDev dev{};
     int N = 0, D = 0, Np = 0, fid = 0;

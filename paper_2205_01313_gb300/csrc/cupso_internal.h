@@ -30,6 +30,9 @@ cudaError_t launch_recompute(const SwarmDev& s, uint32_t t, cudaStream_t st);
 int sync_blocks_per_sm(int fid, int D);
 int async_blocks_per_sm(int fid, int D);
 
+// Record an error message for cupso_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 // On-chip variant: whole swarm in the shared memory of one thread-block
 // cluster, many iterations per launch.
 bool onchip_fits(int N, int D, int* cluster_out, int* per_cta_out);

@@ -37,7 +37,10 @@ CUPSO_OPT_FAULT_HOLD_LOCK = 100
 # The names the library must export (every function of include/cupso.h).
 ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_step", "cupso_get_gbest",
                  "cupso_get_state", "cupso_set_state", "cupso_get_info", "cupso_solve_batch", "cupso_destroy",
-                 "cupso_status_string", "cupso_last_error")
+                 "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc")
+
+CUPSO_NOALLOC_MAX_N = 4194304
+CUPSO_NOALLOC_MAX_D = 1024
 
 
 class cupso_bounds(C.Structure):
@@ -83,6 +86,10 @@ def _load():
     L.cupso_get_info.argtypes = [h, C.POINTER(cupso_info)]
     L.cupso_solve_batch.argtypes = [C.c_int, C.POINTER(cupso_problem), C.c_int, C.POINTER(cupso_result),
                                     C.c_void_p]
+    L.cupso_tree_step_noalloc.argtypes = [C.c_int, C.c_int, C.POINTER(cupso_bounds), C.c_float, C.c_float,
+                                          C.c_float, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p, C.c_void_p]
     L.cupso_destroy.argtypes = [h]
     L.cupso_status_string.argtypes = [C.c_int]
     L.cupso_status_string.restype = C.c_char_p
@@ -200,6 +207,18 @@ def cupso_solve_batch(problems, iters, cuda_stream=None, want_pos=True):
     out = [{"fit": np.float32(R[k].fit), "idx": int(R[k].idx), "pos": keep[k], "status": int(R[k].status)}
            for k in range(n)]
     return rc, out
+
+
+def cupso_tree_step_noalloc(D, N, bounds, w, c1, c2, fitness_id, seed, swarm_id, t, pos, v, pbest_pos, pbest_fit,
+                            ld, gbest_pos, gbest_fit=0, gbest_idx=0, status_out=0, cuda_stream=0):
+    """One iteration on caller-owned device buffers; every buffer argument is a
+    device address (int), e.g. torch.Tensor.data_ptr(). Allocates nothing."""
+    b = _bounds(bounds)
+    _check(_lib.cupso_tree_step_noalloc(int(D), int(N), C.byref(b), float(w), float(c1), float(c2),
+                                        int(fitness_id), int(seed) & 0xFFFFFFFFFFFFFFFF, int(swarm_id), int(t),
+                                        pos, v, pbest_pos, pbest_fit, int(ld), gbest_pos, gbest_fit or None,
+                                        gbest_idx or None, status_out or None, cuda_stream or None),
+           "cupso_tree_step_noalloc")
 
 
 def cupso_destroy(h):

@@ -33,7 +33,8 @@ METRIC = "particle·dim updates/s per fused iter vs HBM roofline; batched & BF16
 UNIT = "particle-dim updates/s"
 DEFAULT_WORKLOAD = "rosenbrock_1048576x64"
 FALLBACK_HBM_GBS = 6800.0
-KERNEL_SOURCES = ["paper_2205_01313_gb300/csrc/kernels_stream.cu", "paper_2205_01313_gb300/csrc/cupso_device.cuh"]
+KERNEL_SOURCES = ["paper_2205_01313_gb300/csrc/kernels_stream.cu", "paper_2205_01313_gb300/csrc/kernels_pipelined.cu",
+                  "paper_2205_01313_gb300/csrc/stream_common.cuh", "paper_2205_01313_gb300/csrc/cupso_device.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_sync_step_kernel.json")
 
 
@@ -45,6 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.CONFIGS))
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
+    ap.add_argument("--sync-kernel", default="auto", choices=["auto", "register", "pipelined3", "pipelined4"])
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -189,7 +191,12 @@ def run_ours(a):
     sw = P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], fid, cfg["seed"] + rank,
                  mode=a.mode, stream=stream.cuda_stream)
     sw.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)   # one kernel per step: events bracket that launch
-    mode_used = {v: k for k, v in P.MODES.items()}[sw.info()["mode"]]
+    sw.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[a.sync_kernel])
+    info = sw.info()
+    mode_used = {v: k for k, v in P.MODES.items()}[info["mode"]]
+    if mode_used == "sync":
+        mode_used = "sync (%s kernel)" % ("pipelined, %d-stage ring" % info["sync_stages"]
+                                          if info["sync_stages"] else "register")
 
     for _ in range(a.warmup):
         sw.step(1)
@@ -240,6 +247,7 @@ def run_ours(a):
                    "mode": mode_used, "step": "one PSO iteration over the whole swarm",
                    "l2": "inputs larger than L2 (%.0f MB swarm state vs 129 MB L2), no flush"
                          % (3 * 4 * N * D / 1e6),
+                   "grid": info["sync_grid"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 4 + 8 + 4 * D + 4,
@@ -247,7 +255,8 @@ def run_ours(a):
         "gpu_launches": K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(a.workload),
-                     "kernel": "sync_step_kernel", "algorithmic_bytes_per_launch": bpl,
+                     "kernel": "sync_pipelined_kernel" if info["sync_stages"] else "sync_step_kernel",
+                     "algorithmic_bytes_per_launch": bpl,
                      "launch_ms": per_launch_ms, "peak_source": peak_src},
         "clocks": clk,
         "result": {"gbest_fit": float(fit), "gbest_idx": idx, "status": rc},

@@ -92,9 +92,18 @@ typedef enum {
     CUPSO_OPT_WAIT_LIMIT_NS = 3,  /* bound of every device-side wait (default 2e9 ns)          */
     CUPSO_OPT_CLEAR_STATUS = 4,   /* any value: clear the sticky device status                 */
     CUPSO_OPT_GRID = 5,           /* CTAs of the persistent kernels (SYNC/ASYNC); 0 = automatic */
+    CUPSO_OPT_SYNC_KERNEL = 6,    /* value: cupso_sync_kernel (which SYNC kernel runs)         */
     CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
                                        lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
 } cupso_option;
+
+/* The two implementations of the SYNC step; both compute the same bits. */
+typedef enum {
+    CUPSO_SYNC_KERNEL_AUTO = 0,       /* pipelined where supported, else register          */
+    CUPSO_SYNC_KERNEL_REGISTER = 1,   /* loads straight into registers, 1024-particle tiles */
+    CUPSO_SYNC_KERNEL_PIPELINED3 = 2, /* rows staged through shared memory, 2 pairs ahead   */
+    CUPSO_SYNC_KERNEL_PIPELINED4 = 3  /* the same, 3 pairs ahead                            */
+} cupso_sync_kernel;
 
 typedef struct {
     int N, D;             /* particles, dimensions                   */
@@ -104,6 +113,7 @@ typedef struct {
     int sync_grid;        /* CTAs of the persistent SYNC launch      */
     int async_grid;       /* CTAs of the ASYNC launch                */
     int onchip_cluster;   /* CTAs per cluster if ONCHIP fits, else 0 */
+    int sync_stages;      /* ring depth of the SYNC kernel in use, 0 = register kernel */
     uint64_t device_bytes;/* device memory held by the handle        */
 } cupso_info;
 

@@ -64,6 +64,8 @@ struct cupso_swarm {
     int hold_lock = 0;
     int grid_override = 0;
     int onchip_cluster = 0;
+    int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
+    bool pipelined_ok = false;      // shared-memory limit raised for the pipelined kernels
 };
 
 namespace {
@@ -73,7 +75,28 @@ int resolved_mode(const cupso_swarm* h) {
     return h->onchip_cluster > 0 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
 }
 
+// Ring depth of the pipelined SYNC kernel, or 0 for the register kernel.
+int sync_stages(const cupso_swarm* h) {
+    int want = 0;
+    switch (h->sync_kernel) {
+        case CUPSO_SYNC_KERNEL_REGISTER: return 0;
+        case CUPSO_SYNC_KERNEL_PIPELINED3: want = 3; break;
+        case CUPSO_SYNC_KERNEL_PIPELINED4: want = 4; break;
+        default: want = 3; break;
+    }
+    return (h->pipelined_ok && pipelined_supported(want, h->D)) ? want : 0;
+}
+
 int sync_grid(const cupso_swarm* h) {
+    const int stages = sync_stages(h);
+    if (stages) {
+        // persistent: warps pull 128-particle units from a counter
+        const int units = h->Np / 128;
+        const int per_sm = pipelined_blocks_per_sm(stages, h->fid, h->D);
+        int g = h->grid_override > 0 ? h->grid_override : h->num_sms * per_sm;
+        const int useful = (units + kBlock / 32 - 1) / (kBlock / 32);
+        return g < useful ? g : useful;
+    }
     const int ntiles = tiles_of(h->Np);
     int g = h->grid_override > 0 ? h->grid_override : h->num_sms * sync_blocks_per_sm(h->fid, h->D);
     return g < ntiles ? g : ntiles;
@@ -102,7 +125,11 @@ void drop_graph(cupso_swarm* h) {
 
 cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
     switch (mode) {
-        case CUPSO_MODE_SYNC: return launch_sync_step(h->dev, h->fid, sync_grid(h), st);
+        case CUPSO_MODE_SYNC: {
+            const int stages = sync_stages(h);
+            if (stages) return launch_sync_pipelined(h->dev, h->fid, stages, sync_grid(h), st);
+            return launch_sync_step(h->dev, h->fid, sync_grid(h), st);
+        }
         case CUPSO_MODE_TREE: return launch_tree_step(h->dev, h->fid, false, st);
         case CUPSO_MODE_TREE_UNROLLED: return launch_tree_step(h->dev, h->fid, true, st);
         default: return cudaErrorInvalidValue;
@@ -213,6 +240,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.status = w32 + 2;
     s.lock = w32 + 3;
     s.seq = w32 + 4;
+    s.work = w32 + 5;
     s.N = N;
     s.D = D;
     s.Np = h->Np;
@@ -229,6 +257,8 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
 
     int cl = 0, per = 0;
     h->onchip_cluster = onchip_fits(N, D, &cl, &per) ? cl : 0;
+    h->pipelined_ok = prepare_pipelined(D) == cudaSuccess;
+    cudaGetLastError();
 
     e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(unsigned long long), h->stream);
@@ -305,6 +335,12 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
         case CUPSO_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(CUPSO_ERR_INVALID_ARG, "grid out of range%s");
             h->grid_override = (int)value;
+            drop_graph(h);
+            return CUPSO_OK;
+        case CUPSO_OPT_SYNC_KERNEL:
+            if (value < CUPSO_SYNC_KERNEL_AUTO || value > CUPSO_SYNC_KERNEL_PIPELINED4)
+                return fail(CUPSO_ERR_INVALID_ARG, "unknown sync kernel%s");
+            h->sync_kernel = (int)value;
             drop_graph(h);
             return CUPSO_OK;
         case CUPSO_OPT_FAULT_HOLD_LOCK:
@@ -424,6 +460,7 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     info->sync_grid = sync_grid(h);
     info->async_grid = async_grid(h);
     info->onchip_cluster = h->onchip_cluster;
+    info->sync_stages = sync_stages(h);
     info->device_bytes = (uint64_t)h->arena_bytes;
     return CUPSO_OK;
 }

@@ -28,6 +28,7 @@ struct SwarmDev {
     unsigned int* t_dev;        // iterations completed
     unsigned int* status;       // sticky error bits (kStatus*)
     unsigned long long* aux;    // tree baseline: one key per block of the first kernel
+    unsigned int* work;         // pipelined step: next 128-particle unit to hand out
     // asynchronous variant: lock-protected gbest record read under a sequence lock
     float* Grec;                // [D]
     unsigned long long* claim;  // lowest key claimed so far (atomicMin target)

@@ -26,6 +26,12 @@ cudaError_t launch_async(const SwarmDev& s, int fid, int grid, int block, uint32
                          int hold_lock, cudaStream_t st);
 cudaError_t launch_recompute(const SwarmDev& s, uint32_t t, cudaStream_t st);
 
+// Pipelined fused step (kernels_pipelined.cu): `stages`-deep cp.async ring.
+bool pipelined_supported(int stages, int D);
+cudaError_t prepare_pipelined(int D);   // raise the dynamic shared-memory limit; call outside capture
+int pipelined_blocks_per_sm(int stages, int fid, int D);
+cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int grid, cudaStream_t st);
+
 // Resident CTAs per SM of the persistent kernels (for grid sizing).
 int sync_blocks_per_sm(int fid, int D);
 int async_blocks_per_sm(int fid, int D);

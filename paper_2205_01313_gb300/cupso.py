@@ -32,6 +32,8 @@ CUPSO_OPT_GRAPH_CHUNK = 2
 CUPSO_OPT_WAIT_LIMIT_NS = 3
 CUPSO_OPT_CLEAR_STATUS = 4
 CUPSO_OPT_GRID = 5
+CUPSO_OPT_SYNC_KERNEL = 6
+SYNC_KERNELS = {"auto": 0, "register": 1, "pipelined3": 2, "pipelined4": 3}
 CUPSO_OPT_FAULT_HOLD_LOCK = 100
 
 # The names the library must export (every function of include/cupso.h).
@@ -50,7 +52,7 @@ class cupso_bounds(C.Structure):
 class cupso_info(C.Structure):
     _fields_ = [("N", C.c_int), ("D", C.c_int), ("Np", C.c_int), ("mode", C.c_int), ("t", C.c_uint32),
                 ("sync_grid", C.c_int), ("async_grid", C.c_int), ("onchip_cluster", C.c_int),
-                ("device_bytes", C.c_uint64)]
+                ("sync_stages", C.c_int), ("device_bytes", C.c_uint64)]
 
 
 class cupso_problem(C.Structure):

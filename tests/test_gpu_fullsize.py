@@ -43,12 +43,16 @@ def _check_step(P, s, fid, N, D, seed, samples):
     assert idx == g and same_bits(fit, after["pbest_fit"][g]) and same_bits(pos, after["pbest_pos"][g])
 
 
-@pytest.mark.parametrize("mode", ["sync", "tree"])
+@pytest.mark.parametrize("mode", ["sync", "sync_register", "tree"])
 def test_rosenbrock_2p20_x64_sampled(P, mode):
+    """The benchmark's launch configuration is the default SYNC kernel, one launch per step."""
     fid, N, D, seed = 3, 1 << 20, 64, 1
     rng = np.random.default_rng(1)
     samples = np.concatenate([[0, 1, 1023, 1024, N - 1], rng.integers(0, N, 250)])
-    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed, mode=mode) as s:
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed, mode=mode.split("_")[0]) as s:
+        s.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)
+        if mode == "sync_register":
+            s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["register"])
         s.step(3)
         _check_step(P, s, fid, N, D, seed, samples)
 

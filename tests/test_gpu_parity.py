@@ -12,7 +12,7 @@ from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, ora
 
 pytestmark = pytest.mark.gpu
 
-SYNC_MODES = ["sync", "tree", "tree_unrolled", "onchip"]
+SYNC_MODES = ["sync", "sync_register", "sync_pipelined4", "tree", "tree_unrolled", "onchip"]
 
 
 @pytest.fixture(scope="module")
@@ -21,9 +21,25 @@ def P():
 
 
 def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
+    """mode: a cupso mode name, or sync_<kernel> for a given SYNC kernel."""
     s = P.Swarm(D, N, bounds or BOUNDS[fid], w, c1, c2, fid, seed)
-    s.set_mode(mode)
+    if mode.startswith("sync_"):
+        s.set_mode("sync")
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[mode[5:]])
+    else:
+        s.set_mode(mode)
     return s
+
+
+def test_sync_kernel_selection(P):
+    with gpu_swarm(P, 3, 5000, 7, 1, "sync") as s:
+        assert s.info()["sync_stages"] == 3
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
+        assert s.info()["sync_stages"] == 4
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["register"])
+        assert s.info()["sync_stages"] == 0
+    with gpu_swarm(P, 3, 5000, 2, 1, "sync_pipelined4") as s:   # too few dimension pairs: register kernel
+        assert s.info()["sync_stages"] == 0
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])
@@ -103,11 +119,12 @@ def test_modes_interchangeable_mid_run(P):
     assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 
 
+@pytest.mark.parametrize("kernel", ["sync_register", "sync_pipelined3", "sync_pipelined4"])
 @pytest.mark.parametrize("grid", [1, 2, 5])
 @pytest.mark.parametrize("chunk", [0, 4])
-def test_launch_shape_does_not_change_results(P, grid, chunk):
+def test_launch_shape_does_not_change_results(P, grid, chunk, kernel):
     fid, N, D, T = 2, 5000, 6, 12
-    with gpu_swarm(P, fid, N, D, 4, "sync") as s:
+    with gpu_swarm(P, fid, N, D, 4, kernel) as s:
         s.set_option(P.CUPSO_OPT_GRID, grid)
         s.set_option(P.CUPSO_OPT_GRAPH_CHUNK, chunk)
         s.step(T)

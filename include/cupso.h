@@ -99,7 +99,7 @@ typedef enum {
 
 /* The two implementations of the SYNC step; both compute the same bits. */
 typedef enum {
-    CUPSO_SYNC_KERNEL_AUTO = 0,       /* pipelined where supported, else register          */
+    CUPSO_SYNC_KERNEL_AUTO = 0,       /* deepest pipelined ring supported, else register   */
     CUPSO_SYNC_KERNEL_REGISTER = 1,   /* loads straight into registers, 1024-particle tiles */
     CUPSO_SYNC_KERNEL_PIPELINED3 = 2, /* rows staged through shared memory, 2 pairs ahead   */
     CUPSO_SYNC_KERNEL_PIPELINED4 = 3  /* the same, 3 pairs ahead                            */

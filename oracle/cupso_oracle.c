@@ -15,7 +15,7 @@
  *  - minimisation (the paper maximises its cubic; we minimise -f);
  *  - r1, r2 drawn fresh per (iteration, particle, dimension);
  *  - v0 ~ U(-max_v, max_v], pos0 ~ U(min_pos, max_pos];
- *  - closed clamps written as comparisons (NaN passes through unchanged);
+ *  - closed clamps; a NaN is clamped to the lower bound (IEEE maxNum/minNum);
  *  - synchronous gbest: iteration t uses the gbest at the end of t-1;
  *  - ties: strict "<" for pbest, lowest index among equal pbest_fit for gbest.
  *
@@ -275,8 +275,12 @@ static void take_gbest(const ora_params* p, ora_state* s, int64_t g)
 /* Step 1: initialisation                                                    */
 /* ------------------------------------------------------------------------- */
 
+/* Closed clamp to [lo, hi] (Alg. 1, "keep in range"). A NaN is clamped to the
+ * lower bound, as IEEE-754 maxNum/minNum do (fmin(fmax(a, lo), hi)); written
+ * with comparisons so that no platform's handling of fmax(-0, +0) enters. */
 static float clampf(float a, float lo, float hi)
 {
+    if (isnan(a)) return lo;
     return a < lo ? lo : (a > hi ? hi : a);
 }
 

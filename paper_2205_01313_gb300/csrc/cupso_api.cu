@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -66,6 +67,7 @@ struct cupso_swarm {
     int onchip_cluster = 0;
     int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
     bool pipelined_ok = false;      // shared-memory limit raised for the pipelined kernels
+    bool lazy_pending = false;      // the pipelined step may have left pbest rows unwritten
 };
 
 namespace {
@@ -82,7 +84,10 @@ int sync_stages(const cupso_swarm* h) {
         case CUPSO_SYNC_KERNEL_REGISTER: return 0;
         case CUPSO_SYNC_KERNEL_PIPELINED3: want = 3; break;
         case CUPSO_SYNC_KERNEL_PIPELINED4: want = 4; break;
-        default: want = 3; break;
+        default:  // deepest ring the dimension count allows
+            if (h->pipelined_ok && pipelined_supported(4, h->D)) return 4;
+            want = 3;
+            break;
     }
     return (h->pipelined_ok && pipelined_supported(want, h->D)) ? want : 0;
 }
@@ -134,6 +139,17 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
         case CUPSO_MODE_TREE_UNROLLED: return launch_tree_step(h->dev, h->fid, true, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Before any kernel that reads pbest_pos directly: write back the rows the
+// pipelined step left pending.
+int ensure_materialized(cupso_swarm* h) {
+    if (!h->lazy_pending) return CUPSO_OK;
+    const int grid = std::max(1, std::min(h->num_sms * 8, (h->Np / 4 + kBlock - 1) / kBlock));
+    cudaError_t e = launch_materialize(h->dev, grid, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "materialize launch");
+    h->lazy_pending = false;
+    return CUPSO_OK;
 }
 
 // A graph of `len` iterations. The kernels read the iteration counter from
@@ -217,6 +233,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     const size_t o_G = off; off = align_up(off + sizeof(float) * 2 * (size_t)D, A);
     const size_t o_Grec = off; off = align_up(off + sizeof(float) * (size_t)D, A);
     const size_t o_aux = off; off = align_up(off + sizeof(unsigned long long) * ntiles, A);
+    const size_t o_flag = off; off = align_up(off + (size_t)h->Np, A);
     const size_t o_words = off; off = align_up(off + 128, A);
     h->arena_bytes = off;
     e = cudaMalloc(&h->arena, h->arena_bytes);
@@ -230,6 +247,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.G = reinterpret_cast<float*>(base + o_G);
     s.Grec = reinterpret_cast<float*>(base + o_Grec);
     s.aux = reinterpret_cast<unsigned long long*>(base + o_aux);
+    s.pflag = reinterpret_cast<unsigned char*>(base + o_flag);
     unsigned long long* w64 = reinterpret_cast<unsigned long long*>(base + o_words);
     s.gkey = w64;        // [2]
     s.claim = w64 + 2;
@@ -254,6 +272,13 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.key1 = (uint32_t)(seed >> 32);
     s.swarm = swarm;
     s.wait_limit_ns = 2000000000ll;
+    // c * 2^-24 is exact unless it would be subnormal; check by scaling back.
+    s.c1s = std::ldexp(c1, -24);
+    s.c2s = std::ldexp(c2, -24);
+    s.fast_cr = (std::ldexp(s.c1s, 24) == c1 && std::ldexp(s.c2s, 24) == c2 &&
+                 (c1 == 0.0f || std::fabs(s.c1s) >= FLT_MIN) && (c2 == 0.0f || std::fabs(s.c2s) >= FLT_MIN))
+                    ? 1 : 0;
+    s.fast_clamp = (b->min_pos != 0.0f && b->max_pos != 0.0f) ? 1 : 0;
 
     int cl = 0, per = 0;
     h->onchip_cluster = onchip_fits(N, D, &cl, &per) ? cl : 0;
@@ -261,6 +286,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     cudaGetLastError();
 
     e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.pflag, 0, (size_t)h->Np, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(unsigned long long), h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
     const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
@@ -358,6 +384,11 @@ int cupso_step(cupso_handle h, int iters) {
     if ((uint64_t)h->t_host + (uint64_t)iters > 0xFFFFFFFFull)
         return fail(CUPSO_ERR_INVALID_ARG, "iteration counter would overflow%s");
     const int mode = resolved_mode(h);
+    const bool pipelined = mode == CUPSO_MODE_SYNC && sync_stages(h) > 0;
+    if (!pipelined) {
+        const int rc = ensure_materialized(h);
+        if (rc) return rc;
+    }
     cudaError_t e = cudaSuccess;
     if (mode == CUPSO_MODE_ASYNC) {
         e = launch_async(h->dev, h->fid, async_grid(h), async_block(h), h->t_host + 1u, iters, h->hold_lock,
@@ -383,6 +414,7 @@ int cupso_step(cupso_handle h, int iters) {
             if (e != cudaSuccess) return cuda_fail(e, "step launch");
         }
     }
+    if (pipelined) h->lazy_pending = true;
     h->t_host += (uint32_t)iters;
     return CUPSO_OK;
 }
@@ -413,6 +445,8 @@ int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, floa
     std::vector<float> stage;
     float* outs[3] = {pos, v, pbest_pos};
     const float* srcs[3] = {h->dev.x, h->dev.v, h->dev.pb};
+    const int mrc = ensure_materialized(h);
+    if (mrc) return mrc;
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     for (int a = 0; a < 3; ++a) {
         if (!outs[a]) continue;
@@ -444,6 +478,8 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
     std::vector<float> pf(Np, INFINITY);
     std::memcpy(pf.data(), pbest_fit, sizeof(float) * N);
     CUPSO_CUDA(cudaMemcpy(h->dev.pf, pf.data(), sizeof(float) * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
+    CUPSO_CUDA(cudaMemset(h->dev.pflag, 0, Np), "cudaMemset");
+    h->lazy_pending = false;
     CUPSO_CUDA(launch_recompute(h->dev, t, h->stream), "recompute launch");
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     h->t_host = t;

@@ -29,6 +29,10 @@ struct SwarmDev {
     unsigned int* status;       // sticky error bits (kStatus*)
     unsigned long long* aux;    // tree baseline: one key per block of the first kernel
     unsigned int* work;         // pipelined step: next 128-particle unit to hand out
+    // Lazy pbest (pipelined step): byte i is 1 when particle i improved in the
+    // last iteration and its pbest_pos row has not been written yet; its
+    // pbest_pos is then its pos. NULL or all-zero means pb is complete.
+    unsigned char* pflag;       // [Np]
     // asynchronous variant: lock-protected gbest record read under a sequence lock
     float* Grec;                // [D]
     unsigned long long* claim;  // lowest key claimed so far (atomicMin target)
@@ -39,6 +43,11 @@ struct SwarmDev {
     float lo, hi, vmax, w, c1, c2;
     uint32_t key0, key1, swarm;
     long long wait_limit_ns;    // bound of every device-side wait
+    // c1 * 2^-24 and c2 * 2^-24 (exact): c * r with r = (k + 1) 2^-24 is then
+    // fma(cs, k, cs), one rounding of the same product. Valid when fast_cr.
+    float c1s, c2s;
+    int fast_cr;                // c1s, c2s exact (normal or zero)
+    int fast_clamp;             // no bound is +-0: clampf_minmax == clampf
 };
 
 constexpr unsigned int kStatusNaN = 1u;
@@ -200,9 +209,17 @@ __device__ __forceinline__ unsigned long long pack_key(float f, uint32_t i) {
     return ((unsigned long long)fit_key(f) << 32) | (unsigned long long)i;
 }
 
-// Closed clamp written as comparisons: a NaN passes through unchanged.
+// Closed clamp to [lo, hi]; a NaN goes to the lower bound (IEEE maxNum).
+// Written with comparisons, valid for any bounds.
 __device__ __forceinline__ float clampf(float a, float lo, float hi) {
+    if (a != a) return lo;
     return a < lo ? lo : (a > hi ? hi : a);
+}
+
+// The same clamp as two min/max instructions. Equal to clampf for every a
+// when neither bound is +-0 (then no signed-zero tie can reach fmaxf/fminf).
+__device__ __forceinline__ float clampf_minmax(float a, float lo, float hi) {
+    return fminf(fmaxf(a, lo), hi);
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long k) {

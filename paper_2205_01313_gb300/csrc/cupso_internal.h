@@ -31,6 +31,8 @@ bool pipelined_supported(int stages, int D);
 cudaError_t prepare_pipelined(int D);   // raise the dynamic shared-memory limit; call outside capture
 int pipelined_blocks_per_sm(int stages, int fid, int D);
 cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int grid, cudaStream_t st);
+// Write back the pbest rows the pipelined step left pending (lazy pbest) and clear the flags.
+cudaError_t launch_materialize(const SwarmDev& s, int grid, cudaStream_t st);
 
 // Resident CTAs per SM of the persistent kernels (for grid sizing).
 int sync_blocks_per_sm(int fid, int D);

@@ -65,10 +65,24 @@ __device__ __forceinline__ void issue_step(const SwarmDev& s, float4* my, uint32
 
 }  // namespace
 
+// Lazy pbest: when particle i improves at iteration t its new pbest_pos is its
+// new pos, which this kernel has just written to pos; instead of copying it to
+// pbest_pos at once (a re-read of D values long evicted from L2), the kernel
+// sets flag i. At iteration t+1 the flagged particle's pbest_pos is the pos it
+// reads anyway: it uses that value (pbest - pos = 0 exactly, as with an
+// explicit copy) and writes the pbest_pos row from it with full 16-byte
+// stores. The arithmetic is unchanged; only when pbest_pos is stored differs.
+__device__ __forceinline__ uint32_t flag_bit(uint32_t fl, int j) { return (fl >> (8 * j)) & 1u; }
+
+__device__ __forceinline__ uint32_t load_flags(const SwarmDev& s, uint32_t i0) {
+    return __ldcg(reinterpret_cast<const unsigned int*>(s.pflag + i0));
+}
+
 // Requires (D + 1) / 2 >= STAGES - 1 (the host falls back to the register
-// kernel otherwise) and Np a multiple of 128.
-template <int FIT, int STAGES>
-__global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_constant__ SwarmDev s) {
+// kernel otherwise), Np a multiple of 128 and s.pflag set.
+// FAST selects move_one_fast (requires s.fast_cr and s.fast_clamp).
+template <int FIT, int STAGES, bool FAST>
+__global__ void __launch_bounds__(kBlock, 3) sync_pipelined_kernel(const __grid_constant__ SwarmDev s) {
     extern __shared__ float4 ring[];  // [STAGES][6][kBlock] float4, then gbest_pos [D]
     float* Gs = reinterpret_cast<float*>(ring + STAGES * 6 * kBlock);
     const uint32_t t_prev = __ldcg(s.t_dev);
@@ -85,7 +99,8 @@ __global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_con
     float4* my = ring + threadIdx.x;
 
     uint32_t u_cur = fetch_unit(s, lane_id);
-    uint32_t u_nxt = 0xFFFFFFFFu;
+    uint32_t fl_cur = u_cur < nunits ? load_flags(s, u_cur * kUnit + (uint32_t)lane_id * 4) : 0u;
+    uint32_t u_nxt = 0xFFFFFFFFu, fl_nxt = 0u;
 #pragma unroll
     for (int j = 0; j < STAGES - 1; ++j) issue_step<STAGES>(s, my, u_cur, j, j, nunits, lane_id);
     int ig = STAGES - 1;  // pair of the next issue, counted from the current unit
@@ -96,6 +111,7 @@ __global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_con
     while (u_cur < nunits) {
         const uint32_t i0 = u_cur * kUnit + (uint32_t)lane_id * 4;
         FitAcc<FIT> acc[4];
+        float4 PF = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int g = 0; g < npairs; ++g) {
             // keep STAGES-1 pairs in flight: issue the pair STAGES-1 ahead
             {
@@ -104,11 +120,15 @@ __global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_con
                 if (ig < npairs) {
                     issue_step<STAGES>(s, my, u_cur, ig, ws, nunits, lane_id);
                 } else {
-                    if (u_nxt == 0xFFFFFFFFu) u_nxt = fetch_unit(s, lane_id);
+                    if (u_nxt == 0xFFFFFFFFu) {
+                        u_nxt = fetch_unit(s, lane_id);
+                        if (u_nxt < nunits) fl_nxt = load_flags(s, u_nxt * kUnit + (uint32_t)lane_id * 4);
+                    }
                     issue_step<STAGES>(s, my, u_nxt, ig - npairs, ws, nunits, lane_id);
                 }
                 ++ig;
             }
+            if (g == npairs - 1) PF = ld4(s.pf + i0);  // needed after the last pair
             cp_wait<STAGES - 1>();  // this thread's copies of the current pair have landed
             const uint4 rr[4] = {
                 philox4x32_10(make_uint4((uint32_t)g, i0 + 0, t, s.swarm), s.key0, s.key1),
@@ -121,37 +141,53 @@ __global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_con
                 if (h == 1 && d >= D) break;
                 float4 X = my[(stage * 6 + 0 + h) * kBlock];
                 float4 V = my[(stage * 6 + 2 + h) * kBlock];
-                const float4 P = my[(stage * 6 + 4 + h) * kBlock];
+                float4 P = my[(stage * 6 + 4 + h) * kBlock];
+                const size_t off = (size_t)d * Np + i0;
+                if (fl_cur) {
+                    // pbest_pos of a flagged particle is its pos: use it and write it back
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (flag_bit(fl_cur, j)) set_lane(P, j, lane(X, j));
+                    st4(s.pb + off, P);
+                }
                 const float gd = Gs[d];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     float xj = lane(X, j), vj = lane(V, j);
-                    move_one(xj, vj, lane(P, j), gd, u01(word(rr[j], 2 * h)), u01(word(rr[j], 2 * h + 1)), s);
+                    if constexpr (FAST)
+                        move_one_fast(xj, vj, lane(P, j), gd, hi24(word(rr[j], 2 * h)), hi24(word(rr[j], 2 * h + 1)),
+                                      s);
+                    else
+                        move_one(xj, vj, lane(P, j), gd, u01(word(rr[j], 2 * h)), u01(word(rr[j], 2 * h + 1)), s);
                     set_lane(X, j, xj);
                     set_lane(V, j, vj);
                     acc[j].add(d, xj);
                 }
-                const size_t off = (size_t)d * Np + i0;
                 st4(s.x + off, X);
                 st4(s.v + off, V);
             }
             if (++stage == STAGES) stage = 0;
         }
-        // Steps 4 and 5 for the unit's particles.
-        float f[4], pf[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) f[j] = acc[j].finish(D);
-        const unsigned mask = pbest4(s, i0, f, pf);
+        // Step 4 (strict improvement; the new pbest_pos is pos, flagged) and Step 5.
+        uint32_t fl_new = 0u;
+        float f[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (mask & (1u << j)) {
+            f[j] = acc[j].finish(D);
+            if ((i0 + j) < (uint32_t)s.N && f[j] < lane(PF, j)) {
+                fl_new |= 1u << (8 * j);
+                set_lane(PF, j, f[j]);
                 const unsigned long long k = pack_key(f[j], i0 + j);
                 if (k < K && k < best) best = k;
             }
         }
+        if (fl_new) st4(s.pf + i0, PF);
+        if (fl_new != fl_cur) *reinterpret_cast<unsigned int*>(s.pflag + i0) = fl_new;
         nan |= any_nan4(s, i0, f);
         u_cur = u_nxt;
+        fl_cur = fl_nxt;
         u_nxt = 0xFFFFFFFFu;
+        fl_nxt = 0u;
         ig -= npairs;
     }
     cp_wait<0>();
@@ -161,6 +197,28 @@ __global__ void __launch_bounds__(kBlock) sync_pipelined_kernel(const __grid_con
     finish_iteration(s, cur, nxt, t);
 }
 
+// Writes back every pending pbest_pos row (pbest_pos := pos where flagged) and
+// clears the flags, so that kernels without lazy pbest see a complete pb.
+__global__ void __launch_bounds__(kBlock) materialize_kernel(const __grid_constant__ SwarmDev s) {
+    const uint32_t ngroups = (uint32_t)s.Np / 4;
+    const size_t Np = (size_t)s.Np;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < ngroups; q += gridDim.x * blockDim.x) {
+        unsigned int* fw = reinterpret_cast<unsigned int*>(s.pflag) + q;
+        const uint32_t fl = *fw;
+        if (!fl) continue;
+        for (int d = 0; d < s.D; ++d) {
+            const size_t off = (size_t)d * Np + 4 * (size_t)q;
+            const float4 X = ld4(s.x + off);
+            float4 P = ld4(s.pb + off);
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (flag_bit(fl, j)) set_lane(P, j, lane(X, j));
+            st4(s.pb + off, P);
+        }
+        *fw = 0u;
+    }
+}
+
 namespace {
 
 template <int STAGES>
@@ -168,40 +226,25 @@ size_t pipelined_smem(int D) {
     return sizeof(float4) * (size_t)STAGES * 6 * kBlock + sizeof(float) * (size_t)D;
 }
 
-template <int STAGES>
-cudaError_t launch_pipelined_t(const SwarmDev& s, int fid, int grid, cudaStream_t st) {
-    const size_t smem = pipelined_smem<STAGES>(s.D);
+// The kernel instance for (fitness, ring depth, fast path).
+template <int STAGES, bool FAST>
+const void* kernel_of_t(int fid) {
     switch (fid) {
-        case kSphere: sync_pipelined_kernel<kSphere, STAGES><<<grid, kBlock, smem, st>>>(s); break;
-        case kRastrigin: sync_pipelined_kernel<kRastrigin, STAGES><<<grid, kBlock, smem, st>>>(s); break;
-        case kAckley: sync_pipelined_kernel<kAckley, STAGES><<<grid, kBlock, smem, st>>>(s); break;
-        case kRosenbrock: sync_pipelined_kernel<kRosenbrock, STAGES><<<grid, kBlock, smem, st>>>(s); break;
-        case kCubicMax: sync_pipelined_kernel<kCubicMax, STAGES><<<grid, kBlock, smem, st>>>(s); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <int STAGES, typename F>
-cudaError_t for_each_fit(F f) {
-    cudaError_t e = f(sync_pipelined_kernel<kSphere, STAGES>);
-    if (e == cudaSuccess) e = f(sync_pipelined_kernel<kRastrigin, STAGES>);
-    if (e == cudaSuccess) e = f(sync_pipelined_kernel<kAckley, STAGES>);
-    if (e == cudaSuccess) e = f(sync_pipelined_kernel<kRosenbrock, STAGES>);
-    if (e == cudaSuccess) e = f(sync_pipelined_kernel<kCubicMax, STAGES>);
-    return e;
-}
-
-template <int STAGES>
-void* kernel_of(int fid) {
-    switch (fid) {
-        case kSphere: return (void*)sync_pipelined_kernel<kSphere, STAGES>;
-        case kRastrigin: return (void*)sync_pipelined_kernel<kRastrigin, STAGES>;
-        case kAckley: return (void*)sync_pipelined_kernel<kAckley, STAGES>;
-        case kRosenbrock: return (void*)sync_pipelined_kernel<kRosenbrock, STAGES>;
-        default: return (void*)sync_pipelined_kernel<kCubicMax, STAGES>;
+        case kSphere: return (const void*)sync_pipelined_kernel<kSphere, STAGES, FAST>;
+        case kRastrigin: return (const void*)sync_pipelined_kernel<kRastrigin, STAGES, FAST>;
+        case kAckley: return (const void*)sync_pipelined_kernel<kAckley, STAGES, FAST>;
+        case kRosenbrock: return (const void*)sync_pipelined_kernel<kRosenbrock, STAGES, FAST>;
+        case kCubicMax: return (const void*)sync_pipelined_kernel<kCubicMax, STAGES, FAST>;
+        default: return nullptr;
     }
 }
+
+const void* kernel_of(int stages, bool fast, int fid) {
+    if (stages == 3) return fast ? kernel_of_t<3, true>(fid) : kernel_of_t<3, false>(fid);
+    return fast ? kernel_of_t<4, true>(fid) : kernel_of_t<4, false>(fid);
+}
+
+size_t smem_of(int stages, int D) { return stages == 3 ? pipelined_smem<3>(D) : pipelined_smem<4>(D); }
 
 }  // namespace
 
@@ -210,26 +253,36 @@ bool pipelined_supported(int stages, int D) {
 }
 
 cudaError_t prepare_pipelined(int D) {
-    cudaError_t e = for_each_fit<3>([&](auto k) {
-        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipelined_smem<3>(D));
-    });
-    if (e != cudaSuccess) return e;
-    return for_each_fit<4>([&](auto k) {
-        return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipelined_smem<4>(D));
-    });
+    for (int stages = 3; stages <= 4; ++stages)
+        for (int fast = 0; fast < 2; ++fast)
+            for (int fid = kSphere; fid <= kCubicMax; ++fid) {
+                cudaError_t e = cudaFuncSetAttribute(kernel_of(stages, fast != 0, fid),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_of(stages, D));
+                if (e != cudaSuccess) return e;
+            }
+    return cudaSuccess;
 }
 
 int pipelined_blocks_per_sm(int stages, int fid, int D) {
     int n = 0;
-    const void* k = stages == 3 ? kernel_of<3>(fid) : kernel_of<4>(fid);
-    const size_t smem = stages == 3 ? pipelined_smem<3>(D) : pipelined_smem<4>(D);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBlock, smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel_of(stages, true, fid), kBlock,
+                                                      smem_of(stages, D)) != cudaSuccess)
+        return 1;
     return n > 0 ? n : 1;
 }
 
+cudaError_t launch_materialize(const SwarmDev& s, int grid, cudaStream_t st) {
+    if (!s.pflag) return cudaSuccess;
+    materialize_kernel<<<grid, kBlock, 0, st>>>(s);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int grid, cudaStream_t st) {
-    if (!pipelined_supported(stages, s.D)) return cudaErrorInvalidValue;
-    return stages == 3 ? launch_pipelined_t<3>(s, fid, grid, st) : launch_pipelined_t<4>(s, fid, grid, st);
+    if (!pipelined_supported(stages, s.D) || !s.pflag) return cudaErrorInvalidValue;
+    const void* k = kernel_of(stages, s.fast_cr && s.fast_clamp, fid);
+    if (!k) return cudaErrorInvalidValue;
+    void* args[] = {const_cast<SwarmDev*>(&s)};
+    return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, smem_of(stages, s.D), st);
 }
 
 }  // namespace cupso

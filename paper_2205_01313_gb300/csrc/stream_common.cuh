@@ -33,6 +33,22 @@ __device__ __forceinline__ void move_one(float& x, float& v, float pb, float g, 
     x = clampf(__fadd_rn(x, v), s.lo, s.hi);
 }
 
+// The same update on the fast path: c * r as fma(cs, k, cs) with
+// k = float(w >> 8) (the identical rounded product), clamps as min/max.
+// Bit-identical to move_one when s.fast_cr and s.fast_clamp hold.
+__device__ __forceinline__ void move_one_fast(float& x, float& v, float pb, float g, float k1, float k2,
+                                              const SwarmDev& s) {
+    const float cognitive = __fsub_rn(pb, x);
+    const float social = __fsub_rn(g, x);
+    float vel = __fmul_rn(s.w, v);
+    vel = __fmaf_rn(__fmaf_rn(s.c1s, k1, s.c1s), cognitive, vel);
+    vel = __fmaf_rn(__fmaf_rn(s.c2s, k2, s.c2s), social, vel);
+    v = clampf_minmax(vel, -s.vmax, s.vmax);
+    x = clampf_minmax(__fadd_rn(x, v), s.lo, s.hi);
+}
+
+__device__ __forceinline__ float hi24(uint32_t w) { return __uint2float_rn(w >> 8); }
+
 // Steps 2-3 for the particles i0..i0+3 at iteration t: reads x, v, pb, writes
 // x', v', returns the four fitness values. Gs is gbest_pos in shared memory.
 template <int FIT>
@@ -142,8 +158,12 @@ __device__ __forceinline__ void finish_iteration(const SwarmDev& s, int cur, int
     const uint32_t g = (uint32_t)(knew & 0xFFFFFFFFull);
     const size_t Np = (size_t)s.Np;
     if (g < (uint32_t)s.N) {
+        // a particle whose pbest is not yet written back has pbest_pos == pos
+        const bool lazy = s.pflag && ((__ldcg(reinterpret_cast<const unsigned int*>(s.pflag) + (g >> 2)) >>
+                                       (8u * (g & 3u))) & 0xFFu);
+        const float* src = lazy ? s.x : s.pb;
         for (int d = threadIdx.x; d < s.D; d += blockDim.x)
-            s.G[(size_t)nxt * s.D + d] = __ldcg(s.pb + (size_t)d * Np + g);
+            s.G[(size_t)nxt * s.D + d] = __ldcg(src + (size_t)d * Np + g);
     }
     if (threadIdx.x == 0) {
         s.gkey[cur] = knew;

@@ -26,6 +26,9 @@ CONFIGS = {
     # a quarter of the swarm above (201 MB of state, still larger than L2): the
     # case the detailed profiler captures run on
     "rosenbrock_262144x64": (3, 1 << 18, 64, 1000, 1),
+    # the 2^20-particle swarm with half the dimensions (403 MB): same per-warp
+    # work pattern as the 2^20 x 64 swarm at half the size, for detailed captures
+    "rosenbrock_1048576x32": (3, 1 << 20, 32, 1000, 1),
 }
 
 FITNESS_NAMES = {0: "sphere", 1: "rastrigin", 2: "ackley", 3: "rosenbrock", 4: "cubic_max"}

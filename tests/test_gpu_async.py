@@ -94,3 +94,20 @@ def test_async_lock_wait_expires_and_reports(P):
         s2.step(5)
         st = s2.state()
     assert_state_equal(st, oracle_swarm(0, 200, 3, 5).init().step_sync(5))
+
+
+def test_async_after_pipelined_sync_steps(P):
+    """The pipelined SYNC step leaves pbest rows pending (lazy pbest); the next
+    kernel that reads pbest_pos directly must see them written back."""
+    fid, N, D = 3, 3000, 9
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 4, mode="sync") as s:
+        assert s.info()["sync_stages"] > 0
+        s.step(6)
+        s.set_mode("async")
+        s.set_option(P.CUPSO_OPT_GRID, 1)
+        s.step(5)
+        st = s.state()
+        _, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 4).init().step_sync(11)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)

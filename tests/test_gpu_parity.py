@@ -12,7 +12,7 @@ from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, ora
 
 pytestmark = pytest.mark.gpu
 
-SYNC_MODES = ["sync", "sync_register", "sync_pipelined4", "tree", "tree_unrolled", "onchip"]
+SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "tree", "tree_unrolled", "onchip"]
 
 
 @pytest.fixture(scope="module")
@@ -33,11 +33,13 @@ def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
 
 def test_sync_kernel_selection(P):
     with gpu_swarm(P, 3, 5000, 7, 1, "sync") as s:
-        assert s.info()["sync_stages"] == 3
-        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
         assert s.info()["sync_stages"] == 4
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined3"])
+        assert s.info()["sync_stages"] == 3
         s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["register"])
         assert s.info()["sync_stages"] == 0
+    with gpu_swarm(P, 3, 5000, 4, 1, "sync") as s:   # two dimension pairs: only the 3-stage ring
+        assert s.info()["sync_stages"] == 3
     with gpu_swarm(P, 3, 5000, 2, 1, "sync_pipelined4") as s:   # too few dimension pairs: register kernel
         assert s.info()["sync_stages"] == 0
 
@@ -164,20 +166,52 @@ def test_gbest_ties_go_to_lowest_index(P):
 
 
 def test_nan_fitness_sets_status(P):
-    fid, N, D = 0, 256, 4
+    """A NaN fitness (here inf - inf inside the cubic at +-1e30) sets the sticky
+    status; the particle never becomes pbest or gbest."""
+    fid, N, D = 4, 256, 2
+    bounds = (-1e30, 1e30, 1.0)
     rng = np.random.default_rng(2)
     pos = rng.uniform(-1, 1, (N, D)).astype(np.float32)
-    pos[77, 2] = np.nan
-    pf = np.full(N, np.inf, np.float32)
-    with gpu_swarm(P, fid, N, D, 1, "sync") as s:
+    pos[77] = [1e30, -1e30]
+    from oracle import oracle as O
+    pf = np.array([O.fitness(fid, p) for p in pos], np.float32)
+    assert np.isnan(pf[77])
+    with gpu_swarm(P, fid, N, D, 1, "sync", bounds=bounds) as s:
         s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
         s.step(1)
         rc, fit, idx, _ = s.gbest()
+        st = s.state()
         assert rc == P.CUPSO_ERR_NAN
         assert idx != 77
         s.set_option(P.CUPSO_OPT_CLEAR_STATUS, 1)
         rc, _, _, _ = s.gbest()
         assert rc == P.CUPSO_OK
+    ref = oracle_swarm(fid, N, D, 1, bounds=bounds)
+    ref.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+    ref.step_sync(1)
+    assert_state_equal(st, ref)
+
+
+@pytest.mark.parametrize("case", ["zero_lower_bound", "zero_upper_bound", "tiny_c1"])
+@pytest.mark.parametrize("mode", ["sync", "sync_register", "onchip"])
+def test_trajectory_other_arithmetic_paths(P, case, mode):
+    """Bounds at 0 (signed-zero ties possible: the min/max clamp is not used) and
+    c1 so small that c1 * 2^-24 is subnormal (the fused c*r form is not used)."""
+    fid, N, D, T = 0, 2000, 6, 30
+    bounds, c1 = BOUNDS[0], C12
+    if case == "zero_lower_bound":
+        bounds = (0.0, 10.0, 2.0)
+    elif case == "zero_upper_bound":
+        bounds = (-10.0, 0.0, 2.0)
+    else:
+        c1 = 1e-38
+    with gpu_swarm(P, fid, N, D, 5, mode, bounds=bounds, c1=c1) as s:
+        s.step(T)
+        st = s.state()
+        _, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 5, bounds=bounds, c1=c1).init().step_sync(T)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 
 
 def test_solve_batch_matches_single_swarms(P):

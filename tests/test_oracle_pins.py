@@ -316,6 +316,18 @@ def test_frozen_swarm():
     assert s.gbest_idx == g0
 
 
+def test_nan_is_clamped_to_lower_bound():
+    """Clamp reading: a NaN velocity or position goes to the lower bound (IEEE maxNum)."""
+    s = O.Swarm(3, 2, -4, 6, 2, 0.5, 1, 1, O.SPHERE, 1)
+    pos = np.array([[np.nan, 1.0], [0.5, 0.5], [2.0, -1.0]], np.float32)
+    pf = np.array([O.fitness(O.SPHERE, p) for p in pos], np.float32)
+    s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+    s.step_sync(1, np.full((1, 3, 2, 2), 0.5, np.float32))
+    assert s.v[0, 0] == np.float32(-2.0)       # NaN velocity -> -max_v
+    assert s.pos[0, 0] == np.float32(-4.0)     # NaN position -> min_pos
+    assert np.all(np.isfinite(s.pos))
+
+
 def test_gbest_ties_lowest_index():
     N, D = 6, 2
     s = O.Swarm(N, D, -10, 10, 1, 0.5, 1, 1, O.SPHERE, 1)

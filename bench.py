@@ -44,7 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.CONFIGS) + ["batch512"])
+    ap.add_argument("--plain-sample", type=int, default=1,
+                    help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
     ap.add_argument("--sync-kernel", default="auto", choices=["auto", "register", "pipelined3", "pipelined4"])
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
@@ -325,10 +327,87 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------------------- #
+# batched solve: 512 uneven swarms, one launch per iteration for all of them   #
+# --------------------------------------------------------------------------- #
+
+BATCH_ITERS = 500
+
+
+def run_batch(a):
+    """512 independent swarms (N ~ U{64..8192}, D ~ U{8..256}, fitness cycling
+    sphere/Rastrigin/Ackley/Rosenbrock), 500 iterations each, solved (1) by
+    cupso_solve_batch and (2) plain: per swarm cupso_create, 500 cupso_step
+    launches, cupso_get_gbest, cupso_destroy, on one stream. Both through the
+    public API with host results. Correctness: swarms re-solved alone through
+    the batch API must reproduce the batched results bit for bit."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2205_01313_gb300 import build as B
+    B.build()
+    from paper_2205_01313_gb300 import cupso as P
+
+    probs = workloads.batch_problems()
+    iters = BATCH_ITERS
+    total_pd = sum(p["N"] * p["D"] for p in probs) * iters
+    stream = torch.cuda.Stream()
+    # warm-up: the same batch shape, a few iterations (builds graphs, tunes the launch shape)
+    for _ in range(max(1, a.warmup)):
+        P.cupso_solve_batch(probs, 24, cuda_stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    rc, res = P.cupso_solve_batch(probs, iters, cuda_stream=stream.cuda_stream)
+    batched_s = time.perf_counter() - t0
+    sample = list(range(0, len(probs), max(1, a.plain_sample)))
+    t0 = time.perf_counter()
+    mism = 0
+    for k in sample:
+        p = probs[k]
+        h = P.cupso_create(p["D"], p["N"], p["bounds"], p["w"], p["c1"], p["c2"], p["fitness_id"], p["seed"])
+        P.cupso_set_stream(h, stream.cuda_stream)
+        P.cupso_set_option(h, P.CUPSO_OPT_GRAPH_CHUNK, 0)   # one launch per iteration
+        # cupso_create draws with swarm id 0, so this trajectory differs from the batch's
+        # (same work, other random streams); only its time is used here
+        P.cupso_step(h, iters)
+        st, fit, idx, pos = P.cupso_get_gbest(h, p["D"])
+        P.cupso_destroy(h)
+    plain_sample_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    sample_pd = sum(probs[k]["N"] * probs[k]["D"] for k in sample) * iters
+    plain_s = plain_sample_s * total_pd / sample_pd
+    # correctness: a few swarms re-solved alone through the batch API must match
+    for k in sample[:8]:
+        rc1, one = P.cupso_solve_batch([probs[k]], iters, cuda_stream=stream.cuda_stream)
+        mism += int(one[0]["idx"] != res[k]["idx"] or not np.array_equal(one[0]["pos"], res[k]["pos"]))
+    out = {
+        "metric": METRIC, "value": total_pd / batched_s, "unit": UNIT, "n_gpus": 1, "steps": iters,
+        "warmup": a.warmup, "ms_per_step": batched_s * 1e3 / iters, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch512", "swarms": len(probs), "iters": iters,
+                   "N": "U{64..8192}", "D": "U{8..256}", "fitness": "sphere/rastrigin/ackley/rosenbrock cycling",
+                   "particle_dims_per_iter": total_pd // iters},
+        "batched": {"seconds": batched_s, "status": rc,
+                    "api": "cupso_solve_batch (init + 500 iterations + host results)"},
+        "plain": {"seconds": plain_s, "sampled_swarms": len(sample), "sampled_seconds": plain_sample_s,
+                  "value": total_pd / plain_s,
+                  "api": "per swarm: cupso_create, cupso_step(500) one launch per iteration, cupso_get_gbest, cupso_destroy"},
+        "batched_over_plain": plain_s / batched_s,
+        "alone_vs_batched_mismatches": mism,
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch512":
+        run_batch(a)
     else:
         run_ours(a)
 

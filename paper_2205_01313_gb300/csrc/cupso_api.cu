@@ -179,7 +179,9 @@ int ensure_graph(cupso_swarm* h, int mode, int len) {
     return CUPSO_OK;
 }
 
-int check_problem(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid) {
+}  // namespace
+
+int cupso::check_problem_args(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid) {
     if (D < 1 || N < 1) return fail(CUPSO_ERR_INVALID_ARG, "D and N must be >= 1%s");
     if ((long long)N > (long long)0x7FFFFFFF - kPad) return fail(CUPSO_ERR_INVALID_ARG, "N too large%s");
     const long long Np = ((long long)N + kPad - 1) / kPad * kPad;
@@ -195,11 +197,13 @@ int check_problem(int D, int N, const cupso_bounds* b, float w, float c1, float 
     return CUPSO_OK;
 }
 
+namespace {
+
 int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid, uint64_t seed,
                  uint32_t swarm, cudaStream_t user_stream, cupso_handle* out) {
     if (!out) return fail(CUPSO_ERR_INVALID_ARG, "out is NULL%s");
     *out = nullptr;
-    int rc = check_problem(D, N, b, w, c1, c2, fid);
+    int rc = check_problem_args(D, N, b, w, c1, c2, fid);
     if (rc) return rc;
     cupso_swarm* h = new (std::nothrow) cupso_swarm();
     if (!h) return fail(CUPSO_ERR_OOM, "host allocation failed%s");
@@ -321,6 +325,19 @@ float key_to_fit(unsigned long long key) {
 }
 
 }  // namespace
+
+// One problem solved through its own handle: create, `iters` steps, gbest.
+int cupso::solve_one_plain(const cupso_problem& p, int iters, cupso_result& r, cudaStream_t stream) {
+    cupso_handle h = nullptr;
+    int rc = create_swarm(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id, p.seed, p.swarm_id, stream, &h);
+    if (rc == CUPSO_OK) rc = cupso_step(h, iters);
+    if (rc == CUPSO_OK) rc = cupso_get_gbest(h, &r.fit, r.pos, &r.idx);
+    r.status = rc;
+    if (h) cupso_destroy(h);
+    return rc;
+}
+
+void cupso::set_cuda_error(cudaError_t e, const char* where) { cuda_fail(e, where); }
 
 extern "C" {
 
@@ -499,30 +516,6 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     info->sync_stages = sync_stages(h);
     info->device_bytes = (uint64_t)h->arena_bytes;
     return CUPSO_OK;
-}
-
-int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters, cupso_result* results,
-                      void* cuda_stream) {
-    if (n_swarms < 0 || iters < 0) return fail(CUPSO_ERR_INVALID_ARG, "n_swarms and iters must be >= 0%s");
-    if (n_swarms > 0 && (!problems || !results)) return fail(CUPSO_ERR_INVALID_ARG, "NULL problems/results%s");
-    for (int k = 0; k < n_swarms; ++k) {
-        const cupso_problem& p = problems[k];
-        int rc = check_problem(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id);
-        if (rc) return rc;
-    }
-    int first = CUPSO_OK;
-    for (int k = 0; k < n_swarms; ++k) {
-        const cupso_problem& p = problems[k];
-        cupso_handle h = nullptr;
-        int rc = create_swarm(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id, p.seed, p.swarm_id,
-                              static_cast<cudaStream_t>(cuda_stream), &h);
-        if (rc == CUPSO_OK) rc = cupso_step(h, iters);
-        if (rc == CUPSO_OK) rc = cupso_get_gbest(h, &results[k].fit, results[k].pos, &results[k].idx);
-        results[k].status = rc;
-        if (h) cupso_destroy(h);
-        if (rc != CUPSO_OK && first == CUPSO_OK) first = rc;
-    }
-    return first;
 }
 
 int cupso_destroy(cupso_handle h) {

@@ -1,0 +1,364 @@
+// cupso_batch.cu -- cupso_solve_batch: many independent swarms at once.
+//
+// All swarms of a batch live in one device arena. Each is initialised by the
+// ordinary Step-1 kernel, then every iteration is ONE launch of
+// batch_step_kernel covering the units of all swarms (kernels_batch.cu); the
+// `iters` launches are replayed from captured CUDA graphs. The launch shape
+// (ring depth, CTAs per SM) is chosen online: the first iterations of the
+// real run are timed under each candidate shape and the fastest one runs the
+// rest -- every shape computes the same bits, so tuning costs no extra work.
+// Choices are remembered per batch shape for the life of the process.
+//
+// Swarms with fewer than three dimensions (too few dimension pairs for the
+// ring's look-ahead) are solved one by one through their own handles.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/cupso.h"
+#include "cupso_device.cuh"
+#include "cupso_internal.h"
+
+using namespace cupso;
+
+namespace {
+
+size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Shape {
+    int stages;
+    int minb;            // register budget: CTAs per SM
+    int blocks_per_sm;   // CTAs per SM launched
+};
+
+// Launch shapes remembered per batch signature.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, long long, int, int>, Shape> g_tuned;
+
+struct BatchRun {
+    cudaStream_t st = nullptr;
+    BatchDev dev{};
+    int num_sms = 1;
+    cudaGraphExec_t graph = nullptr;
+    Shape graph_shape{0, 0, 0};
+    int graph_len = 0;
+
+    ~BatchRun() {
+        if (graph) cudaGraphExecDestroy(graph);
+    }
+
+    cudaError_t launch(const Shape& sh) {
+        return launch_batch_step(dev, sh.stages, sh.minb, num_sms * sh.blocks_per_sm, st);
+    }
+
+    // `n` iterations with shape `sh`, through a captured graph of up to 32 launches.
+    int run(const Shape& sh, int n) {
+        const int L = std::min(n, 32);
+        if (L >= 4 && (!graph || graph_len != L || graph_shape.stages != sh.stages || graph_shape.minb != sh.minb ||
+                       graph_shape.blocks_per_sm != sh.blocks_per_sm)) {
+            if (graph) cudaGraphExecDestroy(graph);
+            graph = nullptr;
+            cudaStream_t cap = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamCreate"), CUPSO_ERR_CUDA;
+            e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            cudaError_t le = cudaSuccess;
+            for (int k = 0; k < L && e == cudaSuccess && le == cudaSuccess; ++k)
+                le = launch_batch_step(dev, sh.stages, sh.minb, num_sms * sh.blocks_per_sm, cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(cap, &g) : e;
+            cudaStreamDestroy(cap);
+            if (le != cudaSuccess || ee != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                set_cuda_error(le != cudaSuccess ? le : ee, "batch graph capture");
+                return CUPSO_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                graph = nullptr;
+                set_cuda_error(e, "cudaGraphInstantiate");
+                return CUPSO_ERR_CUDA;
+            }
+            graph_len = L;
+            graph_shape = sh;
+        }
+        int left = n;
+        while (graph && left >= graph_len) {
+            cudaError_t e = cudaGraphLaunch(graph, st);
+            if (e != cudaSuccess) return set_cuda_error(e, "cudaGraphLaunch"), CUPSO_ERR_CUDA;
+            left -= graph_len;
+        }
+        for (; left > 0; --left) {
+            cudaError_t e = launch(sh);
+            if (e != cudaSuccess) return set_cuda_error(e, "batch launch"), CUPSO_ERR_CUDA;
+        }
+        return CUPSO_OK;
+    }
+};
+
+float key_fit(unsigned long long key) {
+    const uint32_t k = (uint32_t)(key >> 32);
+    if (k == 0xFFFFFFFFu) return NAN;
+    const uint32_t bits = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    float f;
+    std::memcpy(&f, &bits, 4);
+    return f;
+}
+
+}  // namespace
+
+extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters, cupso_result* results,
+                                 void* cuda_stream) {
+    if (n_swarms < 0 || iters < 0) {
+        set_last_error("n_swarms and iters must be >= 0");
+        return CUPSO_ERR_INVALID_ARG;
+    }
+    if (n_swarms > 0 && (!problems || !results)) {
+        set_last_error("NULL problems/results");
+        return CUPSO_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < n_swarms; ++k) {
+        const cupso_problem& p = problems[k];
+        const int rc = check_problem_args(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id);
+        if (rc) return rc;
+    }
+    if (n_swarms == 0) return CUPSO_OK;
+
+    BatchRun run;
+    cudaStream_t own = nullptr;
+    if (cuda_stream) {
+        run.st = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return set_cuda_error(e, "cudaStreamCreate"), CUPSO_ERR_CUDA;
+        run.st = own;
+    }
+    int first = CUPSO_OK;
+    auto note = [&](int rc) {
+        if (rc != CUPSO_OK && first == CUPSO_OK) first = rc;
+    };
+
+    std::vector<int> batched;
+    for (int k = 0; k < n_swarms; ++k) {
+        if (problems[k].D >= 3) {
+            batched.push_back(k);
+        } else {
+            note(solve_one_plain(problems[k], iters, results[k], run.st));
+        }
+    }
+    const int nb = (int)batched.size();
+    void* arena = nullptr;
+    int rc = CUPSO_OK;
+    do {
+        if (nb == 0) break;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&run.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = prepare_batch();
+        if (e != cudaSuccess) { set_cuda_error(e, "batch setup"); rc = CUPSO_ERR_CUDA; break; }
+
+        // Arena: per-swarm planes, then gbest positions, keys, words, flags, descriptors, units, counters.
+        const size_t A = 256;
+        std::vector<size_t> o_state(nb), o_G(nb), o_flag(nb);
+        std::vector<int> Np(nb);
+        size_t off = 0, total_units = 0, sumG = 0, sumFlag = 0;
+        int minD = 1 << 30, maxD = 0;
+        long long total_pd = 0;
+        for (int j = 0; j < nb; ++j) {
+            const cupso_problem& p = problems[batched[j]];
+            Np[j] = (p.N + kPad - 1) / kPad * kPad;
+            o_state[j] = off;
+            off = up(off + sizeof(float) * ((size_t)3 * p.D * Np[j] + Np[j]), A);
+            o_G[j] = sumG;
+            sumG += 2 * (size_t)p.D;
+            o_flag[j] = sumFlag;
+            sumFlag += (size_t)Np[j];
+            total_units += (size_t)Np[j] / 128;
+            minD = std::min(minD, p.D);
+            maxD = std::max(maxD, p.D);
+            total_pd += (long long)p.N * p.D;
+        }
+        const size_t o_Gall = off; off = up(off + sizeof(float) * sumG, A);
+        const size_t o_keys = off; off = up(off + sizeof(unsigned long long) * 2 * nb, A);
+        const size_t o_words = off; off = up(off + sizeof(unsigned int) * 4 * nb, A);
+        const size_t o_flags = off; off = up(off + sumFlag, A);
+        const size_t o_desc = off; off = up(off + sizeof(BatchSwarm) * nb, A);
+        const size_t o_units = off; off = up(off + sizeof(uint2) * total_units, A);
+        const size_t o_ctr = off; off = up(off + 64, A);
+        e = cudaMalloc(&arena, off);
+        if (e != cudaSuccess) { set_cuda_error(e, "cudaMalloc (batch arena)"); rc = e == cudaErrorMemoryAllocation ? CUPSO_ERR_OOM : CUPSO_ERR_CUDA; break; }
+        char* base = static_cast<char*>(arena);
+        float* Gall = reinterpret_cast<float*>(base + o_Gall);
+        unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + o_keys);
+        unsigned int* words = reinterpret_cast<unsigned int*>(base + o_words);   // done, status, ticket, t
+        unsigned char* flags = reinterpret_cast<unsigned char*>(base + o_flags);
+        unsigned int* ctr = reinterpret_cast<unsigned int*>(base + o_ctr);       // work[2], ticket, t
+        e = cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * 2 * nb, run.st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + o_words, 0, o_desc - o_words, run.st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64, run.st);
+        if (e != cudaSuccess) { set_cuda_error(e, "cudaMemsetAsync"); rc = CUPSO_ERR_CUDA; break; }
+
+        // Step 1 of every swarm, and its descriptor.
+        std::vector<BatchSwarm> desc(nb);
+        for (int j = 0; j < nb && rc == CUPSO_OK; ++j) {
+            const cupso_problem& p = problems[batched[j]];
+            float* st = reinterpret_cast<float*>(base + o_state[j]);
+            const size_t plane = (size_t)p.D * Np[j];
+            SwarmDev s{};
+            s.x = st;
+            s.v = st + plane;
+            s.pb = st + 2 * plane;
+            s.pf = st + 3 * plane;
+            s.G = Gall + o_G[j];
+            s.gkey = keys + 2 * j;
+            s.status = words + 4 * j + 1;
+            s.ticket = words + 4 * j + 2;
+            s.t_dev = words + 4 * j + 3;
+            s.N = p.N;
+            s.D = p.D;
+            s.Np = Np[j];
+            s.lo = p.bounds.min_pos;
+            s.hi = p.bounds.max_pos;
+            s.vmax = p.bounds.max_v;
+            s.w = p.w;
+            s.c1 = p.c1;
+            s.c2 = p.c2;
+            s.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+            s.key1 = (uint32_t)(p.seed >> 32);
+            s.swarm = p.swarm_id;
+            e = launch_init(s, p.fitness_id, std::min(tiles_of(Np[j]), run.num_sms * 4), run.st);
+            if (e != cudaSuccess) { set_cuda_error(e, "batch init launch"); rc = CUPSO_ERR_CUDA; break; }
+            BatchSwarm& w = desc[j];
+            w.x = s.x; w.v = s.v; w.pb = s.pb; w.pf = s.pf;
+            w.pflag = flags + o_flag[j];
+            w.G = s.G;
+            w.gkey = s.gkey;
+            w.done = words + 4 * j + 0;
+            w.status = s.status;
+            w.N = p.N; w.D = p.D; w.Np = Np[j]; w.fid = p.fitness_id;
+            w.nunits = (unsigned)(Np[j] / 128);
+            w.lo = s.lo; w.hi = s.hi; w.vmax = s.vmax; w.w = p.w; w.c1 = p.c1; w.c2 = p.c2;
+            w.c1s = std::ldexp(p.c1, -24);
+            w.c2s = std::ldexp(p.c2, -24);
+            const bool fast_cr = std::ldexp(w.c1s, 24) == p.c1 && std::ldexp(w.c2s, 24) == p.c2 &&
+                                 (p.c1 == 0.0f || std::fabs(w.c1s) >= FLT_MIN) &&
+                                 (p.c2 == 0.0f || std::fabs(w.c2s) >= FLT_MIN);
+            w.fast = fast_cr && p.bounds.min_pos != 0.0f && p.bounds.max_pos != 0.0f;
+            w.key0 = s.key0; w.key1 = s.key1; w.swarm = p.swarm_id;
+        }
+        if (rc != CUPSO_OK) break;
+
+        // Hand-out order: the units with the most dimensions first; swarms interleaved.
+        std::vector<uint2> units;
+        units.reserve(total_units);
+        std::vector<int> order(nb);
+        for (int j = 0; j < nb; ++j) order[j] = j;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return desc[a].D > desc[b].D; });
+        for (size_t pos = 0; pos < (size_t)nb;) {
+            size_t endg = pos;
+            while (endg < (size_t)nb && desc[order[endg]].D == desc[order[pos]].D) ++endg;
+            unsigned most = 0;
+            for (size_t q = pos; q < endg; ++q) most = std::max(most, desc[order[q]].nunits);
+            for (unsigned u = 0; u < most; ++u)
+                for (size_t q = pos; q < endg; ++q)
+                    if (u < desc[order[q]].nunits) units.push_back(make_uint2((unsigned)order[q], u));
+            pos = endg;
+        }
+        e = cudaMemcpyAsync(base + o_desc, desc.data(), sizeof(BatchSwarm) * nb, cudaMemcpyHostToDevice, run.st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + o_units, units.data(), sizeof(uint2) * units.size(), cudaMemcpyHostToDevice,
+                                run.st);
+        if (e != cudaSuccess) { set_cuda_error(e, "cudaMemcpyAsync"); rc = CUPSO_ERR_CUDA; break; }
+        run.dev.swarms = reinterpret_cast<const BatchSwarm*>(base + o_desc);
+        run.dev.units = reinterpret_cast<const uint2*>(base + o_units);
+        run.dev.nunits = (unsigned)units.size();
+        run.dev.work = ctr;
+        run.dev.ticket = ctr + 2;
+        run.dev.t_dev = ctr + 3;
+
+        // Launch shapes to try: ring depth 4 needs three dimension pairs everywhere.
+        std::vector<Shape> cand;
+        if ((minD + 1) / 2 >= 3) cand.push_back(Shape{4, 2, batch_blocks_per_sm(4, 2)});
+        cand.push_back(Shape{3, 2, batch_blocks_per_sm(3, 2)});
+        cand.push_back(Shape{3, 3, batch_blocks_per_sm(3, 3)});
+        const auto key = std::make_tuple(nb, total_pd, minD, maxD);
+        Shape best = cand[0];
+        bool known = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mutex);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) { best = it->second; known = true; }
+        }
+        int done_iters = 0;
+        const int probe = 2;
+        if (!known && iters >= (int)cand.size() * probe * 2) {
+            float best_ms = 1e30f;
+            cudaEvent_t ev0, ev1;
+            cudaEventCreate(&ev0);
+            cudaEventCreate(&ev1);
+            for (const Shape& sh : cand) {
+                cudaEventRecord(ev0, run.st);
+                for (int k = 0; k < probe && rc == CUPSO_OK; ++k) {
+                    e = run.launch(sh);
+                    if (e != cudaSuccess) { set_cuda_error(e, "batch launch"); rc = CUPSO_ERR_CUDA; }
+                }
+                cudaEventRecord(ev1, run.st);
+                cudaEventSynchronize(ev1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev0, ev1);
+                if (rc == CUPSO_OK && ms < best_ms) { best_ms = ms; best = sh; }
+                done_iters += probe;
+            }
+            cudaEventDestroy(ev0);
+            cudaEventDestroy(ev1);
+            if (rc == CUPSO_OK) {
+                std::lock_guard<std::mutex> lk(g_tune_mutex);
+                g_tuned[key] = best;
+            }
+        }
+        if (rc != CUPSO_OK) break;
+        rc = run.run(best, iters - done_iters);
+        if (rc != CUPSO_OK) break;
+
+        // Results: gbest key, position and status of every swarm.
+        std::vector<unsigned long long> hkeys(2 * (size_t)nb);
+        std::vector<float> hG(sumG);
+        std::vector<unsigned int> hw(4 * (size_t)nb);
+        e = cudaMemcpyAsync(hkeys.data(), keys, sizeof(unsigned long long) * 2 * nb, cudaMemcpyDeviceToHost, run.st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hG.data(), Gall, sizeof(float) * sumG, cudaMemcpyDeviceToHost, run.st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hw.data(), words, sizeof(unsigned) * 4 * nb, cudaMemcpyDeviceToHost, run.st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(run.st);
+        if (e != cudaSuccess) { set_cuda_error(e, "batch results"); rc = CUPSO_ERR_CUDA; break; }
+        const int cur = iters & 1;
+        for (int j = 0; j < nb; ++j) {
+            cupso_result& r = results[batched[j]];
+            const unsigned long long k = hkeys[2 * j + cur];
+            r.fit = key_fit(k);
+            r.idx = (int64_t)(k & 0xFFFFFFFFull);
+            if (r.pos) std::memcpy(r.pos, hG.data() + o_G[j] + (size_t)cur * desc[j].D, sizeof(float) * desc[j].D);
+            r.status = (hw[4 * j + 1] & kStatusTimeout) ? CUPSO_ERR_DEVICE_TIMEOUT
+                       : (hw[4 * j + 1] & kStatusNaN)   ? CUPSO_ERR_NAN
+                                                        : CUPSO_OK;
+            note(r.status);
+        }
+    } while (false);
+    if (rc != CUPSO_OK) {
+        for (int j = 0; j < nb; ++j) results[batched[j]].status = rc;
+        note(rc);
+    }
+    if (arena) {
+        cudaStreamSynchronize(run.st);
+        cudaFree(arena);
+    }
+    if (own) cudaStreamDestroy(own);
+    return first;
+}

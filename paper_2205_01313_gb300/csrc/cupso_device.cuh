@@ -50,6 +50,31 @@ struct SwarmDev {
     int fast_clamp;             // no bound is +-0: clampf_minmax == clampf
 };
 
+// One swarm of a batch (kernels_batch.cu): its state in the batch arena and
+// its parameters. Same layouts as SwarmDev.
+struct BatchSwarm {
+    float *x, *v, *pb, *pf;
+    unsigned char* pflag;
+    float* G;                   // [2][D]
+    unsigned long long* gkey;   // [2]
+    unsigned int* done;         // units of this swarm finished in the current iteration
+    unsigned int* status;
+    int N, D, Np, fid;
+    unsigned int nunits;        // Np / 128
+    float lo, hi, vmax, w, c1, c2, c1s, c2s;
+    uint32_t key0, key1, swarm;
+    int fast;                   // fast_cr && fast_clamp
+};
+
+struct BatchDev {
+    const BatchSwarm* swarms;
+    const uint2* units;         // (swarm, unit) in hand-out order
+    unsigned int nunits;
+    unsigned int* work;         // [2] unit counters, alternating by iteration parity
+    unsigned int* ticket;
+    unsigned int* t_dev;
+};
+
 constexpr unsigned int kStatusNaN = 1u;
 constexpr unsigned int kStatusTimeout = 2u;
 constexpr unsigned int kStatusBadArg = 4u;

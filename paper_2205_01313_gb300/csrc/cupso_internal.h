@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/cupso.h"
 #include "cupso_device.cuh"
 
 namespace cupso {
@@ -34,12 +35,25 @@ cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int gr
 // Write back the pbest rows the pipelined step left pending (lazy pbest) and clear the flags.
 cudaError_t launch_materialize(const SwarmDev& s, int grid, cudaStream_t st);
 
+// Batched step (kernels_batch.cu): one iteration of every swarm of a batch.
+cudaError_t prepare_batch();
+// Shapes: (stages, minb) in {(3, 2), (3, 3), (4, 2)}; minb = CTAs per SM the
+// register budget is sized for.
+int batch_blocks_per_sm(int stages, int minb);
+cudaError_t launch_batch_step(const BatchDev& b, int stages, int minb, int grid, cudaStream_t st);
+
 // Resident CTAs per SM of the persistent kernels (for grid sizing).
 int sync_blocks_per_sm(int fid, int D);
 int async_blocks_per_sm(int fid, int D);
 
 // Record an error message for cupso_last_error() on the calling thread.
 void set_last_error(const char* msg);
+void set_cuda_error(cudaError_t e, const char* where);
+
+// Host-side argument check of one problem (CUPSO_OK or CUPSO_ERR_INVALID_ARG).
+int check_problem_args(int D, int N, const cupso_bounds* b, float w, float c1, float c2, int fid);
+// Solve one problem through its own handle (create, iters steps, gbest, destroy).
+int solve_one_plain(const cupso_problem& p, int iters, cupso_result& r, cudaStream_t stream);
 
 // On-chip variant: whole swarm in the shared memory of one thread-block
 // cluster, many iterations per launch.

@@ -228,6 +228,42 @@ def test_solve_batch_matches_single_swarms(P):
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos)
 
 
+def _mixed_batch(n, seed, n_range, d_range):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        fid = k % 5
+        out.append(dict(D=int(rng.integers(*d_range)), N=int(rng.integers(*n_range)), bounds=BOUNDS[fid], w=W,
+                        c1=C12, c2=C12, fitness_id=fid, seed=1000 + k, swarm_id=k))
+    return out
+
+
+@pytest.mark.parametrize("iters", [5, 30])
+def test_batched_solve_matches_oracle(P, iters):
+    """Uneven swarms with every fitness function in one batch; 30 iterations run the
+    launch-shape tuner on the real work first. Each swarm must equal its oracle run."""
+    probs = _mixed_batch(24, 7, (64, 2500), (3, 40))
+    probs[3]["D"] = 2              # too few dimension pairs: solved through its own handle
+    probs[5]["D"] = 3              # the smallest batched dimension count
+    rc, res = P.cupso_solve_batch(probs, iters)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"]).init().step_sync(iters)
+        assert res[k]["status"] == P.CUPSO_OK
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
+def test_batched_solve_repeatable(P):
+    """A second identical batch reuses the remembered launch shape; same results."""
+    probs = _mixed_batch(10, 9, (100, 1200), (5, 20))
+    rc1, a = P.cupso_solve_batch(probs, 24)
+    rc2, b = P.cupso_solve_batch(probs, 24)
+    assert rc1 == rc2 == P.CUPSO_OK
+    for x, y in zip(a, b):
+        assert x["idx"] == y["idx"] and same_bits(x["pos"], y["pos"])
+
+
 def test_onchip_selected_for_small_swarm(P):
     with P.Swarm(32, 1024, BOUNDS[0], W, C12, C12, 0, 1) as s:
         info = s.info()

@@ -63,8 +63,16 @@ typedef enum {
     CUPSO_RASTRIGIN = 1,  /* 10 D + sum (x^2 - 10 cos 2 pi x)          */
     CUPSO_ACKLEY = 2,     /* -20 e^{-0.2 sqrt(mean x^2)} - e^{mean cos 2 pi x} + 20 + e */
     CUPSO_ROSENBROCK = 3, /* sum 100 (x_{d+1} - x_d^2)^2 + (1 - x_d)^2 */
-    CUPSO_CUBIC_MAX = 4   /* Eq. 3: maximise sum x^3 - 0.8 x^2 - 1000 x + 8000 */
+    CUPSO_CUBIC_MAX = 4,  /* Eq. 3: maximise sum x^3 - 0.8 x^2 - 1000 x + 8000 */
+    CUPSO_LSQ = 5         /* ||A x - b||^2 with A, b given by cupso_set_lsq */
 } cupso_fitness;
+
+/* Arithmetic of the least-squares fitness. */
+typedef enum {
+    CUPSO_LSQ_FP32 = 0,   /* CUDA cores, fixed FP32 order (bit-exact with the oracle)          */
+    CUPSO_LSQ_BF16 = 1,   /* tensor cores, BF16 operands, FP32 accumulation                    */
+    CUPSO_LSQ_FP8 = 2     /* tensor cores, FP8 e4m3 operands (A scaled per row), FP32 accumulation */
+} cupso_lsq_precision;
 
 typedef enum {
     CUPSO_OK = 0,
@@ -231,6 +239,17 @@ CUPSO_API int cupso_tree_step_noalloc(int D, int N, const cupso_bounds* bounds, 
                                       float* pos, float* v, float* pbest_pos, float* pbest_fit, int ld,
                                       float* gbest_pos, float* gbest_fit, int64_t* gbest_idx,
                                       unsigned int* status_out, void* cuda_stream);
+
+/* Least-squares fitness of N given positions: f_out[i] = ||A x_i - b||^2 with
+ * A device [M][D] row-major, b device [M], X device [N][D] row-major, f_out
+ * device [N], all float32 (caller-owned). precision selects the arithmetic:
+ * FP32 follows a fixed order (per row m, r = -b_m then r = fma(A_md, x_d, r)
+ * for d in order; f = sum over m in order of fma(r, r, .)); BF16 and FP8 form
+ * X A^T on the tensor cores (the fitness of the dense-fitness extension of the
+ * method; the paper's own fitness is analytic, Sec. 5.1). Allocates temporary
+ * device memory, queues on `cuda_stream` and waits. */
+CUPSO_API int cupso_lsq_eval(const float* A_dev, const float* b_dev, int M, int D, const float* X_dev, int N,
+                             int precision, float* f_out_dev, void* cuda_stream);
 
 /* Wait for the handle's work and free everything it holds. NULL is a no-op. */
 CUPSO_API int cupso_destroy(cupso_handle h);

@@ -235,6 +235,37 @@ float ora_fitness(int fitness, const float* x, int D)
     }
 }
 
+/* Least squares ||A x - b||^2 (the dense fitness of the precision study). */
+float ora_lsq_f32(const float* A, const float* b, int M, int D, const float* x)
+{
+    float acc = 0.0f;
+    for (int m = 0; m < M; ++m) {
+        const float* row = A + (size_t)m * D;
+        float r = -b[m];
+        for (int d = 0; d < D; ++d) r = fmaf(row[d], x[d], r);
+        acc = fmaf(r, r, acc);
+    }
+    return acc;
+}
+
+double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x)
+{
+    double acc = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const float* row = A + (size_t)m * D;
+        double r = -(double)b[m];
+        for (int d = 0; d < D; ++d) r += (double)row[d] * (double)x[d];
+        acc += r * r;
+    }
+    return acc;
+}
+
+float ora_fitness_p(const ora_params* p, const float* x)
+{
+    if (p->fitness == ORA_LSQ) return ora_lsq_f32(p->lsq_A, p->lsq_b, p->lsq_M, p->D, x);
+    return ora_fitness(p->fitness, x, p->D);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Ordering of fitness values                                                */
 /* ------------------------------------------------------------------------- */
@@ -288,7 +319,8 @@ static int check_params(const ora_params* p)
 {
     if (p->N <= 0 || p->D <= 0) return -1;
     if (!(p->min_pos < p->max_pos) || !(p->max_v > 0.0f)) return -1;
-    if (p->fitness < ORA_SPHERE || p->fitness > ORA_CUBIC_MAX) return -1;
+    if (p->fitness < ORA_SPHERE || p->fitness > ORA_LSQ) return -1;
+    if (p->fitness == ORA_LSQ && (!p->lsq_A || !p->lsq_b || p->lsq_M <= 0)) return -1;
     return 0;
 }
 
@@ -307,7 +339,7 @@ int ora_init(const ora_params* p, ora_state* s)
             pos[d] = clampf(fmaf(ora_u01(wx), span, p->min_pos), p->min_pos, p->max_pos);
             v[d] = clampf(fmaf(ora_u01(wv), vspan, -p->max_v), -p->max_v, p->max_v);
         }
-        s->fit[i] = ora_fitness(p->fitness, pos, D);
+        s->fit[i] = ora_fitness_p(p, pos);
         s->pbest_fit[i] = s->fit[i];
         memcpy(s->pbest_pos + (size_t)i * D, pos, sizeof(float) * (size_t)D);
     }
@@ -342,7 +374,7 @@ float ora_move_one(const ora_params* p, uint32_t t, int i, float* pos, float* v,
         /* Eq. 2: pos <- pos + v */
         pos[d] = clampf(pos[d] + v[d], p->min_pos, p->max_pos);
     }
-    float fit = ora_fitness(p->fitness, pos, D);             /* Step 3 */
+    float fit = ora_fitness_p(p, pos);                        /* Step 3 */
     if (fit < *pbest_fit) {                                   /* Step 4 */
         *pbest_fit = fit;
         memcpy(pbest, pos, sizeof(float) * (size_t)D);

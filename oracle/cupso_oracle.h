@@ -29,7 +29,8 @@ enum {
     ORA_RASTRIGIN = 1,
     ORA_ACKLEY = 2,
     ORA_ROSENBROCK = 3,
-    ORA_CUBIC_MAX = 4
+    ORA_CUBIC_MAX = 4,
+    ORA_LSQ = 5
 };
 
 typedef struct {
@@ -42,6 +43,10 @@ typedef struct {
     int fitness;    /* ORA_* */
     uint64_t seed;  /* Philox key */
     uint32_t swarm; /* fourth Philox counter word */
+    /* least squares ||A x - b||^2 (ORA_LSQ only): A is [lsq_M][D] row-major */
+    const float* lsq_A;
+    const float* lsq_b;
+    int lsq_M;
 } ora_params;
 
 typedef struct {
@@ -75,6 +80,14 @@ void ora_exp_coeffs(float out[9], float* log2e, float* ln2_hi, float* ln2_lo);
 
 /* Fitness of one position (D contiguous floats); lower is better. */
 float ora_fitness(int fitness, const float* x, int D);
+
+/* Least-squares fitness in FP32 with a fixed order: per m, r = -b_m, then
+ * r = fma(A_md, x_d, r) for d = 0..D-1; acc = fma(r, r, acc) for m = 0..M-1. */
+float ora_lsq_f32(const float* A, const float* b, int M, int D, const float* x);
+/* The same sum in double precision (the FP64 reference of the rescoring). */
+double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x);
+/* Fitness with the swarm's parameters (LSQ needs p->lsq_*). */
+float ora_fitness_p(const ora_params* p, const float* x);
 
 /* Order-preserving 32-bit key of a fitness value (NaN -> 0xFFFFFFFF). */
 uint32_t ora_fit_key(float f);

@@ -12,7 +12,7 @@ import numpy as np
 
 from .build import build_oracle
 
-SPHERE, RASTRIGIN, ACKLEY, ROSENBROCK, CUBIC_MAX = 0, 1, 2, 3, 4
+SPHERE, RASTRIGIN, ACKLEY, ROSENBROCK, CUBIC_MAX, LSQ = 0, 1, 2, 3, 4, 5
 
 _lib = None
 
@@ -21,7 +21,8 @@ class _Params(C.Structure):
     _fields_ = [("N", C.c_int), ("D", C.c_int),
                 ("min_pos", C.c_float), ("max_pos", C.c_float), ("max_v", C.c_float),
                 ("w", C.c_float), ("c1", C.c_float), ("c2", C.c_float),
-                ("fitness", C.c_int), ("seed", C.c_uint64), ("swarm", C.c_uint32)]
+                ("fitness", C.c_int), ("seed", C.c_uint64), ("swarm", C.c_uint32),
+                ("lsq_A", C.c_void_p), ("lsq_b", C.c_void_p), ("lsq_M", C.c_int)]
 
 
 class _State(C.Structure):
@@ -58,6 +59,10 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.ora_move_one.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_int, f32p, f32p, f32p, f32p, f32p, f32p]
         L.ora_move_one.restype = C.c_float
+        L.ora_lsq_f32.argtypes = [f32p, f32p, C.c_int, C.c_int, f32p]
+        L.ora_lsq_f32.restype = C.c_float
+        L.ora_lsq_f64.argtypes = [f32p, f32p, C.c_int, C.c_int, f32p]
+        L.ora_lsq_f64.restype = C.c_double
         L.ora_argmin_pbest.argtypes = [C.POINTER(_Params), C.POINTER(_State)]
         L.ora_argmin_pbest.restype = C.c_int64
         _lib = L
@@ -106,6 +111,20 @@ def fitness(fid, x):
     return np.float32(lib().ora_fitness(int(fid), _f32p(x), int(x.shape[-1])))
 
 
+def lsq_f32(A, b, x):
+    A = np.ascontiguousarray(A, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    return np.float32(lib().ora_lsq_f32(_f32p(A), _f32p(b), A.shape[0], A.shape[1], _f32p(x)))
+
+
+def lsq_f64(A, b, x):
+    A = np.ascontiguousarray(A, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    return float(lib().ora_lsq_f64(_f32p(A), _f32p(b), A.shape[0], A.shape[1], _f32p(x)))
+
+
 def fit_key(f):
     return int(lib().ora_fit_key(float(np.float32(f))))
 
@@ -113,10 +132,18 @@ def fit_key(f):
 class Swarm:
     """One swarm as the oracle holds it. Fields mirror Table 1 of the paper."""
 
-    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0):
+    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0, lsq=None):
+        """lsq = (A [M][D] float32, b [M] float32) for the least-squares fitness."""
         self.p = _Params(int(N), int(D), float(np.float32(min_pos)), float(np.float32(max_pos)),
                          float(np.float32(max_v)), float(np.float32(w)), float(np.float32(c1)),
-                         float(np.float32(c2)), int(fitness), int(seed), int(swarm))
+                         float(np.float32(c2)), int(fitness), int(seed), int(swarm), None, None, 0)
+        if lsq is not None:
+            self._A = np.ascontiguousarray(lsq[0], np.float32)
+            self._b = np.ascontiguousarray(lsq[1], np.float32)
+            assert self._A.shape == (self._b.size, int(D))
+            self.p.lsq_A = self._A.ctypes.data
+            self.p.lsq_b = self._b.ctypes.data
+            self.p.lsq_M = int(self._b.size)
         self.N, self.D = int(N), int(D)
         self.pos = np.zeros((N, D), np.float32)
         self.v = np.zeros((N, D), np.float32)

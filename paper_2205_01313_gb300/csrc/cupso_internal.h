@@ -42,6 +42,48 @@ cudaError_t prepare_batch();
 int batch_blocks_per_sm(int stages, int minb);
 cudaError_t launch_batch_step(const BatchDev& b, int stages, int minb, int grid, cudaStream_t st);
 
+// Least-squares fitness (kernels_lsq.cu).
+struct LsqTcPlan {
+    alignas(64) unsigned char tmX[128];   // CUtensorMap of the position operand [Np][Kp]
+    alignas(64) unsigned char tmA[128];   // CUtensorMap of A [Mp][Kp]
+    bool fp8;
+    int Np, Mp, Kp;                       // Np % 128 == 0, Mp % 256 == 0, Kp * elem % 128 == 0
+};
+bool lsq_tc_available();
+cudaError_t lsq_prepare();
+// dst[i][k] = round(src[i * si + k * sk] * (fp8 ? scale : 1)), zero-padded to [Np][Kp].
+cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
+                        void* dst, cudaStream_t st);
+bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp);
+// part[s][i] (s < splits actually used) = partial sum of squared residuals.
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, int splits, float* part,
+                          unsigned int* status, long long limit_ns, cudaStream_t st);
+int lsq_tc_splits_used(const LsqTcPlan& p, int splits);
+// Tensor-core fitness state for fixed (A, b): operand copies, scales, plan.
+struct LsqTcState {
+    void* arena = nullptr;
+    bool fp8 = false;
+    int M = 0, D = 0, Np = 0, Mp = 0, Kp = 0;
+    float sx = 1.0f;                 // FP8 scale of the positions
+    void* Aq = nullptr;              // [Mp][Kp] operand copy of A
+    void* Xq = nullptr;              // [Np][Kp] operand copy of the positions
+    float* bpad = nullptr;           // [Mp]
+    float* inv = nullptr;            // [Mp] 1 / (sx * row scale of A) (FP8)
+    float* part = nullptr;           // [splits][Np] partial sums
+    unsigned int* status = nullptr;
+    int splits = 2;
+    LsqTcPlan plan;
+};
+int lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, int D, int Np, bool fp8, float sx,
+                 cudaStream_t stream);
+void lsq_free_tc(LsqTcState* st);
+// f[i] for positions X(i, k) = src[i * si + k * sk], i < N (asynchronous).
+int lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, float* f, cudaStream_t stream);
+
+// f[i] = plain FP32 fitness of X(i, d) = x[d * ldx + i], i < N.
+cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
+                            cudaStream_t st);
+
 // Resident CTAs per SM of the persistent kernels (for grid sizing).
 int sync_blocks_per_sm(int fid, int D);
 int async_blocks_per_sm(int fid, int D);

@@ -1,0 +1,491 @@
+// kernels_lsq.cu -- least-squares fitness f_i = ||A x_i - b||^2 of a whole swarm.
+//
+// For the dense fitness the swarm's Step 3 is a matrix product: with X the
+// N x D matrix of positions, the residuals are R = X A^T - 1 b^T (N x M) and
+// f_i = sum_m R_im^2. Three implementations:
+//
+//  * lsq_fp32_kernel: plain FP32 on the CUDA cores, every residual a chain of
+//    fma over d in order and the squares summed over m in order -- the same
+//    rounding as the oracle, so its trajectories match bit for bit.
+//  * lsq_tc_kernel<false>: BF16 operands on the 5th-generation tensor cores
+//    (tcgen05.mma, FP32 accumulation in tensor memory), operands staged by TMA
+//    with 128-byte swizzle, and the epilogue (subtract b, square, sum over m)
+//    fused onto the accumulator read-back.
+//  * lsq_tc_kernel<true>: the same with FP8 e4m3 operands: A scaled per row,
+//    X by one factor from the search bounds; the epilogue undoes the scales.
+//
+// The tensor-core kernel is warp-specialised: warp 0 issues the TMA loads
+// into a 4-stage shared-memory ring, warp 1 owns the tensor memory and issues
+// the MMAs (128 particles x 256 residual rows per accumulator, two
+// accumulators alternating), warps 2-5 drain the accumulators. Every
+// mbarrier wait is bounded in time; on expiry the kernel records a timeout,
+// lets the copies in flight land, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "cupso_device.cuh"
+#include "cupso_internal.h"
+
+namespace cupso {
+
+namespace {
+
+constexpr int BM = 128;          // particles per tile (MMA M)
+constexpr int BN = 256;          // residual rows per tile (MMA N)
+constexpr int KB = 128;          // K bytes per stage: one 128-byte swizzle row
+constexpr int STAGES = 4;
+constexpr int kTcThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int X_BYTES = BM * KB; // 16 KB
+constexpr int A_BYTES = BN * KB; // 32 KB
+constexpr int STAGE_BYTES = X_BYTES + A_BYTES;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity`; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    for (;;) {
+        for (int k = 0; k < 32; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// rows of 128 bytes, 8-row atoms of 1024 bytes (stride byte offset), tile
+// base 1024-byte aligned.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= (uint64_t)(16u >> 4) << 16;            // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset: one 8-row atom
+    d |= (uint64_t)1 << 46;                     // descriptor version of tcgen05
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = 256.
+// ab_fmt: BF16 = 1 for kind::f16, E4M3 = 0 for kind::f8f6f4.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_fmt) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <bool FP8>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (FP8) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+}  // namespace
+
+// Per-particle partial fitness over this CTA's residual rows:
+//   part[split][i] = sum over m in the split of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
+// X: [Np][Kp] (K-major), A: [Mp][Kp], b: [Mp] (zero-padded rows contribute 0).
+// grid = (Np / 128, splits); each split covers `mt_per_split` tiles of 256 rows.
+template <bool FP8>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    lsq_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
+                  const float* __restrict__ b, const float* __restrict__ inv_scale, int Mp, int KT, int mt_per_split,
+                  int Np, float* __restrict__ part, unsigned int* status, long long limit_ns) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base for the swizzled tiles
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char* base_ptr = smem_raw + (base - raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base_ptr + STAGES * STAGE_BYTES);
+    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM address slot
+    const uint32_t bar0 = base + STAGES * STAGE_BYTES;
+    auto full_bar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (uint32_t)(STAGES + s); };
+    auto tfull_bar = [&](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + a); };
+    auto tempty_bar = [&](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + 2 + a); };
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * STAGES + 5);
+    const uint32_t drain_bar = bar0 + 8u * (uint32_t)(2 * STAGES + 4);
+    __shared__ volatile int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pblock = blockIdx.x;
+    const int mt0 = blockIdx.y * mt_per_split;
+    const int mt1 = min(mt0 + mt_per_split, Mp / BN);
+    const int nt = mt1 - mt0;
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 4);
+        }
+        mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        // 512 columns: two 128 x 256 FP32 accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32((const void*)tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int total = nt * KT;   // (tile, k-stage) steps
+    int issued = 0;              // TMA stages issued (producer)
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int step = 0; step < total; ++step) {
+                const int s = step % STAGES, f = step / STAGES;
+                if (f > 0 && !mbar_wait(empty_bar(s), (uint32_t)((f - 1) & 1), limit_ns)) {
+                    atomicOr(status, kStatusTimeout);
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                const int jj = step / KT, kk = step % KT;
+                mbar_expect_tx(full_bar(s), (uint32_t)STAGE_BYTES);
+                const uint32_t xs = base + (uint32_t)(s * STAGE_BYTES);
+                tma_load_2d(xs, &tmX, kk * KB / (FP8 ? 1 : 2), pblock * BM, full_bar(s));
+                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / (FP8 ? 1 : 2), (mt0 + jj) * BN, full_bar(s));
+                ++issued;
+            }
+            // let every issued copy land before shared memory can go away
+            for (int step = 0; step < issued; ++step) {
+                if (step + STAGES < issued) continue;   // older stages were consumed already
+                mbar_wait(full_bar(step % STAGES), (uint32_t)((step / STAGES) & 1), limit_ns);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc(FP8 ? 0u : 1u);
+            constexpr uint32_t kstep_bytes = 32;   // 16 bf16 or 32 fp8 per MMA
+            int step = 0;
+            for (int jj = 0; jj < nt && !s_fail; ++jj) {
+                const int a = jj & 1, u = jj >> 1;
+                if (u > 0 && !mbar_wait(tempty_bar(a), (uint32_t)((u - 1) & 1), limit_ns)) {
+                    atomicOr(status, kStatusTimeout);
+                    s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(a * BN);
+                for (int kk = 0; kk < KT; ++kk, ++step) {
+                    const int s = step % STAGES, f = step / STAGES;
+                    if (!mbar_wait(full_bar(s), (uint32_t)(f & 1), limit_ns)) {
+                        atomicOr(status, kStatusTimeout);
+                        s_fail = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xs = base + (uint32_t)(s * STAGE_BYTES);
+#pragma unroll
+                    for (int k4 = 0; k4 < KB / (int)kstep_bytes; ++k4) {
+                        const uint64_t ad = desc_sw128(xs + k4 * kstep_bytes);
+                        const uint64_t bd = desc_sw128(xs + X_BYTES + k4 * kstep_bytes);
+                        umma<FP8>(d_tmem, ad, bd, idesc, (kk > 0 || k4 > 0) ? 1u : 0u);
+                    }
+                    umma_commit(empty_bar(s));   // the stage is free once these MMAs are done
+                }
+                if (s_fail) break;
+                umma_commit(tfull_bar(a));       // accumulator a holds tile jj
+            }
+            // every MMA issued has finished before tensor memory is released
+            umma_commit(drain_bar);
+            if (!mbar_wait(drain_bar, 0u, limit_ns)) atomicOr(status, kStatusTimeout);
+        }
+        __syncwarp();
+    } else {
+        // epilogue: thread = one particle row of the tile
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int row = q * 32 + lane;
+        const int i = pblock * BM + row;
+        float sum = 0.0f;
+        bool ok = true;
+        for (int jj = 0; jj < nt; ++jj) {
+            const int a = jj & 1, u = jj >> 1;
+            // warp-uniform outcome: tcgen05.ld below needs the whole warp
+            if (!__all_sync(0xFFFFFFFFu, mbar_wait(tfull_bar(a), (uint32_t)(u & 1), limit_ns))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int m0 = (mt0 + jj) * BN;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
+            for (int c = 0; c < BN; c += 16) {
+                float v[16];
+                tmem_ld16(taddr + (uint32_t)c, v);
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int m = m0 + c + e;
+                    const float val = FP8 ? __fmul_rn(v[e], __ldg(inv_scale + m)) : v[e];
+                    const float r = __fsub_rn(val, __ldg(b + m));
+                    sum = __fmaf_rn(r, r, sum);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(a));
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(status, kStatusTimeout);
+            s_fail = 1;
+        }
+        if (i < Np) part[(size_t)blockIdx.y * Np + i] = ok ? sum : __int_as_float(0x7fc00000);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// Converts positions to the K-major tensor-core operand: dst[i][k] = src(i, k)
+// rounded to BF16 (or x * scale to FP8 e4m3), zero for i >= N or k >= D.
+// src(i, k) = src[i * si + k * sk]. One thread per 4 consecutive k of one row.
+template <bool FP8>
+__global__ void convert_operand_kernel(const float* __restrict__ src, size_t si, size_t sk, int N, int D, int Np,
+                                       int Kp, float scale, void* __restrict__ dst) {
+    const size_t groups = (size_t)Np * (size_t)(Kp / 4);
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g / (size_t)(Kp / 4));
+        const int k0 = (int)(g % (size_t)(Kp / 4)) * 4;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = k0 + e;
+            v[e] = (i < N && k < D) ? src[(size_t)i * si + (size_t)k * sk] : 0.0f;
+        }
+        if constexpr (FP8) {
+            __nv_fp8x4_e4m3 q(make_float4(v[0] * scale, v[1] * scale, v[2] * scale, v[3] * scale));
+            reinterpret_cast<__nv_fp8x4_e4m3*>(dst)[(size_t)i * (Kp / 4) + k0 / 4] = q;
+        } else {
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v[0], v[1]);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(v[2], v[3]);
+            __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(dst) + ((size_t)i * Kp + k0) / 2;
+            d[0] = lo;
+            d[1] = hi;
+        }
+    }
+}
+
+// Plain FP32 least-squares fitness with the oracle's rounding order. Block =
+// 64 particles x all M, in tiles of 64 residual rows; thread (ty, tx) holds a
+// 4 x 4 block of (particle, row) residuals, each a chain of fma over d in
+// order; then 64 threads add the tile's squares to their particle's sum in
+// row order. X(i, d) = x[d * ldx + i] (the swarm layout).
+__global__ void __launch_bounds__(256) lsq_fp32_kernel(const float* __restrict__ x, int ldx, int N, int D,
+                                                       const float* __restrict__ A, const float* __restrict__ b, int M,
+                                                       float* __restrict__ f) {
+    __shared__ float Xs[32][64 + 4];   // [d][particle]
+    __shared__ float As[32][64 + 4];   // [d][row]
+    __shared__ float Rs[64][64 + 1];   // [particle][row]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * 64;
+    float acc_i = 0.0f;                // the running sum of particle i0 + threadIdx.x (threads < 64)
+    for (int m0 = 0; m0 < M; m0 += 64) {
+        float r[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int m = m0 + tx * 4 + c;
+                r[a][c] = m < M ? -b[m] : 0.0f;
+            }
+        for (int d0 = 0; d0 < D; d0 += 32) {
+            for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+                const int dd = e / 64, col = e % 64;
+                const int d = d0 + dd;
+                Xs[dd][col] = (d < D && i0 + col < N) ? x[(size_t)d * ldx + i0 + col] : 0.0f;
+                As[dd][col] = (d < D && m0 + col < M) ? A[(size_t)(m0 + col) * D + d] : 0.0f;
+            }
+            __syncthreads();
+            const int dn = min(32, D - d0);
+            for (int dd = 0; dd < dn; ++dd) {
+                float xv[4], av[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xv[a] = Xs[dd][ty * 4 + a];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) av[c] = As[dd][tx * 4 + c];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) r[a][c] = __fmaf_rn(av[c], xv[a], r[a][c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) Rs[ty * 4 + a][tx * 4 + c] = r[a][c];
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int mn = min(64, M - m0);
+            for (int c = 0; c < mn; ++c) acc_i = __fmaf_rn(Rs[threadIdx.x][c], Rs[threadIdx.x][c], acc_i);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 64 && i0 + threadIdx.x < N) f[i0 + threadIdx.x] = acc_i;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D map over a K-major [rows][Kp] operand, box = (128 bytes of K) x box_rows.
+bool make_map(CUtensorMap* tm, void* ptr, bool fp8, int rows, int Kp, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const int esz = fp8 ? 1 : 2;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(KB / esz), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(tm, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t tc_smem() { return (size_t)STAGES * STAGE_BYTES + 1024 + 256; }
+
+}  // namespace
+
+bool lsq_tc_available() { return encode_fn() != nullptr; }
+
+cudaError_t lsq_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(lsq_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(lsq_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());
+}
+
+cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
+                        void* dst, cudaStream_t st) {
+    const size_t groups = (size_t)Np * (size_t)(Kp / 4);
+    const int grid = (int)std::min<size_t>((groups + 255) / 256, 8192);
+    if (fp8) convert_operand_kernel<true><<<grid, 256, 0, st>>>(src, si, sk, N, D, Np, Kp, scale, dst);
+    else convert_operand_kernel<false><<<grid, 256, 0, st>>>(src, si, sk, N, D, Np, Kp, scale, dst);
+    return cudaGetLastError();
+}
+
+bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp) {
+    p->fp8 = fp8;
+    p->Np = Np;
+    p->Mp = Mp;
+    p->Kp = Kp;
+    if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmX), Xq, fp8, Np, Kp, BM)) return false;
+    if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmA), Aq, fp8, Mp, Kp, BN)) return false;
+    return true;
+}
+
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, int splits, float* part,
+                          unsigned int* status, long long limit_ns, cudaStream_t st) {
+    const int mtiles = p.Mp / BN;
+    const int per = (mtiles + splits - 1) / splits;
+    const int KT = p.Kp * (p.fp8 ? 1 : 2) / KB;
+    dim3 grid(p.Np / BM, (mtiles + per - 1) / per);
+    const CUtensorMap& tx = *reinterpret_cast<const CUtensorMap*>(p.tmX);
+    const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(p.tmA);
+    if (p.fp8)
+        lsq_tc_kernel<true><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, per, p.Np, part,
+                                                                  status, limit_ns);
+    else
+        lsq_tc_kernel<false><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, per, p.Np, part,
+                                                                   status, limit_ns);
+    return cudaGetLastError();
+}
+
+int lsq_tc_splits_used(const LsqTcPlan& p, int splits) {
+    const int mtiles = p.Mp / BN;
+    const int per = (mtiles + splits - 1) / splits;
+    return (mtiles + per - 1) / per;
+}
+
+cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
+                            cudaStream_t st) {
+    lsq_fp32_kernel<<<(N + 63) / 64, 256, 0, st>>>(x, ldx, N, D, A, b, M, f);
+    return cudaGetLastError();
+}
+
+}  // namespace cupso

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcupso.so")
 
 CUPSO_SPHERE, CUPSO_RASTRIGIN, CUPSO_ACKLEY, CUPSO_ROSENBROCK, CUPSO_CUBIC_MAX = 0, 1, 2, 3, 4
-FITNESS = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "cubic_max": 4}
+FITNESS = {"sphere": 0, "rastrigin": 1, "ackley": 2, "rosenbrock": 3, "cubic_max": 4, "lsq": 5}
 
 CUPSO_OK = 0
 CUPSO_ERR_INVALID_ARG = -1
@@ -39,7 +39,11 @@ CUPSO_OPT_FAULT_HOLD_LOCK = 100
 # The names the library must export (every function of include/cupso.h).
 ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_step", "cupso_get_gbest",
                  "cupso_get_state", "cupso_set_state", "cupso_get_info", "cupso_solve_batch", "cupso_destroy",
-                 "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc")
+                 "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc", "cupso_lsq_eval")
+
+CUPSO_LSQ = 5
+CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8 = 0, 1, 2
+LSQ_PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
 
 CUPSO_NOALLOC_MAX_N = 4194304
 CUPSO_NOALLOC_MAX_D = 1024
@@ -92,6 +96,8 @@ def _load():
                                           C.c_float, C.c_int, C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p, C.c_void_p]
+    L.cupso_lsq_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                 C.c_void_p, C.c_void_p]
     L.cupso_destroy.argtypes = [h]
     L.cupso_status_string.argtypes = [C.c_int]
     L.cupso_status_string.restype = C.c_char_p
@@ -221,6 +227,12 @@ def cupso_tree_step_noalloc(D, N, bounds, w, c1, c2, fitness_id, seed, swarm_id,
                                         pos, v, pbest_pos, pbest_fit, int(ld), gbest_pos, gbest_fit or None,
                                         gbest_idx or None, status_out or None, cuda_stream or None),
            "cupso_tree_step_noalloc")
+
+
+def cupso_lsq_eval(A_dev, b_dev, M, D, X_dev, N, precision, f_out_dev, cuda_stream=0):
+    """f_out[i] = ||A x_i - b||^2; every buffer argument is a device address (int)."""
+    _check(_lib.cupso_lsq_eval(A_dev, b_dev, int(M), int(D), X_dev, int(N), int(precision), f_out_dev,
+                               cuda_stream or None), "cupso_lsq_eval")
 
 
 def cupso_destroy(h):

@@ -1,0 +1,79 @@
+"""Least-squares fitness ||A x - b||^2 of many positions: the plain FP32 path
+against the oracle (bit for bit), the BF16 and FP8 tensor-core paths against
+the FP64 value within bounds derived from the operand rounding."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.gpu_common import load_cupso
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    return load_cupso()
+
+
+def _problem(M, D, N, seed=0):
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((M, D)) / 64.0).astype(np.float32)      # N(0, 1/4096)
+    xs = rng.uniform(-1, 1, D).astype(np.float32)
+    b = (A.astype(np.float64) @ xs + 1e-3 * rng.standard_normal(M)).astype(np.float32)
+    X = rng.uniform(-2, 2, (N, D)).astype(np.float32)
+    return A, b, X
+
+
+def _eval(P, A, b, X, precision):
+    import torch
+    dA, db, dX = (torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (A, b, X))
+    f = torch.full((X.shape[0],), float("nan"), dtype=torch.float32, device="cuda")
+    P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), A.shape[0], A.shape[1], dX.data_ptr(), X.shape[0], precision,
+                     f.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return f.cpu().numpy()
+
+
+def _round_bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("M,D,N", [(40, 7, 30), (300, 65, 257), (513, 130, 129)])
+def test_lsq_fp32_bit_exact(P, M, D, N):
+    A, b, X = _problem(M, D, N)
+    f = _eval(P, A, b, X, P.CUPSO_LSQ_FP32)
+    ref = np.array([O.lsq_f32(A, b, X[i]) for i in range(N)], np.float32)
+    np.testing.assert_array_equal(f.view(np.uint32), ref.view(np.uint32))
+
+
+@pytest.mark.parametrize("M,D,N", [(256, 64, 128), (700, 200, 1000), (4096, 1024, 512)])
+def test_lsq_bf16_tensor_cores(P, M, D, N):
+    """f~ from BF16 operands equals the FP64 fitness of the BF16-rounded operands up
+    to FP32 accumulation error, and the FP64 fitness of the exact operands within
+    the bound the operand rounding implies."""
+    A, b, X = _problem(M, D, N, seed=M)
+    f = _eval(P, A, b, X, P.CUPSO_LSQ_BF16).astype(np.float64)
+    Ab, Xb = _round_bf16(A), _round_bf16(X)
+    Rb = Xb @ Ab.T - b.astype(np.float64)[None, :]
+    f_rounded = np.sum(Rb * Rb, axis=1)
+    np.testing.assert_allclose(f, f_rounded, rtol=2e-5, atol=1e-6)
+    R = X.astype(np.float64) @ A.astype(np.float64).T - b.astype(np.float64)[None, :]
+    f64 = np.sum(R * R, axis=1)
+    dR = np.abs(Xb @ Ab.T - X.astype(np.float64) @ A.astype(np.float64).T)
+    bound = np.sum(2 * np.abs(R) * dR + dR * dR, axis=1) * 1.01 + 1e-5 * f64
+    assert np.all(np.abs(f - f64) <= bound)
+    assert np.median(np.abs(f - f64) / f64) < 5e-3
+
+
+@pytest.mark.parametrize("M,D,N", [(256, 128, 128), (700, 300, 1000)])
+def test_lsq_fp8_tensor_cores(P, M, D, N):
+    A, b, X = _problem(M, D, N, seed=M + 1)
+    f = _eval(P, A, b, X, P.CUPSO_LSQ_FP8).astype(np.float64)
+    R = X.astype(np.float64) @ A.astype(np.float64).T - b.astype(np.float64)[None, :]
+    f64 = np.sum(R * R, axis=1)
+    # e4m3 keeps 3 mantissa bits: relative rounding 2^-4 per operand (scaled to use the range)
+    dR = np.abs(X.astype(np.float64)) @ np.abs(A.astype(np.float64)).T * (2 * 2.0 ** -4 + 2.0 ** -8)
+    bound = np.sum(2 * np.abs(R) * dR + dR * dR, axis=1) + 1e-5 * f64
+    assert np.all(np.abs(f - f64) <= bound)
+    assert np.median(np.abs(f - f64) / f64) < 5e-2

@@ -377,3 +377,52 @@ def test_rejects_invalid_params():
         O.Swarm(4, 3, 1, -1, 1, 0.5, 1, 1, O.SPHERE, 1).init()
     with pytest.raises(ValueError):
         O.Swarm(4, 3, -1, 1, 0, 0.5, 1, 1, O.SPHERE, 1).init()
+
+
+# --------------------------------------------------------------------------- #
+# Least squares ||A x - b||^2 (the dense fitness of the precision study)       #
+# --------------------------------------------------------------------------- #
+
+def _lsq_problem(M, D, seed=0, noise=1e-3):
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((M, D)) / np.sqrt(M)).astype(np.float32)
+    xs = rng.uniform(-1, 1, D).astype(np.float32)
+    b = (A.astype(np.float64) @ xs + noise * rng.standard_normal(M)).astype(np.float32)
+    return A, b, xs
+
+
+def test_lsq_fp64_minimum_is_the_lstsq_solution():
+    """The FP64 fitness at numpy's least-squares solution is the closed-form minimum
+    (the residual norm lstsq reports), and no perturbation goes below it."""
+    A, b, _ = _lsq_problem(96, 12)
+    x64, res, rank, _ = np.linalg.lstsq(A.astype(np.float64), b.astype(np.float64), rcond=None)
+    xf = x64.astype(np.float32)
+    fmin = O.lsq_f64(A, b, xf)
+    assert abs(fmin - float(res[0])) <= 1e-6 * float(res[0]) + 1e-9   # float32 rounding of x only
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        assert O.lsq_f64(A, b, (x64 + 1e-2 * rng.standard_normal(12)).astype(np.float32)) > fmin
+
+
+def test_lsq_f32_within_rounding_of_f64():
+    A, b, xs = _lsq_problem(300, 40, seed=3)
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        x = rng.uniform(-2, 2, 40).astype(np.float32)
+        f64 = O.lsq_f64(A, b, x)
+        f32 = float(O.lsq_f32(A, b, x))
+        assert abs(f32 - f64) <= 1e-5 * f64
+    assert O.lsq_f64(A, b, xs) < 1e-3 * 300       # b = A x* + noise: f(x*) ~ M sigma^2
+
+
+def test_lsq_swarm_steps_follow_the_swarm_rules():
+    A, b, _ = _lsq_problem(64, 6, seed=5)
+    s = O.Swarm(40, 6, -2, 2, 0.4, 0.729, 1.49445, 1.49445, O.LSQ, 2, lsq=(A, b)).init()
+    prev = s.pbest_fit.copy()
+    for _ in range(15):
+        s.step_sync(1)
+        assert np.all(s.pbest_fit <= prev)
+        prev = s.pbest_fit.copy()
+    for i in range(40):
+        assert s.pbest_fit[i] == O.lsq_f32(A, b, s.pbest_pos[i])
+    assert s.gbest_idx == int(np.lexsort((np.arange(40), s.pbest_fit))[0])

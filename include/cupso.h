@@ -168,6 +168,25 @@ CUPSO_API int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest
 CUPSO_API int cupso_set_state(cupso_handle h, const float* pos, const float* v, const float* pbest_pos,
                     const float* pbest_fit, uint32_t t);
 
+/* Least-squares fitness ||A x - b||^2 for a swarm created with CUPSO_LSQ:
+ * A device [M][D] row-major float32, b device [M] float32, both borrowed (they
+ * must stay valid until the handle is destroyed or they are replaced).
+ * precision (cupso_lsq_precision) selects how the swarm's fitness -- one
+ * matrix product X A^T per iteration -- is computed: FP32 on the CUDA cores
+ * in a fixed order (the synchronous trajectory is then exactly the oracle's),
+ * or BF16 / FP8 e4m3 on the tensor cores with FP32 accumulation. In the BF16
+ * and FP8 modes the pbest decisions use the approximate fitness, while a
+ * global best is accepted only after the (up to) 16 improved particles with
+ * the lowest approximate fitness are rescored in FP64; gbest_fit is then that
+ * FP64 value (rounded to float). This call evaluates the fitness of every
+ * particle's pbest_pos (the end of Step 1 for such a swarm) and the gbest, and
+ * waits. Steps of a CUPSO_LSQ swarm fail until it has been called. */
+CUPSO_API int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M, int precision);
+
+/* FP64 fitness ||A g - b||^2 of the current gbest_pos g of a least-squares
+ * swarm (the residual the precision modes are judged by). Waits. */
+CUPSO_API int cupso_get_gbest_f64(cupso_handle h, double* fit_out);
+
 /* Fill *info. */
 CUPSO_API int cupso_get_info(cupso_handle h, cupso_info* info);
 

@@ -68,6 +68,20 @@ struct cupso_swarm {
     int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
     bool pipelined_ok = false;      // shared-memory limit raised for the pipelined kernels
     bool lazy_pending = false;      // the pipelined step may have left pbest rows unwritten
+    // least-squares fitness (fitness_id CUPSO_LSQ), set by cupso_set_lsq
+    struct Lsq {
+        const float* A = nullptr;   // [M][D], borrowed
+        const float* b = nullptr;   // [M], borrowed
+        int M = 0, precision = 0;
+        LsqTcState tc;              // BF16 / FP8 operands and plan
+        void* buf = nullptr;        // f [Np] | cand [blocks*16 + 16] | partial [16 * chunks] | g64
+        float* f = nullptr;
+        unsigned long long* cand = nullptr;
+        double* partial = nullptr;
+        double* g64 = nullptr;
+        int chunks = 64;
+    };
+    Lsq* lsq = nullptr;
 };
 
 namespace {
@@ -128,8 +142,25 @@ void drop_graph(cupso_swarm* h) {
     h->graph_len = 0;
 }
 
+constexpr int kModeLsq = 100;   // internal: one least-squares iteration
+
+cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
+    cupso_swarm::Lsq& L = *h->lsq;
+    const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
+    cudaError_t e = lsq_launch_move(h->dev, grid, st);
+    if (e != cudaSuccess) return e;
+    if (L.precision == CUPSO_LSQ_FP32) {
+        e = lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
+        if (e != cudaSuccess) return e;
+        return lsq_launch_select_exact(h->dev, L.f, grid, st);
+    }
+    if (lsq_eval_tc(&L.tc, h->dev.x, 1, (size_t)h->Np, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
+    return lsq_launch_gbest_approx(h->dev, L.f, 0, L.A, L.b, L.M, L.cand, L.partial, L.chunks, L.g64, st);
+}
+
 cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
     switch (mode) {
+        case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
             const int stages = sync_stages(h);
             if (stages) return launch_sync_pipelined(h->dev, h->fid, stages, sync_grid(h), st);
@@ -193,7 +224,7 @@ int cupso::check_problem_args(int D, int N, const cupso_bounds* b, float w, floa
     if (!(b->max_v > 0.0f)) return fail(CUPSO_ERR_INVALID_ARG, "max_v must be > 0%s");
     if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
         return fail(CUPSO_ERR_INVALID_ARG, "w, c1, c2 must be finite%s");
-    if (fid < CUPSO_SPHERE || fid > CUPSO_CUBIC_MAX) return fail(CUPSO_ERR_INVALID_ARG, "unknown fitness_id%s");
+    if (fid < CUPSO_SPHERE || fid > CUPSO_LSQ) return fail(CUPSO_ERR_INVALID_ARG, "unknown fitness_id%s");
     return CUPSO_OK;
 }
 
@@ -285,7 +316,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.fast_clamp = (b->min_pos != 0.0f && b->max_pos != 0.0f) ? 1 : 0;
 
     int cl = 0, per = 0;
-    h->onchip_cluster = onchip_fits(N, D, &cl, &per) ? cl : 0;
+    h->onchip_cluster = (fid != CUPSO_LSQ && onchip_fits(N, D, &cl, &per)) ? cl : 0;
     h->pipelined_ok = prepare_pipelined(D) == cudaSuccess;
     cudaGetLastError();
 
@@ -358,6 +389,8 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
         case CUPSO_OPT_MODE:
             if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_ONCHIP)
                 return fail(CUPSO_ERR_INVALID_ARG, "unknown mode%s");
+            if (h->fid == CUPSO_LSQ && value != CUPSO_MODE_AUTO && value != CUPSO_MODE_SYNC)
+                return fail(CUPSO_ERR_UNSUPPORTED, "least-squares swarms run the synchronous iteration only%s");
             if (value == CUPSO_MODE_ONCHIP && h->onchip_cluster == 0)
                 return fail(CUPSO_ERR_UNSUPPORTED, "swarm does not fit in one cluster's shared memory%s");
             h->mode = (int)value;
@@ -400,6 +433,26 @@ int cupso_step(cupso_handle h, int iters) {
     if (iters == 0) return CUPSO_OK;
     if ((uint64_t)h->t_host + (uint64_t)iters > 0xFFFFFFFFull)
         return fail(CUPSO_ERR_INVALID_ARG, "iteration counter would overflow%s");
+    if (h->fid == CUPSO_LSQ) {
+        if (!h->lsq) return fail(CUPSO_ERR_INVALID_ARG, "least-squares swarm: call cupso_set_lsq first%s");
+        int left = iters;
+        const int L = h->graph_chunk;
+        if (L > 1 && left >= L) {
+            int rc = ensure_graph(h, kModeLsq, L);
+            if (rc) return rc;
+            while (left >= L) {
+                cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+                left -= L;
+            }
+        }
+        for (; left > 0; --left) {
+            cudaError_t e = launch_lsq_iteration(h, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "least-squares iteration");
+        }
+        h->t_host += (uint32_t)iters;
+        return CUPSO_OK;
+    }
     const int mode = resolved_mode(h);
     const bool pipelined = mode == CUPSO_MODE_SYNC && sync_stages(h) > 0;
     if (!pipelined) {
@@ -503,6 +556,91 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
     return CUPSO_OK;
 }
 
+int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M, int precision) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fid != CUPSO_LSQ) return fail(CUPSO_ERR_INVALID_ARG, "swarm was not created with CUPSO_LSQ%s");
+    if (!A_dev || !b_dev || M < 1) return fail(CUPSO_ERR_INVALID_ARG, "A, b must be device arrays and M >= 1%s");
+    if (precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP8) return fail(CUPSO_ERR_INVALID_ARG, "unknown precision%s");
+    if (precision != CUPSO_LSQ_FP32 && !lsq_tc_available())
+        return fail(CUPSO_ERR_UNSUPPORTED, "tensor-core least squares needs cuTensorMapEncodeTiled%s");
+    int rc = ensure_materialized(h);
+    if (rc) return rc;
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    drop_graph(h);
+    if (h->lsq) {
+        lsq_free_tc(&h->lsq->tc);
+        if (h->lsq->buf) cudaFree(h->lsq->buf);
+        delete h->lsq;
+        h->lsq = nullptr;
+    }
+    auto* L = new (std::nothrow) cupso_swarm::Lsq();
+    if (!L) return fail(CUPSO_ERR_OOM, "host allocation failed%s");
+    h->lsq = L;
+    L->A = A_dev;
+    L->b = b_dev;
+    L->M = M;
+    L->precision = precision;
+    const int nblk = tiles_of(h->Np);
+    const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256) +
+                         align_up(sizeof(double) * 16 * L->chunks, 256) + 256;
+    cudaError_t e = cudaMalloc(&L->buf, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (lsq)");
+    char* p = static_cast<char*>(L->buf);
+    L->f = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * h->Np, 256);
+    L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256);
+    L->partial = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * 16 * L->chunks, 256);
+    L->g64 = reinterpret_cast<double*>(p);
+    const double inf = INFINITY;
+    CUPSO_CUDA(cudaMemcpyAsync(L->g64, &inf, sizeof(double), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaMemsetAsync(L->f, 0, sizeof(float) * h->Np, h->stream), "cudaMemsetAsync");
+    if (precision != CUPSO_LSQ_FP32) {
+        // FP8 scale of the positions from the search box
+        const float xmax = std::max(std::fabs(h->dev.lo), std::fabs(h->dev.hi));
+        const float sx = xmax > 0.0f ? 448.0f / xmax : 1.0f;
+        rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
+        if (rc) return rc;
+    }
+    // Step 1 completes here: pbest_fit = f(pbest_pos), gbest from it.
+    if (precision == CUPSO_LSQ_FP32) {
+        CUPSO_CUDA(lsq_fp32_launch(h->dev.pb, h->Np, h->N, h->D, A_dev, b_dev, M, L->f, h->stream), "lsq fitness");
+        CUPSO_CUDA(lsq_launch_set_pf(h->dev, L->f, h->stream), "lsq pbest");
+        CUPSO_CUDA(launch_recompute(h->dev, h->t_host, h->stream), "recompute launch");
+    } else {
+        rc = lsq_eval_tc(&L->tc, h->dev.pb, 1, (size_t)h->Np, h->N, L->f, h->stream);
+        if (rc) return rc;
+        CUPSO_CUDA(lsq_launch_set_pf(h->dev, L->f, h->stream), "lsq pbest");
+        // the accept kernel advances t: start one below and let it land on t_host
+        CUPSO_CUDA(lsq_launch_set_t(h->dev, h->t_host - 1u, h->stream), "lsq t");
+        CUPSO_CUDA(lsq_launch_gbest_approx(h->dev, L->f, 1, A_dev, b_dev, M, L->cand, L->partial, L->chunks, L->g64,
+                                           h->stream),
+                   "lsq gbest");
+    }
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return CUPSO_OK;
+}
+
+int cupso_get_gbest_f64(cupso_handle h, double* fit_out) {
+    if (!h || !fit_out) return fail(CUPSO_ERR_INVALID_ARG, "NULL argument%s");
+    if (h->fid != CUPSO_LSQ || !h->lsq) return fail(CUPSO_ERR_INVALID_ARG, "not a least-squares swarm with A, b set%s");
+    cupso_swarm::Lsq& L = *h->lsq;
+    if (L.precision == CUPSO_LSQ_FP32) {
+        // rescore the gbest particle's pbest_pos (== gbest_pos) in FP64
+        const int rc = ensure_materialized(h);
+        if (rc) return rc;
+        const int cur = (int)(h->t_host & 1u);
+        CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+        unsigned long long key = 0;
+        CUPSO_CUDA(cudaMemcpy(&key, h->dev.gkey + cur, sizeof(key), cudaMemcpyDeviceToHost), "cudaMemcpy");
+        const double inf = INFINITY;
+        CUPSO_CUDA(cudaMemcpy(L.g64, &inf, sizeof(double), cudaMemcpyHostToDevice), "cudaMemcpy");
+        CUPSO_CUDA(lsq_rescore_one(h->dev, L.A, L.b, L.M, key, L.cand, L.partial, L.chunks, L.g64, h->stream),
+                   "lsq rescore");
+    }
+    CUPSO_CUDA(cudaMemcpyAsync(fit_out, L.g64, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    return CUPSO_OK;
+}
+
 int cupso_get_info(cupso_handle h, cupso_info* info) {
     if (!h || !info) return fail(CUPSO_ERR_INVALID_ARG, "NULL argument%s");
     info->N = h->N;
@@ -526,6 +664,12 @@ int cupso_destroy(cupso_handle h) {
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaStreamSynchronize");
     }
     drop_graph(h);
+    if (h->lsq) {
+        lsq_free_tc(&h->lsq->tc);
+        if (h->lsq->buf) cudaFree(h->lsq->buf);
+        delete h->lsq;
+        h->lsq = nullptr;
+    }
     if (h->arena) cudaFree(h->arena);
     if (h->capture) cudaStreamDestroy(h->capture);
     if (h->own) cudaStreamDestroy(h->own);

@@ -84,6 +84,19 @@ int lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, f
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
                             cudaStream_t st);
 
+// Least-squares swarm iteration (kernels_lsq_swarm.cu); all read t from t_dev.
+cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
+cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, int grid, cudaStream_t st);
+int lsq_cand_blocks(const SwarmDev& s);
+cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all, const float* A, const float* b,
+                                    int M, unsigned long long* cand, double* partial, int chunks, double* g64,
+                                    cudaStream_t st);
+cudaError_t lsq_launch_set_pf(const SwarmDev& s, const float* fit, cudaStream_t st);
+// FP64 fitness of the pbest_pos of the particle in `key`, into *g64; waits.
+cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, int M, unsigned long long key,
+                            unsigned long long* scratch, double* partial, int chunks, double* g64, cudaStream_t st);
+cudaError_t lsq_launch_set_t(const SwarmDev& s, uint32_t t, cudaStream_t st);
+
 // Resident CTAs per SM of the persistent kernels (for grid sizing).
 int sync_blocks_per_sm(int fid, int D);
 int async_blocks_per_sm(int fid, int D);

@@ -436,8 +436,12 @@ __global__ void __launch_bounds__(1024) recompute_kernel(const __grid_constant__
         default: return cudaErrorInvalidValue;                     \
     }
 
+// Step 1 also covers the least-squares fitness (its values come later).
+#define CUPSO_DISPATCH_FIT_INIT(fid, KERNEL_CALL)                  \
+    if (fid == kLsq) { constexpr int F = kLsq; KERNEL_CALL; } else CUPSO_DISPATCH_FIT(fid, KERNEL_CALL)
+
 cudaError_t launch_init(const SwarmDev& s, int fid, int grid, cudaStream_t st) {
-    CUPSO_DISPATCH_FIT(fid, (init_kernel<F><<<grid, kBlock, 0, st>>>(s)));
+    CUPSO_DISPATCH_FIT_INIT(fid, (init_kernel<F><<<grid, kBlock, 0, st>>>(s)));
     return cudaGetLastError();
 }
 

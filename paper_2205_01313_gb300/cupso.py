@@ -39,7 +39,8 @@ CUPSO_OPT_FAULT_HOLD_LOCK = 100
 # The names the library must export (every function of include/cupso.h).
 ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_step", "cupso_get_gbest",
                  "cupso_get_state", "cupso_set_state", "cupso_get_info", "cupso_solve_batch", "cupso_destroy",
-                 "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc", "cupso_lsq_eval")
+                 "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc", "cupso_lsq_eval",
+                 "cupso_set_lsq", "cupso_get_gbest_f64")
 
 CUPSO_LSQ = 5
 CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8 = 0, 1, 2
@@ -98,6 +99,8 @@ def _load():
                                           C.c_void_p, C.c_void_p, C.c_void_p]
     L.cupso_lsq_eval.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                  C.c_void_p, C.c_void_p]
+    L.cupso_set_lsq.argtypes = [h, C.c_void_p, C.c_void_p, C.c_int, C.c_int]
+    L.cupso_get_gbest_f64.argtypes = [h, C.POINTER(C.c_double)]
     L.cupso_destroy.argtypes = [h]
     L.cupso_status_string.argtypes = [C.c_int]
     L.cupso_status_string.restype = C.c_char_p
@@ -235,6 +238,17 @@ def cupso_lsq_eval(A_dev, b_dev, M, D, X_dev, N, precision, f_out_dev, cuda_stre
                                cuda_stream or None), "cupso_lsq_eval")
 
 
+def cupso_set_lsq(h, A_dev, b_dev, M, precision):
+    """A_dev, b_dev: device addresses (int) of A [M][D] and b [M], float32, borrowed."""
+    _check(_lib.cupso_set_lsq(h, A_dev, b_dev, int(M), int(precision)), "cupso_set_lsq")
+
+
+def cupso_get_gbest_f64(h):
+    v = C.c_double()
+    _check(_lib.cupso_get_gbest_f64(h, C.byref(v)), "cupso_get_gbest_f64")
+    return float(v.value)
+
+
 def cupso_destroy(h):
     if h is not None and h.value:
         _check(_lib.cupso_destroy(h), "cupso_destroy")
@@ -276,6 +290,12 @@ class Swarm:
 
     def info(self):
         return cupso_get_info(self.h)
+
+    def set_lsq(self, A_dev, b_dev, M, precision):
+        cupso_set_lsq(self.h, A_dev, b_dev, M, LSQ_PRECISIONS[precision] if isinstance(precision, str) else precision)
+
+    def gbest_f64(self):
+        return cupso_get_gbest_f64(self.h)
 
     def close(self):
         cupso_destroy(self.h)

@@ -77,3 +77,71 @@ def test_lsq_fp8_tensor_cores(P, M, D, N):
     bound = np.sum(2 * np.abs(R) * dR + dR * dR, axis=1) + 1e-5 * f64
     assert np.all(np.abs(f - f64) <= bound)
     assert np.median(np.abs(f - f64) / f64) < 5e-2
+
+
+# --------------------------------------------------------------------------- #
+# Swarms with the least-squares fitness                                        #
+# --------------------------------------------------------------------------- #
+
+LSQ_BOUNDS = (-2.0, 2.0, 0.4)
+W, C12 = 0.729, 1.49445
+
+
+def _lsq_swarm(P, A, b, N, seed, precision):
+    import torch
+    dA = torch.from_numpy(A).cuda()
+    db = torch.from_numpy(b).cuda()
+    s = P.Swarm(A.shape[1], N, LSQ_BOUNDS, W, C12, C12, P.CUPSO_LSQ, seed)
+    s.set_lsq(dA.data_ptr(), db.data_ptr(), A.shape[0], precision)
+    s._keep = (dA, db)        # the library borrows A and b
+    return s
+
+
+def test_lsq_swarm_needs_set_lsq(P):
+    with P.Swarm(8, 100, LSQ_BOUNDS, W, C12, C12, P.CUPSO_LSQ, 1) as s:
+        with pytest.raises(P.CupsoError):
+            s.step(1)
+
+
+@pytest.mark.parametrize("N,D,M", [(300, 24, 100), (1100, 9, 40)])
+def test_lsq_fp32_swarm_bit_exact(P, N, D, M):
+    from tests.gpu_common import assert_state_equal, same_bits
+    A, b, _ = _problem(M, D, 1, seed=N)
+    with _lsq_swarm(P, A, b, N, 3, "fp32") as s:
+        st0 = s.state()
+        s.step(1)
+        s.step(17)        # a captured graph of 16 + 1
+        st = s.state()
+        _, fit, idx, pos = s.gbest()
+        g64 = s.gbest_f64()
+    ref = O.Swarm(N, D, *LSQ_BOUNDS, W, C12, C12, O.LSQ, 3, lsq=(A, b)).init()
+    np.testing.assert_array_equal(st0["pbest_fit"], ref.pbest_fit)
+    ref.step_sync(18)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+    assert abs(g64 - O.lsq_f64(A, b, pos)) <= 1e-12 * g64
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_lsq_approx_swarm_gbest_is_fp64_verified(P, precision):
+    """pbest follows the approximate fitness; gbest only moves to FP64-verified
+    improvements: its FP64 fitness never increases and equals ||A g - b||^2."""
+    N, D, M = 2000, 96, 640
+    A, b, _ = _problem(M, D, 1, seed=11)
+    with _lsq_swarm(P, A, b, N, 5, precision) as s:
+        prev64 = s.gbest_f64()
+        prev = s.state()
+        for _ in range(6):
+            s.step(3)
+            rc, fit, idx, pos = s.gbest()
+            g64 = s.gbest_f64()
+            st = s.state()
+            assert rc == P.CUPSO_OK
+            assert g64 <= prev64
+            exact = float(np.sum((A.astype(np.float64) @ pos.astype(np.float64) - b.astype(np.float64)) ** 2))
+            assert abs(g64 - exact) <= 1e-9 * exact
+            assert np.float32(g64) == fit
+            np.testing.assert_array_equal(st["pbest_pos"][idx], pos)
+            assert np.all(st["pbest_fit"] <= prev["pbest_fit"])
+            assert np.all(np.abs(st["v"]) <= np.float32(0.4))
+            prev64, prev = g64, st

@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(workloads.CONFIGS) + ["batch512"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(workloads.CONFIGS) + ["batch512", "lsq8192"])
     ap.add_argument("--plain-sample", type=int, default=1,
                     help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
@@ -402,12 +403,95 @@ def run_batch(a):
     print(json.dumps(out), flush=True)
 
 
+# --------------------------------------------------------------------------- #
+# least squares: fitness as a GEMM, FP32 CUDA cores vs BF16 / FP8 tensor cores #
+# --------------------------------------------------------------------------- #
+
+def run_lsq(a):
+    """||A x - b||^2, A 4096 x 1024 ~ N(0, 1/4096), x* ~ U[-1, 1], b = A x* + N(0, 1e-6);
+    N = 8192 particles in [-2, 2]^1024, max_v 0.4, 300 iterations, per precision.
+    Reports the time of the whole run, the final FP64 residual of each precision's
+    gbest, and the tensor-core fitness kernel against the bf16 peak."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2205_01313_gb300 import build as B
+    B.build()
+    from paper_2205_01313_gb300 import cupso as P
+
+    cfg = workloads.lsq_config()
+    N, D, M, T = cfg["N"], cfg["D"], cfg["M"], cfg["iters"]
+    A, b, xs = workloads.lsq_problem(M, D, seed=cfg["seed"])
+    dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    stream = torch.cuda.Stream()
+    x64, res, _, _ = np.linalg.lstsq(A.astype(np.float64), b.astype(np.float64), rcond=None)
+    f_opt = float(res[0])
+    runs = {}
+    for prec in ("bf16", "fp8", "fp32"):
+        with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
+                     stream=stream.cuda_stream) as s:
+            s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(T)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            runs[prec] = {"seconds": ms / 1e3, "ms_per_iter": ms / T, "final_residual_f64": s.gbest_f64(),
+                          "pd_per_s": N * D * T / (ms / 1e3)}
+    # the fitness kernel alone (all particles), timed per launch
+    X = torch.from_numpy(np.random.default_rng(3).uniform(-2, 2, (N, D)).astype(np.float32)).cuda()
+    f = torch.empty(N, dtype=torch.float32, device="cuda")
+    fit_ms = {}
+    for prec, code in (("bf16", 1), ("fp8", 2), ("fp32", 0)):
+        reps = 3 if prec == "fp32" else 10
+        P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, X.data_ptr(), N, code, f.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, X.data_ptr(), N, code, f.data_ptr(),
+                             stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fit_ms[prec] = e0.elapsed_time(e1) / reps
+    flops = 2.0 * N * M * D
+    peak = 1918.5
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = float(json.load(fh)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        pass
+    ref = runs["fp32"]["final_residual_f64"]
+    for prec in runs:
+        runs[prec]["residual_rel_gap_vs_fp32_run"] = abs(runs[prec]["final_residual_f64"] - ref) / ref
+    out = {
+        "metric": METRIC, "value": runs["bf16"]["pd_per_s"], "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": 0,
+        "ms_per_step": runs["bf16"]["ms_per_iter"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 fitness GEMM (fp32 accumulate), f32 state", "data": "synthetic",
+        "config": {"workload": "lsq8192", "N": N, "D": D, "M": M, "iters": T, "bounds": cfg["bounds"],
+                   "lstsq_optimum_f64": f_opt},
+        "runs": runs,
+        "bf16_over_fp32": runs["fp32"]["seconds"] / runs["bf16"]["seconds"],
+        "fp8_over_fp32": runs["fp32"]["seconds"] / runs["fp8"]["seconds"],
+        "fitness_eval_ms": fit_ms,
+        "roofline": {"bound": "tensor", "kernel": "lsq_tc_kernel<bf16> (+ operand conversion)",
+                     "achieved": flops / (fit_ms["bf16"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / (fit_ms["bf16"] / 1e3) / 1e12 / peak, "traffic": None},
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
     elif a.workload == "batch512":
         run_batch(a)
+    elif a.workload == "lsq8192":
+        run_lsq(a)
     else:
         run_ours(a)
 

@@ -79,7 +79,10 @@ struct cupso_swarm {
         unsigned long long* cand = nullptr;
         double* partial = nullptr;
         double* g64 = nullptr;
-        int chunks = 64;
+        unsigned int* flags = nullptr;   // [Np / 4]: improved this iteration (one byte per particle)
+        int chunks = 32;
+        LsqGram gram;                    // FP64 A^T A etc. for the rescoring when D <= M
+        void* gram_buf = nullptr;
     };
     Lsq* lsq = nullptr;
 };
@@ -146,16 +149,17 @@ constexpr int kModeLsq = 100;   // internal: one least-squares iteration
 
 cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
     cupso_swarm::Lsq& L = *h->lsq;
-    const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
+    const int grid = h->num_sms * 8;   // grid-stride over (particle group, dimension) items
     cudaError_t e = lsq_launch_move(h->dev, grid, st);
     if (e != cudaSuccess) return e;
     if (L.precision == CUPSO_LSQ_FP32) {
         e = lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
         if (e != cudaSuccess) return e;
-        return lsq_launch_select_exact(h->dev, L.f, grid, st);
+        return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
     if (lsq_eval_tc(&L.tc, h->dev.x, 1, (size_t)h->Np, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
-    return lsq_launch_gbest_approx(h->dev, L.f, 0, L.A, L.b, L.M, L.cand, L.partial, L.chunks, L.g64, st);
+    return lsq_launch_gbest_approx(h->dev, L.f, 0, L.A, L.b, L.M, L.cand, L.partial, L.chunks, L.g64, L.flags, grid,
+                                   L.gram, st);
 }
 
 cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
@@ -570,6 +574,7 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     if (h->lsq) {
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
+        if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);
         delete h->lsq;
         h->lsq = nullptr;
     }
@@ -582,13 +587,14 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     L->precision = precision;
     const int nblk = tiles_of(h->Np);
     const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256) +
-                         align_up(sizeof(double) * 16 * L->chunks, 256) + 256;
+                         align_up(sizeof(double) * 16 * L->chunks, 256) + align_up((size_t)h->Np, 256) + 256;
     cudaError_t e = cudaMalloc(&L->buf, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (lsq)");
     char* p = static_cast<char*>(L->buf);
     L->f = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * h->Np, 256);
     L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256);
     L->partial = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * 16 * L->chunks, 256);
+    L->flags = reinterpret_cast<unsigned int*>(p); p += align_up((size_t)h->Np, 256);
     L->g64 = reinterpret_cast<double*>(p);
     const double inf = INFINITY;
     CUPSO_CUDA(cudaMemcpyAsync(L->g64, &inf, sizeof(double), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync");
@@ -599,6 +605,20 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         const float sx = xmax > 0.0f ? 448.0f / xmax : 1.0f;
         rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
         if (rc) return rc;
+        if (h->D <= M && (size_t)h->D * h->D <= ((size_t)1 << 26)) {
+            // FP64 Gram data: A^T A, A^T b (device) and b^T b (host, from b)
+            CUPSO_CUDA(cudaMalloc(&L->gram_buf, sizeof(double) * ((size_t)h->D * h->D + h->D)), "cudaMalloc (gram)");
+            L->gram.Gm = static_cast<double*>(L->gram_buf);
+            L->gram.cvec = L->gram.Gm + (size_t)h->D * h->D;
+            CUPSO_CUDA(lsq_launch_gram(A_dev, b_dev, M, h->D, L->gram.Gm, L->gram.cvec, h->stream), "gram launch");
+            std::vector<float> hb((size_t)M);
+            CUPSO_CUDA(cudaMemcpyAsync(hb.data(), b_dev, sizeof(float) * M, cudaMemcpyDeviceToHost, h->stream),
+                       "cudaMemcpyAsync");
+            CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+            double bb = 0.0;
+            for (float v : hb) bb = std::fma((double)v, (double)v, bb);
+            L->gram.bb = bb;
+        }
     }
     // Step 1 completes here: pbest_fit = f(pbest_pos), gbest from it.
     if (precision == CUPSO_LSQ_FP32) {
@@ -612,7 +632,7 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         // the accept kernel advances t: start one below and let it land on t_host
         CUPSO_CUDA(lsq_launch_set_t(h->dev, h->t_host - 1u, h->stream), "lsq t");
         CUPSO_CUDA(lsq_launch_gbest_approx(h->dev, L->f, 1, A_dev, b_dev, M, L->cand, L->partial, L->chunks, L->g64,
-                                           h->stream),
+                                           L->flags, h->num_sms * 8, L->gram, h->stream),
                    "lsq gbest");
     }
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -667,6 +687,7 @@ int cupso_destroy(cupso_handle h) {
     if (h->lsq) {
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
+        if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);
         delete h->lsq;
         h->lsq = nullptr;
     }

@@ -86,11 +86,19 @@ cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* 
 
 // Least-squares swarm iteration (kernels_lsq_swarm.cu); all read t from t_dev.
 cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
-cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, int grid, cudaStream_t st);
+cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
+                                    cudaStream_t st);
 int lsq_cand_blocks(const SwarmDev& s);
+// FP64 Gram data of the rescoring (Gm = A^T A, cvec = A^T b, bb = b^T b); Gm null: direct form.
+struct LsqGram {
+    double* Gm = nullptr;
+    double* cvec = nullptr;
+    double bb = 0.0;
+};
+cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, cudaStream_t st);
 cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all, const float* A, const float* b,
                                     int M, unsigned long long* cand, double* partial, int chunks, double* g64,
-                                    cudaStream_t st);
+                                    unsigned int* flags, int grid, const LsqGram& gram, cudaStream_t st);
 cudaError_t lsq_launch_set_pf(const SwarmDev& s, const float* fit, cudaStream_t st);
 // FP64 fitness of the pbest_pos of the particle in `key`, into *g64; waits.
 cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, int M, unsigned long long key,

@@ -335,6 +335,28 @@ __global__ void convert_operand_kernel(const float* __restrict__ src, size_t si,
     }
 }
 
+// The same conversion from the swarm's dimension-major layout src[k * ld + i]
+// through a shared-memory tile: 64 dimensions x 64 particles per block, read
+// along particles and written along dimensions (BF16 only).
+__global__ void __launch_bounds__(256) convert_dimmajor_bf16_kernel(const float* __restrict__ src, size_t ld, int N,
+                                                                    int D, int Np, int Kp,
+                                                                    __nv_bfloat16* __restrict__ dst) {
+    __shared__ float t[64][65];
+    const int k0 = blockIdx.x * 64, i0 = blockIdx.y * 64;
+    for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+        const int kk = e / 64, ii = e % 64;
+        const int k = k0 + kk, i = i0 + ii;
+        t[kk][ii] = (k < D && i < N) ? src[(size_t)k * ld + i] : 0.0f;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 64 * 32; e += 256) {   // pairs of dimensions
+        const int ii = e / 32, kp = (e % 32) * 2;
+        const int i = i0 + ii, k = k0 + kp;
+        if (i < Np && k < Kp)
+            *reinterpret_cast<__nv_bfloat162*>(dst + (size_t)i * Kp + k) = __floats2bfloat162_rn(t[kp][ii], t[kp + 1][ii]);
+    }
+}
+
 // Plain FP32 least-squares fitness with the oracle's rounding order. Block =
 // 64 particles x all M, in tiles of 64 residual rows; thread (ty, tx) holds a
 // 4 x 4 block of (particle, row) residuals, each a chain of fma over d in
@@ -343,8 +365,8 @@ __global__ void convert_operand_kernel(const float* __restrict__ src, size_t si,
 __global__ void __launch_bounds__(256) lsq_fp32_kernel(const float* __restrict__ x, int ldx, int N, int D,
                                                        const float* __restrict__ A, const float* __restrict__ b, int M,
                                                        float* __restrict__ f) {
-    __shared__ float Xs[32][64 + 4];   // [d][particle]
-    __shared__ float As[32][64 + 4];   // [d][row]
+    __shared__ __align__(16) float Xs[32][64 + 4];   // [d][particle]
+    __shared__ __align__(16) float As[32][64 + 4];   // [d][row]
     __shared__ float Rs[64][64 + 1];   // [particle][row]
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int i0 = blockIdx.x * 64;
@@ -368,11 +390,11 @@ __global__ void __launch_bounds__(256) lsq_fp32_kernel(const float* __restrict__
             __syncthreads();
             const int dn = min(32, D - d0);
             for (int dd = 0; dd < dn; ++dd) {
-                float xv[4], av[4];
-#pragma unroll
-                for (int a = 0; a < 4; ++a) xv[a] = Xs[dd][ty * 4 + a];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) av[c] = As[dd][tx * 4 + c];
+                // rows of 68 floats: every 4-float group is 16-byte aligned
+                const float4 x4 = *reinterpret_cast<const float4*>(&Xs[dd][ty * 4]);
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[dd][tx * 4]);
+                const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+                const float av[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -442,6 +464,11 @@ cudaError_t lsq_prepare() {
 
 cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
                         void* dst, cudaStream_t st) {
+    if (!fp8 && si == 1 && Kp % 64 == 0) {   // dimension-major source: tiled transpose
+        convert_dimmajor_bf16_kernel<<<dim3(Kp / 64, (Np + 63) / 64), 256, 0, st>>>(
+            src, sk, N, D, Np, Kp, reinterpret_cast<__nv_bfloat16*>(dst));
+        return cudaGetLastError();
+    }
     const size_t groups = (size_t)Np * (size_t)(Kp / 4);
     const int grid = (int)std::min<size_t>((groups + 255) / 256, 8192);
     if (fp8) convert_operand_kernel<true><<<grid, 256, 0, st>>>(src, si, sk, N, D, Np, Kp, scale, dst);

@@ -36,38 +36,106 @@ __device__ __forceinline__ unsigned long long my_min4(const unsigned long long k
 
 }  // namespace
 
-// Steps 2 of every particle at iteration t = *t_dev + 1 (no fitness here).
+// Steps 2 of every particle at iteration t = *t_dev + 1 (the fitness is a
+// separate matrix product). No fitness runs along d here, so the work is
+// spread over (4-particle group, dimension pair) items.
 __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant__ SwarmDev s) {
     extern __shared__ float Gs[];
     const uint32_t t_prev = __ldcg(s.t_dev);
+    const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u);
     for (int d = threadIdx.x; d < s.D; d += blockDim.x) Gs[d] = __ldcg(s.G + (size_t)cur * s.D + d);
     __syncthreads();
-    const int ntiles = tiles_of(s.Np);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t i0 = (uint32_t)tile * kTile + threadIdx.x * kPerThread;
-        if (i0 >= (uint32_t)s.Np) continue;
-        float f[4];
-        move4<kLsq>(s, i0, t_prev + 1u, Gs, f);
+    const size_t groups = (size_t)s.Np / 4;
+    const int npairs = (s.D + 1) / 2;
+    const size_t items = groups * (size_t)npairs;
+    const size_t Np = (size_t)s.Np;
+    for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (size_t)gridDim.x * blockDim.x) {
+        const int g = (int)(it / groups);
+        const uint32_t i0 = (uint32_t)(it % groups) * 4u;
+        uint4 r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = philox4x32_10(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.key0, s.key1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = 2 * g + h;
+            if (d >= s.D) break;
+            const size_t off = (size_t)d * Np + i0;
+            float4 X = ld4(s.x + off), V = ld4(s.v + off);
+            const float4 P = ld4(s.pb + off);
+            const float gd = Gs[d];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float xj = lane(X, j), vj = lane(V, j);
+                move_one(xj, vj, lane(P, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
+                set_lane(X, j, xj);
+                set_lane(V, j, vj);
+            }
+            st4(s.x + off, X);
+            st4(s.v + off, V);
+        }
     }
 }
 
-// Steps 4-5 with the exact FP32 fitness f: as in sync_step_kernel.
+// pbest_pos[d][i] = pos[d][i] for every particle flagged as improved (one
+// float4 group of particles per item, all dimensions in parallel).
+__global__ void __launch_bounds__(kBlock) lsq_copy_pbest_kernel(const __grid_constant__ SwarmDev s,
+                                                                const unsigned int* __restrict__ flags) {
+    const size_t groups = (size_t)s.Np / 4;
+    const size_t items = groups * (size_t)s.D;
+    const size_t Np = (size_t)s.Np;
+    for (size_t it = (size_t)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = it % groups;
+        const uint32_t fl = __ldg(flags + q);
+        if (!fl) continue;
+        const size_t off = (it / groups) * Np + 4 * q;
+        const float4 X = ld4(s.x + off);
+        if (fl == 0x01010101u) {
+            st4(s.pb + off, X);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((fl >> (8 * j)) & 1u) s.pb[off + j] = lane(X, j);
+        }
+    }
+}
+
+// Step 4 for every particle: strict improvement of pbest_fit, and the flag
+// that its pbest_pos must become its pos (copied by lsq_copy_pbest_kernel).
+// Returns the improvement mask of the 4 particles at i0.
+__device__ __forceinline__ unsigned lsq_pf4(const SwarmDev& s, uint32_t i0, const float f[4],
+                                            unsigned int* __restrict__ flags) {
+    float4 PF = ld4(s.pf + i0);
+    unsigned mask = 0, fl = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((i0 + j) < (uint32_t)s.N && f[j] < lane(PF, j)) {
+            mask |= 1u << j;
+            fl |= 1u << (8 * j);
+            set_lane(PF, j, f[j]);
+        }
+    }
+    if (mask) st4(s.pf + i0, PF);
+    flags[i0 / 4] = fl;
+    return mask;
+}
+
+// Steps 4-5 with the exact FP32 fitness: strict pbest, then the conditional
+// atomicMin on the packed key (only particles that improved and beat gbest).
 __global__ void __launch_bounds__(kBlock) lsq_select_exact_kernel(const __grid_constant__ SwarmDev s,
-                                                                  const float* __restrict__ fit) {
+                                                                  const float* __restrict__ fit,
+                                                                  unsigned int* __restrict__ flags) {
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
     const unsigned long long K = __ldcg(s.gkey + cur);
     unsigned long long best = kKeyNone;
     bool nan = false;
-    const int ntiles = tiles_of(s.Np);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint32_t i0 = (uint32_t)tile * kTile + threadIdx.x * kPerThread;
-        if (i0 >= (uint32_t)s.Np) continue;
-        float f[4], pf[4];
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < (uint32_t)s.Np / 4; q += gridDim.x * blockDim.x) {
+        const uint32_t i0 = 4 * q;
+        float f[4];
         const float4 F = ld4(fit + i0);
         f[0] = F.x; f[1] = F.y; f[2] = F.z; f[3] = F.w;
-        const unsigned mask = pbest4(s, i0, f, pf);
+        const unsigned mask = lsq_pf4(s, i0, f, flags);
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if (mask & (1u << j)) {
@@ -79,7 +147,22 @@ __global__ void __launch_bounds__(kBlock) lsq_select_exact_kernel(const __grid_c
     best = warp_min_u64(best);
     if ((threadIdx.x & 31) == 0 && best < K) atomicMin(s.gkey + nxt, best);
     if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
-    finish_iteration(s, cur, nxt, t_prev + 1u);
+}
+
+// After the pbest copy: gbest_pos from pbest_pos at the winning index; roll t.
+__global__ void lsq_gather_kernel(const __grid_constant__ SwarmDev s) {
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
+    const unsigned long long knew = __ldcg(s.gkey + nxt);
+    const uint32_t g = (uint32_t)(knew & 0xFFFFFFFFull);
+    if (g < (uint32_t)s.N)
+        for (int d = threadIdx.x; d < s.D; d += blockDim.x)
+            s.G[(size_t)nxt * s.D + d] = __ldcg(s.pb + (size_t)d * s.Np + g);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s.gkey[cur] = knew;
+        *s.t_dev = t_prev + 1u;
+    }
 }
 
 // Step 4 with an approximate fitness, and each block's 16 lowest keys among the
@@ -87,7 +170,8 @@ __global__ void __launch_bounds__(kBlock) lsq_select_exact_kernel(const __grid_c
 // One 1024-particle tile per block; cand[block][16] (kKeyNone where fewer).
 __global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
                                                                  const float* __restrict__ fit, int all,
-                                                                 unsigned long long* __restrict__ cand) {
+                                                                 unsigned long long* __restrict__ cand,
+                                                                 unsigned int* __restrict__ flags) {
     __shared__ unsigned long long red[kBlock / 32];
     const uint32_t i0 = (uint32_t)blockIdx.x * kTile + threadIdx.x * kPerThread;
     unsigned long long k4[4] = {kKeyNone, kKeyNone, kKeyNone, kKeyNone};
@@ -96,7 +180,9 @@ __global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_co
         float f[4], pf[4];
         const float4 F = ld4(fit + i0);
         f[0] = F.x; f[1] = F.y; f[2] = F.z; f[3] = F.w;
-        const unsigned mask = all ? 0u : pbest4(s, i0, f, pf);
+        if (all) flags[i0 / 4] = 0u;
+        const unsigned mask = all ? 0u : lsq_pf4(s, i0, f, flags);
+        (void)pf;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const bool real = (i0 + j) < (uint32_t)s.N;
@@ -162,8 +248,17 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
     double acc = 0.0;   // this warp's rows, in order
     for (int m = m0 + warp; m < m1; m += 8) {
         const float* row = A + (size_t)m * s.D;
-        double p = 0.0;
-        for (int d = lane; d < s.D; d += 32) p = fma((double)row[d], xc[d], p);
+        // four independent chains per lane (d = lane + 32 (4k + j)), summed in a fixed order
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        int d = lane;
+        for (; d + 96 < s.D; d += 128) {
+            p0 = fma((double)row[d], xc[d], p0);
+            p1 = fma((double)row[d + 32], xc[d + 32], p1);
+            p2 = fma((double)row[d + 64], xc[d + 64], p2);
+            p3 = fma((double)row[d + 96], xc[d + 96], p3);
+        }
+        for (; d < s.D; d += 32) p0 = fma((double)row[d], xc[d], p0);
+        double p = (p0 + p1) + (p2 + p3);
         for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xFFFFFFFFu, p, o);
         const double r = p - (double)b[m];
         acc = fma(r, r, acc);
@@ -177,21 +272,127 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
     }
 }
 
+// FP64 Gram form of the rescoring, for D <= M: with Gm = A^T A, c = A^T b,
+// bb = b^T b (all FP64, computed once), f(x) = x^T Gm x - 2 c^T x + bb.
+// Block (group, chunk) handles 4 candidates (group 4g..4g+3) and the rows
+// r of the chunk: partial[cand][chunk] = sum_r x_r ((Gm x)_r - 2 c_r)
+// (+ bb in chunk 0). Rows in order per warp, warps in a fixed order.
+__global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_constant__ SwarmDev s,
+                                                               const double* __restrict__ Gm,
+                                                               const double* __restrict__ cvec, double bb,
+                                                               const unsigned long long* __restrict__ top,
+                                                               int rows_per_chunk, int chunks,
+                                                               double* __restrict__ partial) {
+    extern __shared__ double xg[];            // [4][D]
+    __shared__ double wsum[8][4];
+    const int grp = blockIdx.x, chunk = blockIdx.y;
+    const int D = s.D;
+    bool live[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned long long key = top[grp * 4 + q];
+        live[q] = key != kKeyNone;
+        const uint32_t i = live[q] ? (uint32_t)(key & 0xFFFFFFFFull) : 0u;
+        for (int d = threadIdx.x; d < D; d += blockDim.x)
+            xg[q * D + d] = live[q] ? (double)s.pb[(size_t)d * s.Np + i] : 0.0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = chunk * rows_per_chunk, r1 = min(D, r0 + rows_per_chunk);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // lane 0: this warp's rows, in order
+    for (int r = r0 + warp; r < r1; r += 8) {
+        const double* row = Gm + (size_t)r * D;
+        double y[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int d = lane; d < D; d += 32) {
+            const double g = row[d];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) y[q] = fma(g, xg[q * D + d], y[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double v = y[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+            acc[q] = fma(xg[q * D + r], v - 2.0 * cvec[r], acc[q]);
+        }
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) wsum[warp][q] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int q = threadIdx.x;
+        double tot = chunk == 0 ? bb : 0.0;
+        for (int w = 0; w < 8; ++w) tot += wsum[w][q];
+        partial[(size_t)(grp * 4 + q) * chunks + chunk] =
+            live[q] ? tot : __longlong_as_double(0x7FF8000000000000ll);
+    }
+}
+
+// Gm = A^T A (D x D), cvec = A^T b, in FP64 (one-time setup). 32 x 32 output
+// tile per block, rows of A in order.
+__global__ void __launch_bounds__(256) lsq_gram_kernel(const float* __restrict__ A, const float* __restrict__ b,
+                                                       int M, int D, double* __restrict__ Gm,
+                                                       double* __restrict__ cvec) {
+    __shared__ double ta[32][33], tb[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int m0 = 0; m0 < M; m0 += 32) {
+        for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+            const int mm = e / 32, cc = e % 32;
+            const int m = m0 + mm;
+            ta[mm][cc] = (m < M && r0 + cc < D) ? (double)A[(size_t)m * D + r0 + cc] : 0.0;
+            tb[mm][cc] = (m < M && c0 + cc < D) ? (double)A[(size_t)m * D + c0 + cc] : 0.0;
+        }
+        __syncthreads();
+        for (int mm = 0; mm < 32; ++mm) {
+            const double bv = tb[mm][tx];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] = fma(ta[mm][ty * 4 + k], bv, acc[k]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = r0 + ty * 4 + k, c = c0 + tx;
+        if (r < D && c < D) Gm[(size_t)r * D + c] = acc[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const int r = r0 + threadIdx.x;
+        if (r < D) {
+            double v = 0.0;
+            for (int m = 0; m < M; ++m) v = fma((double)A[(size_t)m * D + r], (double)b[m], v);
+            cvec[r] = v;
+        }
+    }
+}
+
 // Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
-__global__ void lsq_accept_kernel(const __grid_constant__ SwarmDev s, const unsigned long long* __restrict__ top,
-                                  const double* __restrict__ partial, int chunks, double* __restrict__ g64) {
+// Warp c sums candidate c's chunks (in chunk order); thread 0 compares.
+__global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__ SwarmDev s,
+                                                         const unsigned long long* __restrict__ top,
+                                                         const double* __restrict__ partial, int chunks,
+                                                         double* __restrict__ g64) {
+    __shared__ double fsum[kCand];
     __shared__ int s_best;
     __shared__ double s_f;
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < kCand) {
+        double f = 0.0;   // lane l: chunks l, l + 32, ... in order; then a fixed tree
+        for (int h = lane; h < chunks; h += 32) f += partial[(size_t)warp * chunks + h];
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
+        if (lane == 0) fsum[warp] = f;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
         int best = -1;
         double bf = 0.0;
         for (int c = 0; c < kCand; ++c) {
             const unsigned long long k = top[c];
             if (k == kKeyNone) break;
-            double f = 0.0;
-            for (int h = 0; h < chunks; ++h) f += partial[(size_t)c * chunks + h];
+            const double f = fsum[c];
             const int i = (int)(k & 0xFFFFFFFFull);
             if (f == f && (best < 0 || f < bf || (f == bf && i < best))) {
                 best = i;
@@ -245,30 +446,57 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, int grid, cudaStream_t st) {
-    lsq_select_exact_kernel<<<grid, kBlock, 0, st>>>(s, fit);
+cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
+                                    cudaStream_t st) {
+    const int g1 = std::max(1, std::min(grid, (s.Np / 4 + kBlock - 1) / kBlock));
+    lsq_select_exact_kernel<<<g1, kBlock, 0, st>>>(s, fit, flags);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lsq_copy_pbest_kernel<<<grid, kBlock, 0, st>>>(s, flags);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lsq_gather_kernel<<<1, 256, 0, st>>>(s);
     return cudaGetLastError();
 }
 
 int lsq_cand_blocks(const SwarmDev& s) { return tiles_of(s.Np); }
 
-// cand: [blocks * 16] + [16] scratch; partial: [16 * chunks].
+cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec,
+                            cudaStream_t st) {
+    lsq_gram_kernel<<<dim3((D + 31) / 32, (D + 31) / 32), 256, 0, st>>>(A, b, M, D, Gm, cvec);
+    return cudaGetLastError();
+}
+
+// cand: [blocks * 16] + [16] scratch; partial: [16 * chunks]; flags: [Np / 4].
+// With Gm set (D <= M) the rescoring uses the FP64 Gram form.
 cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all, const float* A, const float* b,
                                     int M, unsigned long long* cand, double* partial, int chunks, double* g64,
-                                    cudaStream_t st) {
+                                    unsigned int* flags, int grid, const LsqGram& gram, cudaStream_t st) {
     const int nblk = tiles_of(s.Np);
     unsigned long long* top = cand + (size_t)nblk * kCand;
-    lsq_select_cand_kernel<<<nblk, kBlock, 0, st>>>(s, fit, all, cand);
+    lsq_select_cand_kernel<<<nblk, kBlock, 0, st>>>(s, fit, all, cand, flags);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (!all) {
+        lsq_copy_pbest_kernel<<<grid, kBlock, 0, st>>>(s, flags);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     lsq_merge_cand_kernel<<<1, 1024, 0, st>>>(cand, nblk * kCand, top);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int rows = (M + chunks - 1) / chunks;
-    lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, A, b, M, top, rows, partial);
+    if (gram.Gm) {
+        const int rows = (s.D + chunks - 1) / chunks;
+        lsq_rescore_gram_kernel<<<dim3(kCand / 4, chunks), 256, sizeof(double) * 4 * (size_t)s.D, st>>>(
+            s, gram.Gm, gram.cvec, gram.bb, top, rows, chunks, partial);
+    } else {
+        const int rows = (M + chunks - 1) / chunks;
+        lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, A, b, M, top, rows,
+                                                                                          partial);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    lsq_accept_kernel<<<1, 256, 0, st>>>(s, top, partial, chunks, g64);
+    lsq_accept_kernel<<<1, 512, 0, st>>>(s, top, partial, chunks, g64);
     return cudaGetLastError();
 }
 

@@ -53,3 +53,20 @@ def batch_problems(n_swarms=512, seed=1, n_range=(64, 8192), d_range=(8, 256)):
         out.append({"D": int(Ds[s]), "N": int(Ns[s]), "bounds": BOUNDS[fid], "w": W_STD, "c1": C_STD,
                     "c2": C_STD, "fitness_id": fid, "seed": s + 1, "swarm_id": s})
     return out
+
+
+def lsq_config():
+    """The least-squares workload: N = 8192 particles in [-2, 2]^1024 (max_v
+    0.4), A 4096 x 1024, 300 iterations."""
+    return {"N": 8192, "D": 1024, "M": 4096, "iters": 300, "seed": 1, "bounds": (-2.0, 2.0, 0.4),
+            "w": W_STD, "c1": C_STD, "c2": C_STD}
+
+
+def lsq_problem(M, D, seed=1, noise_std=1e-3):
+    """A ~ N(0, 1/4096) entries (unit-norm columns in expectation at M = 4096),
+    x* ~ U[-1, 1], b = A x* + N(0, noise_std^2)."""
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((M, D)) / 64.0).astype(np.float32)
+    xs = rng.uniform(-1.0, 1.0, D).astype(np.float32)
+    b = (A.astype(np.float64) @ xs.astype(np.float64) + noise_std * rng.standard_normal(M)).astype(np.float32)
+    return A, b, xs

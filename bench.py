@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(workloads.CONFIGS) + ["batch512", "lsq8192"])
+                    choices=sorted(workloads.CONFIGS) + ["batch512", "lsq8192", "modes:sphere_1024x32",
+                                                         "modes:rastrigin_65536x128"])
     ap.add_argument("--plain-sample", type=int, default=1,
                     help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
@@ -441,22 +442,17 @@ def run_lsq(a):
             ms = e0.elapsed_time(e1)
             runs[prec] = {"seconds": ms / 1e3, "ms_per_iter": ms / T, "final_residual_f64": s.gbest_f64(),
                           "pd_per_s": N * D * T / (ms / 1e3)}
-    # the fitness kernel alone (all particles), timed per launch
-    X = torch.from_numpy(np.random.default_rng(3).uniform(-2, 2, (N, D)).astype(np.float32)).cuda()
-    f = torch.empty(N, dtype=torch.float32, device="cuda")
+    # the fitness phase alone (operand conversion + tensor-core GEMM + partial sums),
+    # timed live with CUDA events inside 50 further iterations of each tensor-core swarm
     fit_ms = {}
-    for prec, code in (("bf16", 1), ("fp8", 2), ("fp32", 0)):
-        reps = 3 if prec == "fp32" else 10
-        P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, X.data_ptr(), N, code, f.data_ptr(), stream.cuda_stream)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, X.data_ptr(), N, code, f.data_ptr(),
-                             stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fit_ms[prec] = e0.elapsed_time(e1) / reps
+    for prec in ("bf16", "fp8"):
+        with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
+                     stream=stream.cuda_stream) as s:
+            s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
+            s.step(5)
+            s.set_option(P.CUPSO_OPT_TIME_FITNESS, 1)
+            s.step(50)
+            fit_ms[prec] = s.info()["fitness_ms"]
     flops = 2.0 * N * M * D
     peak = 1918.5
     try:
@@ -477,10 +473,65 @@ def run_lsq(a):
         "bf16_over_fp32": runs["fp32"]["seconds"] / runs["bf16"]["seconds"],
         "fp8_over_fp32": runs["fp32"]["seconds"] / runs["fp8"]["seconds"],
         "fitness_eval_ms": fit_ms,
-        "roofline": {"bound": "tensor", "kernel": "lsq_tc_kernel<bf16> (+ operand conversion)",
+        "roofline": {"bound": "tensor",
+                     "kernel": "fitness phase: operand conversion + lsq_tc_kernel<bf16> + partial sums",
                      "achieved": flops / (fit_ms["bf16"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": flops / (fit_ms["bf16"] / 1e3) / 1e12 / peak, "traffic": None},
     }
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# global-best aggregation compared: the paper's tree reduction vs atomics       #
+# --------------------------------------------------------------------------- #
+
+def run_modes(a, name):
+    """One workload, every aggregation mode, the whole run (all iterations of the
+    workload in one cupso_step call) timed with CUDA events from the same
+    initial swarm: on-chip cluster (if the swarm fits), fused atomic SYNC, the
+    tree-reduction baseline (two kernels per iteration) and its unrolled form,
+    and the asynchronous lock-protected mode."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2205_01313_gb300 import build as B
+    B.build()
+    from paper_2205_01313_gb300 import cupso as P
+
+    cfg = workloads.config(name)
+    N, D, T, fid = cfg["N"], cfg["D"], cfg["iters"], cfg["fitness_id"]
+    stream = torch.cuda.Stream()
+    modes = ["onchip", "sync", "tree", "tree_unrolled", "async"]
+    out_modes = {}
+    for mode in modes:
+        with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], fid, cfg["seed"],
+                     stream=stream.cuda_stream) as s:
+            try:
+                s.set_mode(mode)
+            except P.CupsoError:
+                continue   # on-chip: the swarm does not fit
+            s.step(min(3, T))          # warm-up (compiles graphs, first launches)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(T)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rc, fit, idx, _ = s.gbest()
+            out_modes[mode] = {"seconds": ms / 1e3, "us_per_iter": ms * 1e3 / T,
+                               "pd_per_s": N * D * T / (ms / 1e3), "final_gbest_fit": float(fit), "status": rc}
+    base = out_modes.get("tree", {}).get("seconds")
+    for m in out_modes:
+        if base:
+            out_modes[m]["speedup_vs_tree"] = base / out_modes[m]["seconds"]
+    best = max(out_modes.values(), key=lambda v: v["pd_per_s"])
+    out = {"metric": METRIC, "value": best["pd_per_s"], "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": 3,
+           "ms_per_step": best["us_per_iter"] / 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": name, "N": N, "D": D, "iters": T,
+                      "fitness": workloads.FITNESS_NAMES[fid]},
+           "modes": out_modes}
     print(json.dumps(out), flush=True)
 
 
@@ -492,6 +543,8 @@ def main():
         run_batch(a)
     elif a.workload == "lsq8192":
         run_lsq(a)
+    elif a.workload.startswith("modes:"):
+        run_modes(a, a.workload.split(":", 1)[1])
     else:
         run_ours(a)
 

@@ -83,6 +83,10 @@ struct cupso_swarm {
         int chunks = 32;
         LsqGram gram;                    // FP64 A^T A etc. for the rescoring when D <= M
         void* gram_buf = nullptr;
+        bool time_fitness = false;       // CUPSO_OPT_TIME_FITNESS
+        std::vector<cudaEvent_t> ev;     // pairs around the fitness phase
+        double fitness_ms_sum = 0.0;
+        int fitness_timed = 0;
     };
     Lsq* lsq = nullptr;
 };
@@ -157,7 +161,18 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (L.time_fitness) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, st);
+    }
     if (lsq_eval_tc(&L.tc, h->dev.x, 1, (size_t)h->Np, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
+    if (L.time_fitness) {
+        cudaEventRecord(e1, st);
+        L.ev.push_back(e0);
+        L.ev.push_back(e1);
+    }
     return lsq_launch_gbest_approx(h->dev, L.f, 0, L.A, L.b, L.M, L.cand, L.partial, L.chunks, L.g64, L.flags, grid,
                                    L.gram, st);
 }
@@ -423,6 +438,11 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             h->sync_kernel = (int)value;
             drop_graph(h);
             return CUPSO_OK;
+        case CUPSO_OPT_TIME_FITNESS:
+            if (!h->lsq) return fail(CUPSO_ERR_INVALID_ARG, "timing applies to least-squares swarms after cupso_set_lsq%s");
+            h->lsq->time_fitness = value != 0;
+            drop_graph(h);
+            return CUPSO_OK;
         case CUPSO_OPT_FAULT_HOLD_LOCK:
             h->hold_lock = value ? 1 : 0;
             return CUPSO_OK;
@@ -440,7 +460,7 @@ int cupso_step(cupso_handle h, int iters) {
     if (h->fid == CUPSO_LSQ) {
         if (!h->lsq) return fail(CUPSO_ERR_INVALID_ARG, "least-squares swarm: call cupso_set_lsq first%s");
         int left = iters;
-        const int L = h->graph_chunk;
+        const int L = h->lsq->time_fitness ? 0 : h->graph_chunk;
         if (L > 1 && left >= L) {
             int rc = ensure_graph(h, kModeLsq, L);
             if (rc) return rc;
@@ -572,6 +592,7 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     drop_graph(h);
     if (h->lsq) {
+        for (cudaEvent_t ev : h->lsq->ev) cudaEventDestroy(ev);
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
         if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);
@@ -672,6 +693,28 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     info->async_grid = async_grid(h);
     info->onchip_cluster = h->onchip_cluster;
     info->sync_stages = sync_stages(h);
+    info->fitness_ms = 0.0f;
+    info->fitness_timed = 0;
+    if (h->lsq) {
+        cupso_swarm::Lsq& L = *h->lsq;
+        if (!L.ev.empty()) {
+            CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+            for (size_t k = 0; k + 1 < L.ev.size(); k += 2) {
+                float ms = 0.0f;
+                if (cudaEventElapsedTime(&ms, L.ev[k], L.ev[k + 1]) == cudaSuccess) {
+                    L.fitness_ms_sum += ms;
+                    ++L.fitness_timed;
+                }
+                cudaEventDestroy(L.ev[k]);
+                cudaEventDestroy(L.ev[k + 1]);
+            }
+            L.ev.clear();
+        }
+        if (L.fitness_timed) {
+            info->fitness_ms = (float)(L.fitness_ms_sum / L.fitness_timed);
+            info->fitness_timed = L.fitness_timed;
+        }
+    }
     info->device_bytes = (uint64_t)h->arena_bytes;
     return CUPSO_OK;
 }
@@ -685,6 +728,7 @@ int cupso_destroy(cupso_handle h) {
     }
     drop_graph(h);
     if (h->lsq) {
+        for (cudaEvent_t ev : h->lsq->ev) cudaEventDestroy(ev);
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
         if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);

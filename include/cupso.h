@@ -101,6 +101,8 @@ typedef enum {
     CUPSO_OPT_CLEAR_STATUS = 4,   /* any value: clear the sticky device status                 */
     CUPSO_OPT_GRID = 5,           /* CTAs of the persistent kernels (SYNC/ASYNC); 0 = automatic */
     CUPSO_OPT_SYNC_KERNEL = 6,    /* value: cupso_sync_kernel (which SYNC kernel runs)         */
+    CUPSO_OPT_PARTICLES_PER_THREAD = 8, /* pipelined SYNC kernel: 4, 2, 1, or 0 = automatic (fewer
+                                           for small swarms, so that their units fill the GPU) */
     CUPSO_OPT_TIME_FITNESS = 7,   /* 1: time the fitness phase of least-squares iterations with
                                      CUDA events (no graph capture); 0: off. Read in cupso_info */
     CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
@@ -124,6 +126,7 @@ typedef struct {
     int async_grid;       /* CTAs of the ASYNC launch                */
     int onchip_cluster;   /* CTAs per cluster if ONCHIP fits, else 0 */
     int sync_stages;      /* ring depth of the SYNC kernel in use, 0 = register kernel */
+    int sync_ppt;         /* particles per thread of the pipelined SYNC kernel (0: not in use) */
     float fitness_ms;     /* mean fitness-phase time of the timed LSQ iterations, 0 if none */
     int fitness_timed;    /* how many iterations that mean covers */
     uint64_t device_bytes;/* device memory held by the handle        */

@@ -66,6 +66,7 @@ struct cupso_swarm {
     int grid_override = 0;
     int onchip_cluster = 0;
     int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
+    int ppt_option = 0;             // particles per thread of the pipelined kernel, 0 = automatic
     bool pipelined_ok = false;      // shared-memory limit raised for the pipelined kernels
     bool lazy_pending = false;      // the pipelined step may have left pbest rows unwritten
     // least-squares fitness (fitness_id CUPSO_LSQ), set by cupso_set_lsq
@@ -113,12 +114,24 @@ int sync_stages(const cupso_swarm* h) {
     return (h->pipelined_ok && pipelined_supported(want, h->D)) ? want : 0;
 }
 
+// Particles per thread of the pipelined kernel: 4 when the swarm has enough
+// 128-particle units to keep every resident warp busy twice over, else fewer
+// (more, smaller units).
+int sync_ppt(const cupso_swarm* h) {
+    if (h->ppt_option) return h->ppt_option;
+    const long long resident_warps = (long long)h->num_sms * 16;
+    if ((long long)h->Np >= 128ll * 2 * resident_warps) return 4;
+    if ((long long)h->Np >= 64ll * resident_warps) return 2;
+    return 1;
+}
+
 int sync_grid(const cupso_swarm* h) {
     const int stages = sync_stages(h);
     if (stages) {
-        // persistent: warps pull 128-particle units from a counter
-        const int units = h->Np / 128;
-        const int per_sm = pipelined_blocks_per_sm(stages, h->fid, h->D);
+        // persistent: warps pull units of 32 * ppt particles from a counter
+        const int ppt = sync_ppt(h);
+        const int units = h->Np / (32 * ppt);
+        const int per_sm = pipelined_blocks_per_sm(stages, h->fid, h->D, ppt);
         int g = h->grid_override > 0 ? h->grid_override : h->num_sms * per_sm;
         const int useful = (units + kBlock / 32 - 1) / (kBlock / 32);
         return g < useful ? g : useful;
@@ -182,7 +195,7 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
         case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
             const int stages = sync_stages(h);
-            if (stages) return launch_sync_pipelined(h->dev, h->fid, stages, sync_grid(h), st);
+            if (stages) return launch_sync_pipelined(h->dev, h->fid, stages, sync_ppt(h), sync_grid(h), st);
             return launch_sync_step(h->dev, h->fid, sync_grid(h), st);
         }
         case CUPSO_MODE_TREE: return launch_tree_step(h->dev, h->fid, false, st);
@@ -443,6 +456,12 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             h->lsq->time_fitness = value != 0;
             drop_graph(h);
             return CUPSO_OK;
+        case CUPSO_OPT_PARTICLES_PER_THREAD:
+            if (value != 0 && value != 1 && value != 2 && value != 4)
+                return fail(CUPSO_ERR_INVALID_ARG, "particles per thread must be 0 (automatic), 1, 2 or 4%s");
+            h->ppt_option = (int)value;
+            drop_graph(h);
+            return CUPSO_OK;
         case CUPSO_OPT_FAULT_HOLD_LOCK:
             h->hold_lock = value ? 1 : 0;
             return CUPSO_OK;
@@ -693,6 +712,7 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     info->async_grid = async_grid(h);
     info->onchip_cluster = h->onchip_cluster;
     info->sync_stages = sync_stages(h);
+    info->sync_ppt = sync_stages(h) ? sync_ppt(h) : 0;
     info->fitness_ms = 0.0f;
     info->fitness_timed = 0;
     if (h->lsq) {

@@ -30,8 +30,9 @@ cudaError_t launch_recompute(const SwarmDev& s, uint32_t t, cudaStream_t st);
 // Pipelined fused step (kernels_pipelined.cu): `stages`-deep cp.async ring.
 bool pipelined_supported(int stages, int D);
 cudaError_t prepare_pipelined(int D);   // raise the dynamic shared-memory limit; call outside capture
-int pipelined_blocks_per_sm(int stages, int fid, int D);
-cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int grid, cudaStream_t st);
+// ppt: particles per thread (4, 2 or 1); a warp takes units of 32 * ppt particles.
+int pipelined_blocks_per_sm(int stages, int fid, int D, int ppt);
+cudaError_t launch_sync_pipelined(const SwarmDev& s, int fid, int stages, int ppt, int grid, cudaStream_t st);
 // Write back the pbest rows the pipelined step left pending (lazy pbest) and clear the flags.
 cudaError_t launch_materialize(const SwarmDev& s, int grid, cudaStream_t st);
 

@@ -12,7 +12,8 @@ from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, ora
 
 pytestmark = pytest.mark.gpu
 
-SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "tree", "tree_unrolled", "onchip"]
+SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "sync_ppt1", "sync_ppt2", "tree", "tree_unrolled",
+              "onchip"]
 
 
 @pytest.fixture(scope="module")
@@ -23,7 +24,10 @@ def P():
 def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
     """mode: a cupso mode name, or sync_<kernel> for a given SYNC kernel."""
     s = P.Swarm(D, N, bounds or BOUNDS[fid], w, c1, c2, fid, seed)
-    if mode.startswith("sync_"):
+    if mode.startswith("sync_ppt"):
+        s.set_mode("sync")
+        s.set_option(P.CUPSO_OPT_PARTICLES_PER_THREAD, int(mode[8:]))
+    elif mode.startswith("sync_"):
         s.set_mode("sync")
         s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[mode[5:]])
     else:
@@ -32,7 +36,10 @@ def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
 
 
 def test_sync_kernel_selection(P):
+    with gpu_swarm(P, 3, 1 << 20, 16, 1, "sync") as s:
+        assert s.info()["sync_ppt"] == 4           # a large swarm: 4 particles per thread
     with gpu_swarm(P, 3, 5000, 7, 1, "sync") as s:
+        assert s.info()["sync_ppt"] == 1           # a small one: more, smaller units
         assert s.info()["sync_stages"] == 4
         s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined3"])
         assert s.info()["sync_stages"] == 3
@@ -121,7 +128,7 @@ def test_modes_interchangeable_mid_run(P):
     assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 
 
-@pytest.mark.parametrize("kernel", ["sync_register", "sync_pipelined3", "sync_pipelined4"])
+@pytest.mark.parametrize("kernel", ["sync_register", "sync_pipelined3", "sync_pipelined4", "sync_ppt1", "sync_ppt2"])
 @pytest.mark.parametrize("grid", [1, 2, 5])
 @pytest.mark.parametrize("chunk", [0, 4])
 def test_launch_shape_does_not_change_results(P, grid, chunk, kernel):

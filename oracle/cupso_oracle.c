@@ -419,3 +419,165 @@ int ora_step_serial(const ora_params* p, ora_state* s, int iters, const float* r
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Double precision: the paper's own precision (Sec. 5.1 runs its GPU and    */
+/* CPU versions in FP64). The same steps as above, each one binary64         */
+/* operation rounded to nearest; fma() is the correctly rounded C99 fma.     */
+/* ------------------------------------------------------------------------- */
+
+double ora_u53(uint32_t hi, uint32_t lo)
+{
+    /* 53 random bits: all of hi, the top 21 of lo; (m + 1) 2^-53 is exact. */
+    uint64_t m = ((uint64_t)hi << 21) | (uint64_t)(lo >> 11);
+    return ldexp((double)(m + 1u), -53);
+}
+
+static void draw_words_d(const ora_params_d* p, uint32_t t, int i, int d, uint32_t out[4])
+{
+    uint32_t ctr[4] = {(uint32_t)d, (uint32_t)i, t, p->swarm};
+    uint32_t key[2] = {(uint32_t)(p->seed & 0xFFFFFFFFu), (uint32_t)(p->seed >> 32)};
+    ora_philox4x32_10(ctr, key, out);
+}
+
+void ora_draw_r_d(const ora_params_d* p, uint32_t t, int i, int d, double* r1, double* r2)
+{
+    uint32_t w[4];
+    draw_words_d(p, t, i, d, w);
+    *r1 = ora_u53(w[0], w[1]);
+    *r2 = ora_u53(w[2], w[3]);
+}
+
+double ora_fitness_d(int fitness, const double* x, int D)
+{
+    double acc = 0.0;
+    switch (fitness) {
+    case ORA_SPHERE:
+        for (int d = 0; d < D; ++d) acc = fma(x[d], x[d], acc);
+        return acc;
+    case ORA_ROSENBROCK:
+        for (int d = 0; d + 1 < D; ++d) {
+            double p = fma(-x[d], x[d], x[d + 1]);
+            double q = 1.0 - x[d];
+            acc = acc + fma(100.0 * p, p, q * q);
+        }
+        return acc;
+    case ORA_CUBIC_MAX: /* Eq. 3, maximised: -sum (x^3 - 0.8 x^2 - 1000 x + 8000) */
+        for (int d = 0; d < D; ++d) {
+            double h = fma(fma(x[d] - 0.8, x[d], -1000.0), x[d], 8000.0);
+            acc = acc + h;
+        }
+        return -acc;
+    default:
+        return NAN;
+    }
+}
+
+uint64_t ora_fit_key_d(double f)
+{
+    if (isnan(f)) return ~(uint64_t)0;
+    if (f == 0.0) f = 0.0;
+    uint64_t b;
+    memcpy(&b, &f, 8);
+    return (b >> 63) ? ~b : (b | ((uint64_t)1 << 63));
+}
+
+static double clampd(double a, double lo, double hi)
+{
+    if (isnan(a)) return lo;
+    return a < lo ? lo : (a > hi ? hi : a);
+}
+
+static int check_params_d(const ora_params_d* p)
+{
+    if (p->N <= 0 || p->D <= 0) return -1;
+    if (!(p->min_pos < p->max_pos) || !(p->max_v > 0.0)) return -1;
+    if (p->fitness != ORA_SPHERE && p->fitness != ORA_ROSENBROCK && p->fitness != ORA_CUBIC_MAX) return -1;
+    return 0;
+}
+
+static int better_d(double fa, int64_t ia, double fb, int64_t ib)
+{
+    uint64_t ka = ora_fit_key_d(fa), kb = ora_fit_key_d(fb);
+    if (ka != kb) return ka < kb;
+    return ia < ib;
+}
+
+int64_t ora_argmin_pbest_d(const ora_params_d* p, const ora_state_d* s)
+{
+    int64_t g = 0;
+    for (int64_t i = 1; i < p->N; ++i)
+        if (better_d(s->pbest_fit[i], i, s->pbest_fit[g], g)) g = i;
+    return g;
+}
+
+static void take_gbest_d(const ora_params_d* p, ora_state_d* s, int64_t g)
+{
+    s->gbest_idx = g;
+    s->gbest_fit = s->pbest_fit[g];
+    memcpy(s->gbest_pos, s->pbest_pos + (size_t)g * p->D, sizeof(double) * (size_t)p->D);
+}
+
+int ora_init_d(const ora_params_d* p, ora_state_d* s)
+{
+    if (check_params_d(p)) return -1;
+    const int N = p->N, D = p->D;
+    const double span = p->max_pos - p->min_pos;
+    const double vspan = 2.0 * p->max_v;
+    for (int i = 0; i < N; ++i) {
+        double* pos = s->pos + (size_t)i * D;
+        double* v = s->v + (size_t)i * D;
+        for (int d = 0; d < D; ++d) {
+            uint32_t w[4];
+            draw_words_d(p, 0u, i, d, w);
+            pos[d] = clampd(fma(ora_u53(w[0], w[1]), span, p->min_pos), p->min_pos, p->max_pos);
+            v[d] = clampd(fma(ora_u53(w[2], w[3]), vspan, -p->max_v), -p->max_v, p->max_v);
+        }
+        s->fit[i] = ora_fitness_d(p->fitness, pos, D);
+        s->pbest_fit[i] = s->fit[i];
+        memcpy(s->pbest_pos + (size_t)i * D, pos, sizeof(double) * (size_t)D);
+    }
+    s->t = 0;
+    take_gbest_d(p, s, ora_argmin_pbest_d(p, s));
+    return 0;
+}
+
+double ora_move_one_d(const ora_params_d* p, uint32_t t, int i, double* pos, double* v, double* pbest,
+                      double* pbest_fit, const double* gbest_pos)
+{
+    const int D = p->D;
+    for (int d = 0; d < D; ++d) {
+        double r1, r2;
+        ora_draw_r_d(p, t, i, d, &r1, &r2);
+        /* Eq. 1 */
+        double cognitive = pbest[d] - pos[d];
+        double social = gbest_pos[d] - pos[d];
+        double vel = p->w * v[d];
+        vel = fma(p->c1 * r1, cognitive, vel);
+        vel = fma(p->c2 * r2, social, vel);
+        v[d] = clampd(vel, -p->max_v, p->max_v);
+        /* Eq. 2 */
+        pos[d] = clampd(pos[d] + v[d], p->min_pos, p->max_pos);
+    }
+    double fit = ora_fitness_d(p->fitness, pos, D);  /* Step 3 */
+    if (fit < *pbest_fit) {                          /* Step 4 */
+        *pbest_fit = fit;
+        memcpy(pbest, pos, sizeof(double) * (size_t)D);
+    }
+    return fit;
+}
+
+int ora_step_sync_d(const ora_params_d* p, ora_state_d* s, int iters)
+{
+    if (check_params_d(p) || iters < 0) return -1;
+    const size_t D = (size_t)p->D;
+    for (int k = 0; k < iters; ++k) {
+        uint32_t t = s->t + 1;
+        for (int i = 0; i < p->N; ++i)
+            s->fit[i] = ora_move_one_d(p, t, i, s->pos + i * D, s->v + i * D, s->pbest_pos + i * D,
+                                       &s->pbest_fit[i], s->gbest_pos);
+        take_gbest_d(p, s, ora_argmin_pbest_d(p, s));  /* Step 5 */
+        s->t = t;
+    }
+    return 0;
+}

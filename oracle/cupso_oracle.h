@@ -116,6 +116,54 @@ float ora_move_one(const ora_params* p, uint32_t t, int i, float* pos, float* v,
 /* Lexicographic argmin over (pbest_fit[i], i); NaN ranks last. */
 int64_t ora_argmin_pbest(const ora_params* p, const ora_state* s);
 
+
+/* ------------------------------------------------------------------------- */
+/* Double precision (the paper's own precision, Sec. 5.1: FP64 state and     */
+/* uniforms). Same algorithm as above with every operation in binary64.      */
+/* Fitness: ORA_SPHERE, ORA_ROSENBROCK and ORA_CUBIC_MAX.                    */
+/* ------------------------------------------------------------------------- */
+
+typedef struct {
+    int N, D;
+    double min_pos, max_pos, max_v;
+    double w, c1, c2;
+    int fitness;
+    uint64_t seed;
+    uint32_t swarm;
+} ora_params_d;
+
+typedef struct {
+    double *pos, *v, *pbest_pos;  /* [N][D] */
+    double *pbest_fit, *fit;      /* [N]    */
+    double *gbest_pos;            /* [D]    */
+    double gbest_fit;
+    int64_t gbest_idx;
+    uint32_t t;
+} ora_state_d;
+
+/* Two 32-bit words -> uniform in (0,1] with 53 significant bits:
+ * m = hi * 2^21 + (lo >> 11), u = (m + 1) * 2^-53. */
+double ora_u53(uint32_t hi, uint32_t lo);
+
+/* (r1, r2) of particle i, dimension d, iteration t: one Philox4x32-10 call
+ * with counter (d, i, t, swarm); r1 from words 0,1 and r2 from words 2,3
+ * (at t = 0 the same words give pos0 and v0). */
+void ora_draw_r_d(const ora_params_d* p, uint32_t t, int i, int d, double* r1, double* r2);
+
+/* Fitness of one position in binary64 (same order as the FP32 versions). */
+double ora_fitness_d(int fitness, const double* x, int D);
+
+/* Order-preserving 64-bit key of a binary64 fitness (NaN -> all ones). */
+uint64_t ora_fit_key_d(double f);
+
+int ora_init_d(const ora_params_d* p, ora_state_d* s);
+int ora_step_sync_d(const ora_params_d* p, ora_state_d* s, int iters);
+int64_t ora_argmin_pbest_d(const ora_params_d* p, const ora_state_d* s);
+
+/* Steps 2-4 for ONE particle (global index i, iteration t), in place. */
+double ora_move_one_d(const ora_params_d* p, uint32_t t, int i, double* pos, double* v, double* pbest_pos,
+                      double* pbest_fit, const double* gbest_pos);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,6 +31,19 @@ class _State(C.Structure):
                 ("gbest_fit", C.c_float), ("gbest_idx", C.c_int64), ("t", C.c_uint32)]
 
 
+class _ParamsD(C.Structure):
+    _fields_ = [("N", C.c_int), ("D", C.c_int),
+                ("min_pos", C.c_double), ("max_pos", C.c_double), ("max_v", C.c_double),
+                ("w", C.c_double), ("c1", C.c_double), ("c2", C.c_double),
+                ("fitness", C.c_int), ("seed", C.c_uint64), ("swarm", C.c_uint32)]
+
+
+class _StateD(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("v", C.c_void_p), ("pbest_pos", C.c_void_p),
+                ("pbest_fit", C.c_void_p), ("fit", C.c_void_p), ("gbest_pos", C.c_void_p),
+                ("gbest_fit", C.c_double), ("gbest_idx", C.c_int64), ("t", C.c_uint32)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -65,6 +78,22 @@ def lib():
         L.ora_lsq_f64.restype = C.c_double
         L.ora_argmin_pbest.argtypes = [C.POINTER(_Params), C.POINTER(_State)]
         L.ora_argmin_pbest.restype = C.c_int64
+        f64p = C.POINTER(C.c_double)
+        L.ora_u53.argtypes = [C.c_uint32, C.c_uint32]
+        L.ora_u53.restype = C.c_double
+        L.ora_draw_r_d.argtypes = [C.POINTER(_ParamsD), C.c_uint32, C.c_int, C.c_int, f64p, f64p]
+        L.ora_fitness_d.argtypes = [C.c_int, f64p, C.c_int]
+        L.ora_fitness_d.restype = C.c_double
+        L.ora_fit_key_d.argtypes = [C.c_double]
+        L.ora_fit_key_d.restype = C.c_uint64
+        L.ora_init_d.argtypes = [C.POINTER(_ParamsD), C.POINTER(_StateD)]
+        L.ora_init_d.restype = C.c_int
+        L.ora_step_sync_d.argtypes = [C.POINTER(_ParamsD), C.POINTER(_StateD), C.c_int]
+        L.ora_step_sync_d.restype = C.c_int
+        L.ora_argmin_pbest_d.argtypes = [C.POINTER(_ParamsD), C.POINTER(_StateD)]
+        L.ora_argmin_pbest_d.restype = C.c_int64
+        L.ora_move_one_d.argtypes = [C.POINTER(_ParamsD), C.c_uint32, C.c_int, f64p, f64p, f64p, f64p, f64p]
+        L.ora_move_one_d.restype = C.c_double
         _lib = L
     return _lib
 
@@ -236,3 +265,96 @@ class Swarm:
 
     def argmin_pbest(self):
         return int(lib().ora_argmin_pbest(C.byref(self.p), C.byref(self.s)))
+
+
+# ---------------------------------------------------------------------------
+# Double precision (the paper's precision): sphere, Rosenbrock, cubic.
+# ---------------------------------------------------------------------------
+
+def _f64p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def u53(hi, lo):
+    return float(lib().ora_u53(int(hi) & 0xFFFFFFFF, int(lo) & 0xFFFFFFFF))
+
+
+def fitness_d(fid, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().ora_fitness_d(int(fid), _f64p(x), int(x.shape[-1])))
+
+
+def fit_key_d(f):
+    return int(lib().ora_fit_key_d(float(f)))
+
+
+class Swarm64:
+    """A double-precision swarm as the oracle holds it (state arrays float64, (N, D))."""
+
+    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0):
+        self.p = _ParamsD(int(N), int(D), float(min_pos), float(max_pos), float(max_v), float(w), float(c1),
+                          float(c2), int(fitness), int(seed), int(swarm))
+        self.N, self.D = int(N), int(D)
+        self.pos = np.zeros((N, D), np.float64)
+        self.v = np.zeros((N, D), np.float64)
+        self.pbest_pos = np.zeros((N, D), np.float64)
+        self.pbest_fit = np.zeros(N, np.float64)
+        self.fit = np.zeros(N, np.float64)
+        self.gbest_pos = np.zeros(D, np.float64)
+        self.s = _StateD()
+        s = self.s
+        s.pos, s.v, s.pbest_pos = self.pos.ctypes.data, self.v.ctypes.data, self.pbest_pos.ctypes.data
+        s.pbest_fit, s.fit, s.gbest_pos = self.pbest_fit.ctypes.data, self.fit.ctypes.data, self.gbest_pos.ctypes.data
+
+    @property
+    def t(self):
+        return int(self.s.t)
+
+    @property
+    def gbest_fit(self):
+        return float(self.s.gbest_fit)
+
+    @property
+    def gbest_idx(self):
+        return int(self.s.gbest_idx)
+
+    def init(self):
+        if lib().ora_init_d(C.byref(self.p), C.byref(self.s)) != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def set_state(self, pos, v, pbest_pos, pbest_fit, t):
+        self.pos[...] = pos
+        self.v[...] = v
+        self.pbest_pos[...] = pbest_pos
+        self.pbest_fit[...] = pbest_fit
+        self.s.t = int(t)
+        g = int(lib().ora_argmin_pbest_d(C.byref(self.p), C.byref(self.s)))
+        self.s.gbest_idx = g
+        self.s.gbest_fit = float(self.pbest_fit[g])
+        self.gbest_pos[...] = self.pbest_pos[g]
+        return self
+
+    def step_sync(self, iters=1):
+        if lib().ora_step_sync_d(C.byref(self.p), C.byref(self.s), int(iters)) != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def draw_r(self, t, i, d):
+        r1, r2 = C.c_double(), C.c_double()
+        lib().ora_draw_r_d(C.byref(self.p), int(t), int(i), int(d), C.byref(r1), C.byref(r2))
+        return r1.value, r2.value
+
+    def move_one(self, t, i, pos, v, pbest_pos, pbest_fit, gbest_pos):
+        """Steps 2-4 for one particle at iteration t, on copies: (pos, v, pbest_pos, pbest_fit, fit)."""
+        pos = np.array(pos, np.float64)
+        v = np.array(v, np.float64)
+        pb = np.array(pbest_pos, np.float64)
+        pf = np.array([pbest_fit], np.float64)
+        g = np.ascontiguousarray(gbest_pos, np.float64)
+        f = lib().ora_move_one_d(C.byref(self.p), int(t), int(i), _f64p(pos), _f64p(v), _f64p(pb), _f64p(pf),
+                                 _f64p(g))
+        return pos, v, pb, float(pf[0]), float(f)
+
+    def argmin_pbest(self):
+        return int(lib().ora_argmin_pbest_d(C.byref(self.p), C.byref(self.s)))

@@ -48,10 +48,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(workloads.CONFIGS) + ["batch512", "lsq8192", "modes:sphere_1024x32",
-                                                         "modes:rastrigin_65536x128"])
+                                                         "modes:rastrigin_65536x128", "paper:table2",
+                                                         "paper:table3", "paper:table4"])
     ap.add_argument("--plain-sample", type=int, default=1,
                     help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
-    ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto"])
+    ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto",
+                                                       "queue", "queue_lock"])
     ap.add_argument("--sync-kernel", default="auto", choices=["auto", "register", "pipelined3", "pipelined4"])
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -492,7 +494,8 @@ def run_modes(a, name):
     workload in one cupso_step call) timed with CUDA events from the same
     initial swarm: on-chip cluster (if the swarm fits), fused atomic SYNC, the
     tree-reduction baseline (two kernels per iteration) and its unrolled form,
-    and the asynchronous lock-protected mode."""
+    the paper's queue (Alg. 2) and queue-lock (Alg. 3) designs, and the
+    asynchronous lock-protected mode."""
     import torch
 
     torch.cuda.set_device(0)
@@ -503,7 +506,7 @@ def run_modes(a, name):
     cfg = workloads.config(name)
     N, D, T, fid = cfg["N"], cfg["D"], cfg["iters"], cfg["fitness_id"]
     stream = torch.cuda.Stream()
-    modes = ["onchip", "sync", "tree", "tree_unrolled", "async"]
+    modes = ["onchip", "sync", "tree", "tree_unrolled", "queue", "queue_lock", "async"]
     out_modes = {}
     for mode in modes:
         with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], fid, cfg["seed"],
@@ -537,6 +540,86 @@ def run_modes(a, name):
     print(json.dumps(out), flush=True)
 
 
+def run_paper(a, table):
+    """The paper's own experiments in its precision (FP64): Eq. 3 maximised,
+    w = 1, c1 = c2 = 2, the shapes of Table 2 (1D, N = 32..2048, 100,000
+    iterations; the four GPU designs), Table 3 (queue lock, 1D, N up to
+    131,072) or Table 4 (queue, 120D). Every design the table compares runs as
+    the paper built it (one particle per thread), beside this library's own
+    FP64 paths (the fused SYNC step and, where the swarm fits one CTA, the
+    on-chip kernel). Each run is timed with CUDA events over exactly the
+    table's iteration count after 3 warm-up iterations. The FP64 oracle is
+    timed on a bounded prefix of iterations per row and scaled, as this box's
+    serial baseline. The paper's published seconds (GTX 1080 Ti, Xeon
+    E3-1275 v5) are printed beside them as context."""
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_2205_01313_gb300 import build as B
+    B.build()
+    from paper_2205_01313_gb300 import cupso as P
+    from oracle import oracle as O
+
+    spec = {"table2": workloads.PAPER_TABLE2, "table3": workloads.PAPER_TABLE3,
+            "table4": workloads.PAPER_TABLE4}[table]
+    modes = {"table2": ["tree", "tree_unrolled", "queue", "queue_lock", "sync", "onchip"],
+             "table3": ["queue_lock", "sync", "onchip"],
+             "table4": ["queue", "sync", "onchip"]}[table]
+    S = workloads.PAPER_SETTING
+    D = spec["D"]
+    stream = torch.cuda.Stream()
+    rows = []
+    cpu_total = 0.0
+    for N, paper in spec["rows"].items():
+        cols = dict(zip(spec["columns"], paper))
+        T = int(cols.pop("iters", spec.get("iters", 0)))
+        row = {"N": N, "D": D, "iters": T, "paper_seconds": cols, "seconds": {}, "final_gbest_fit": {}}
+        for mode in modes:
+            with P.Swarm(D, N, S["bounds"], S["w"], S["c1"], S["c2"], S["fitness_id"], S["seed"],
+                         stream=stream.cuda_stream, dtype="f64") as s:
+                try:
+                    s.set_mode(mode)
+                except P.CupsoError:
+                    continue   # on-chip: the swarm does not fit one CTA
+                s.step(3)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                s.step(T)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row["seconds"][mode] = e0.elapsed_time(e1) / 1e3
+                rc, fit, _, _ = s.gbest()
+                row["final_gbest_fit"][mode] = fit if rc == P.CUPSO_OK else "status %d" % rc
+        ours = {m: row["seconds"][m] for m in ("sync", "onchip") if m in row["seconds"]}
+        best_mode = min(ours, key=ours.get)
+        row["ours_best"] = best_mode
+        paper_best_gpu = min(v for k, v in cols.items() if k != "cpu")
+        row["paper_best_gpu_over_ours"] = paper_best_gpu / ours[best_mode]
+        # this box's serial FP64 baseline: a bounded prefix of the same run, scaled
+        k = max(1, min(T, int(2e6 // (N * D))))
+        o = O.Swarm64(N, D, *S["bounds"], S["w"], S["c1"], S["c2"], S["fitness_id"], S["seed"]).init()
+        t0 = time.perf_counter()
+        o.step_sync(k)
+        dt = time.perf_counter() - t0
+        cpu_total += dt
+        row["cpu_oracle_seconds_scaled"] = dt * T / k
+        row["cpu_oracle_sample_iters"] = k
+        rows.append(row)
+    last = rows[-1]
+    best_s = last["seconds"][last["ours_best"]]
+    out = {"metric": METRIC, "value": last["N"] * D * last["iters"] / best_s, "unit": UNIT, "n_gpus": 1,
+           "steps": last["iters"], "warmup": 3, "ms_per_step": best_s * 1e3 / last["iters"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "paper:" + table, "fitness": "cubic_max (Eq. 3, maximised)", "w": S["w"],
+                      "c1": S["c1"], "c2": S["c2"], "bounds": S["bounds"],
+                      "value_is": "particle-dim updates/s of the fastest library mode on the largest row"},
+           "paper_hardware": "GTX 1080 Ti (CUDA 11.2) and one Xeon E3-1275 v5 core, FP64",
+           "cpu_oracle": {"cores": 1, "kind": "oracle (FP64)", "seconds_spent": cpu_total},
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
@@ -547,6 +630,8 @@ def main():
         run_lsq(a)
     elif a.workload.startswith("modes:"):
         run_modes(a, a.workload.split(":", 1)[1])
+    elif a.workload.startswith("paper:"):
+        run_paper(a, a.workload.split(":", 1)[1])
     else:
         run_ours(a)
 

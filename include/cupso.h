@@ -58,6 +58,13 @@ typedef struct {
     float max_v;
 } cupso_bounds;
 
+/* The same search box in double precision (double-precision swarms). */
+typedef struct {
+    double min_pos;
+    double max_pos;
+    double max_v;
+} cupso_bounds_f64;
+
 typedef enum {
     CUPSO_SPHERE = 0,     /* sum x^2                                   */
     CUPSO_RASTRIGIN = 1,  /* 10 D + sum (x^2 - 10 cos 2 pi x)          */
@@ -91,7 +98,13 @@ typedef enum {
     CUPSO_MODE_TREE = 2,   /* parallel-reduction baseline: two kernels per iteration (Sec. 2.2) */
     CUPSO_MODE_TREE_UNROLLED = 3, /* the same with the unrolled reduction (Sec. 2.2)       */
     CUPSO_MODE_ASYNC = 4,  /* persistent CTAs, no grid barrier, lock-protected gbest (Sec. 3.2) */
-    CUPSO_MODE_ONCHIP = 5  /* whole swarm in one CTA cluster's shared memory, many iterations per launch */
+    CUPSO_MODE_ONCHIP = 5, /* whole swarm in one CTA cluster's shared memory, many iterations per launch */
+    CUPSO_MODE_QUEUE = 6,  /* the paper's queue design (Alg. 2): one particle per thread, a
+                              shared-memory queue of the particles that beat gbest, a second kernel */
+    CUPSO_MODE_QUEUE_LOCK = 7 /* the paper's queue-lock design (Alg. 3): the queue, then thread 0 of
+                              each block updates gbest in place under a global lock; one kernel. Blocks
+                              later in the same launch may see an earlier block's update, so with more
+                              than one block (N > 256) the trajectory depends on timing. */
 } cupso_mode;
 
 typedef enum {
@@ -147,11 +160,13 @@ CUPSO_API int cupso_set_stream(cupso_handle h, void* cuda_stream);
 /* Set an option (cupso_option). Unknown keys: CUPSO_ERR_INVALID_ARG. */
 CUPSO_API int cupso_set_option(cupso_handle h, int key, long long value);
 
-/* Queue `iters` >= 0 iterations of Steps 2-5 (Alg. 1). SYNC/TREE/ONCHIP are
- * synchronous PSO: every particle of iteration t uses the gbest from the end
- * of iteration t-1 (Sec. 2.2, "PPSO"), and the result does not depend on the
- * mode or the launch shape. ASYNC lets CTAs run ahead of each other, so its
- * trajectory depends on timing (Sec. 3.2). Does not wait. */
+/* Queue `iters` >= 0 iterations of Steps 2-5 (Alg. 1). SYNC, TREE,
+ * TREE_UNROLLED, QUEUE and ONCHIP are synchronous PSO: every particle of
+ * iteration t uses the gbest from the end of iteration t-1 (Sec. 2.2,
+ * "PPSO"), and the result does not depend on the mode or the launch shape.
+ * ASYNC lets CTAs run ahead of each other, and QUEUE_LOCK updates gbest in
+ * place during an iteration, so their trajectories depend on timing
+ * (Sec. 3.2). Does not wait. */
 CUPSO_API int cupso_step(cupso_handle h, int iters);
 
 /* Wait for the handle's stream, then return gbest: *fit_out = gbest_fit,
@@ -193,6 +208,32 @@ CUPSO_API int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_d
 /* FP64 fitness ||A g - b||^2 of the current gbest_pos g of a least-squares
  * swarm (the residual the precision modes are judged by). Waits. */
 CUPSO_API int cupso_get_gbest_f64(cupso_handle h, double* fit_out);
+
+/* Double-precision swarm: the paper's own precision (Sec. 5.1 runs FP64).
+ * Same algorithm, arguments and conventions as cupso_create, with binary64
+ * state and arithmetic, and 53-bit uniforms: one Philox4x32-10 call per
+ * (dimension, particle, iteration) with counter (d, particle, t, swarm id 0);
+ * words 0,1 give r1 (pos0 at t = 0) and words 2,3 give r2 (v0), each as
+ * (m + 1) 2^-53 with m = w_hi 2^21 + (w_lo >> 11). fitness_id: CUPSO_SPHERE,
+ * CUPSO_ROSENBROCK or CUPSO_CUBIC_MAX (others: CUPSO_ERR_UNSUPPORTED). Modes:
+ * SYNC (one fused launch per iteration: block argmin, a candidate list, the
+ * last block gathers gbest), TREE, TREE_UNROLLED, QUEUE, QUEUE_LOCK (the
+ * paper's four designs, one particle per thread), ONCHIP (one CTA holds the
+ * swarm in shared memory; only when it fits); AUTO picks ONCHIP when it
+ * fits, else SYNC. ASYNC is not available. Use cupso_step, cupso_set_option,
+ * cupso_get_info and cupso_destroy as for any handle, and the _fp64 accessors
+ * below: the float accessors return CUPSO_ERR_UNSUPPORTED on such a handle. */
+CUPSO_API int cupso_create_fp64(int D, int N, const cupso_bounds_f64* bounds, double w, double c1, double c2,
+                                int fitness_id, uint64_t seed, cupso_handle* out);
+
+/* cupso_get_gbest for a double-precision swarm. */
+CUPSO_API int cupso_get_gbest_fp64(cupso_handle h, double* fit_out, double* pos_out, int64_t* idx_out);
+
+/* cupso_get_state / cupso_set_state for a double-precision swarm. */
+CUPSO_API int cupso_get_state_fp64(cupso_handle h, double* pos, double* v, double* pbest_pos, double* pbest_fit,
+                                   uint32_t* t_out);
+CUPSO_API int cupso_set_state_fp64(cupso_handle h, const double* pos, const double* v, const double* pbest_pos,
+                                   const double* pbest_fit, uint32_t t);
 
 /* Fill *info. */
 CUPSO_API int cupso_get_info(cupso_handle h, cupso_info* info);

@@ -2,8 +2,9 @@
 //
 // Host-side control only (Sec. 2.2 splits PSO into host control and device
 // work): argument checks, one device arena per swarm, stream and CUDA-graph
-// management, and the launch of the kernels of kernels_stream.cu and
-// kernels_onchip.cu. Every step of the iteration itself runs on the GPU.
+// management, and the launch of the kernels (kernels_*.cu). A handle holds
+// either a single-precision swarm or a double-precision one (the paper's
+// precision, kernels_paper.cu). Every step of the iteration runs on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,6 +18,7 @@
 #include "../../include/cupso.h"
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "paper_kernels.h"
 
 using namespace cupso;
 
@@ -48,6 +50,10 @@ void cupso::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof
 
 struct cupso_swarm {
     SwarmDev dev{};
+    bool fp64 = false;              // a double-precision swarm: dev64 instead of dev
+    SwarmDev64 dev64{};
+    PaperBufs pbufs{};              // one-particle-per-thread designs (QUEUE, QUEUE_LOCK, FP64 modes)
+    bool onchip64 = false;          // the FP64 swarm fits the on-chip kernel
     int N = 0, D = 0, Np = 0, fid = 0;
     uint64_t seed = 0;
     uint32_t swarm = 0;
@@ -96,6 +102,7 @@ namespace {
 
 int resolved_mode(const cupso_swarm* h) {
     if (h->mode != CUPSO_MODE_AUTO) return h->mode;
+    if (h->fp64) return h->onchip64 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
     return h->onchip_cluster > 0 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
 }
 
@@ -190,7 +197,19 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
                                    L.gram, st);
 }
 
+cudaError_t launch_one64(cupso_swarm* h, int mode, cudaStream_t st) {
+    switch (mode) {
+        case CUPSO_MODE_SYNC: return launch_step64(h->dev64, h->pbufs, h->fid, kAggSyncList, st);
+        case CUPSO_MODE_TREE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduce, st);
+        case CUPSO_MODE_TREE_UNROLLED: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduceUnrolled, st);
+        case CUPSO_MODE_QUEUE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueue, st);
+        case CUPSO_MODE_QUEUE_LOCK: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueueLock, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
+    if (h->fp64) return launch_one64(h, mode, st);
     switch (mode) {
         case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
@@ -200,6 +219,8 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
         }
         case CUPSO_MODE_TREE: return launch_tree_step(h->dev, h->fid, false, st);
         case CUPSO_MODE_TREE_UNROLLED: return launch_tree_step(h->dev, h->fid, true, st);
+        case CUPSO_MODE_QUEUE: return launch_queue_step(h->dev, h->pbufs, h->fid, false, st);
+        case CUPSO_MODE_QUEUE_LOCK: return launch_queue_step(h->dev, h->pbufs, h->fid, true, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -207,7 +228,7 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
 // Before any kernel that reads pbest_pos directly: write back the rows the
 // pipelined step left pending.
 int ensure_materialized(cupso_swarm* h) {
-    if (!h->lazy_pending) return CUPSO_OK;
+    if (h->fp64 || !h->lazy_pending) return CUPSO_OK;
     const int grid = std::max(1, std::min(h->num_sms * 8, (h->Np / 4 + kBlock - 1) / kBlock));
     cudaError_t e = launch_materialize(h->dev, grid, h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "materialize launch");
@@ -302,6 +323,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     const size_t o_aux = off; off = align_up(off + sizeof(unsigned long long) * ntiles, A);
     const size_t o_flag = off; off = align_up(off + (size_t)h->Np, A);
     const size_t o_words = off; off = align_up(off + 128, A);
+    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np), A);
     h->arena_bytes = off;
     e = cudaMalloc(&h->arena, h->arena_bytes);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
@@ -339,6 +361,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.key1 = (uint32_t)(seed >> 32);
     s.swarm = swarm;
     s.wait_limit_ns = 2000000000ll;
+    h->pbufs = paper_bufs_at(base + o_paper, h->Np);
     // c * 2^-24 is exact unless it would be subnormal; check by scaling back.
     s.c1s = std::ldexp(c1, -24);
     s.c2s = std::ldexp(c2, -24);
@@ -355,9 +378,107 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.pflag, 0, (size_t)h->Np, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np), h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
     const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
     e = launch_init(s, fid, grid, h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "init launch"));
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "init"));
+    *out = h;
+    return CUPSO_OK;
+}
+
+// A double-precision swarm: arena x, v, pb [D][Np], pf [Np], G [2][D]
+// (binary64), gbest keys, counters, and the working storage of the
+// one-particle-per-thread kernels.
+int create_swarm64(int D, int N, const cupso_bounds_f64* b, double w, double c1, double c2, int fid, uint64_t seed,
+                   cupso_handle* out) {
+    if (!out) return fail(CUPSO_ERR_INVALID_ARG, "out is NULL%s");
+    *out = nullptr;
+    if (D < 1 || N < 1) return fail(CUPSO_ERR_INVALID_ARG, "D and N must be >= 1%s");
+    if ((long long)N > (long long)0x7FFFFFFF - kPad) return fail(CUPSO_ERR_INVALID_ARG, "N too large%s");
+    const long long Npl = ((long long)N + kPad - 1) / kPad * kPad;
+    if (Npl * (long long)D >= (1ll << 31)) return fail(CUPSO_ERR_INVALID_ARG, "N * D must be < 2^31%s");
+    if (!b) return fail(CUPSO_ERR_INVALID_ARG, "bounds is NULL%s");
+    if (!std::isfinite(b->min_pos) || !std::isfinite(b->max_pos) || !std::isfinite(b->max_v))
+        return fail(CUPSO_ERR_INVALID_ARG, "bounds must be finite%s");
+    if (!(b->min_pos < b->max_pos)) return fail(CUPSO_ERR_INVALID_ARG, "min_pos must be < max_pos%s");
+    if (!(b->max_v > 0.0)) return fail(CUPSO_ERR_INVALID_ARG, "max_v must be > 0%s");
+    if (!std::isfinite(w) || !std::isfinite(c1) || !std::isfinite(c2))
+        return fail(CUPSO_ERR_INVALID_ARG, "w, c1, c2 must be finite%s");
+    if (fid < CUPSO_SPHERE || fid > CUPSO_LSQ) return fail(CUPSO_ERR_INVALID_ARG, "unknown fitness_id%s");
+    if (!fp64_fitness_supported(fid))
+        return fail(CUPSO_ERR_UNSUPPORTED, "double precision supports sphere, Rosenbrock and the cubic%s");
+    cupso_swarm* h = new (std::nothrow) cupso_swarm();
+    if (!h) return fail(CUPSO_ERR_OOM, "host allocation failed%s");
+    h->fp64 = true;
+    h->N = N;
+    h->D = D;
+    h->Np = (int)Npl;
+    h->fid = fid;
+    h->seed = seed;
+    auto bail = [&](int code) {
+        cupso_destroy(h);
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+    e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaStreamCreate"));
+    h->stream = h->own;
+
+    const size_t A = 256;
+    const size_t plane = sizeof(double) * (size_t)D * (size_t)h->Np;
+    size_t off = 0;
+    const size_t o_x = off; off = align_up(off + plane, A);
+    const size_t o_v = off; off = align_up(off + plane, A);
+    const size_t o_pb = off; off = align_up(off + plane, A);
+    const size_t o_pf = off; off = align_up(off + sizeof(double) * (size_t)h->Np, A);
+    const size_t o_G = off; off = align_up(off + sizeof(double) * 2 * (size_t)D, A);
+    const size_t o_key = off; off = align_up(off + 2 * sizeof(PKey), A);
+    const size_t o_words = off; off = align_up(off + 64, A);
+    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np), A);
+    h->arena_bytes = off;
+    e = cudaMalloc(&h->arena, h->arena_bytes);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
+    char* base = static_cast<char*>(h->arena);
+    SwarmDev64& s = h->dev64;
+    s.x = reinterpret_cast<double*>(base + o_x);
+    s.v = reinterpret_cast<double*>(base + o_v);
+    s.pb = reinterpret_cast<double*>(base + o_pb);
+    s.pf = reinterpret_cast<double*>(base + o_pf);
+    s.G = reinterpret_cast<double*>(base + o_G);
+    s.gkey = reinterpret_cast<PKey*>(base + o_key);
+    unsigned int* w32 = reinterpret_cast<unsigned int*>(base + o_words);
+    s.t_dev = w32 + 0;
+    s.status = w32 + 1;
+    s.N = N;
+    s.D = D;
+    s.Np = h->Np;
+    s.lo = b->min_pos;
+    s.hi = b->max_pos;
+    s.vmax = b->max_v;
+    s.w = w;
+    s.c1 = c1;
+    s.c2 = c2;
+    s.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
+    s.key1 = (uint32_t)(seed >> 32);
+    s.swarm = 0u;
+    s.wait_limit_ns = 2000000000ll;
+    h->dev.wait_limit_ns = s.wait_limit_ns;
+    h->dev.status = s.status;
+    h->pbufs = paper_bufs_at(base + o_paper, h->Np);
+    h->onchip64 = onchip64_fits(N, D) && prepare_onchip64() == cudaSuccess;
+    cudaGetLastError();
+
+    e = cudaMemsetAsync(base + o_words, 0, 64, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(PKey), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np), h->stream);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
+    e = launch_init64(s, h->pbufs, fid, h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "init launch"));
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "init"));
@@ -376,6 +497,14 @@ int status_code(unsigned st) {
     if (st & kStatusTimeout) return CUPSO_ERR_DEVICE_TIMEOUT;
     if (st & kStatusNaN) return CUPSO_ERR_NAN;
     return CUPSO_OK;
+}
+
+double key_to_fit64(unsigned long long key) {
+    if (key == ~0ull) return NAN;
+    const unsigned long long bits = (key >> 63) ? (key & 0x7FFFFFFFFFFFFFFFull) : ~key;
+    double f;
+    std::memcpy(&f, &bits, 8);
+    return f;
 }
 
 float key_to_fit(unsigned long long key) {
@@ -419,8 +548,16 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
     switch (key) {
         case CUPSO_OPT_MODE:
-            if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_ONCHIP)
+            if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_QUEUE_LOCK)
                 return fail(CUPSO_ERR_INVALID_ARG, "unknown mode%s");
+            if (h->fp64) {
+                if (value == CUPSO_MODE_ASYNC)
+                    return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarms have no ASYNC mode%s");
+                if (value == CUPSO_MODE_ONCHIP && !h->onchip64)
+                    return fail(CUPSO_ERR_UNSUPPORTED, "swarm does not fit in one CTA's shared memory%s");
+                h->mode = (int)value;
+                return CUPSO_OK;
+            }
             if (h->fid == CUPSO_LSQ && value != CUPSO_MODE_AUTO && value != CUPSO_MODE_SYNC)
                 return fail(CUPSO_ERR_UNSUPPORTED, "least-squares swarms run the synchronous iteration only%s");
             if (value == CUPSO_MODE_ONCHIP && h->onchip_cluster == 0)
@@ -435,6 +572,7 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
         case CUPSO_OPT_WAIT_LIMIT_NS:
             if (value < 1000 || value > 60000000000ll) return fail(CUPSO_ERR_INVALID_ARG, "wait limit out of range%s");
             h->dev.wait_limit_ns = value;
+            h->dev64.wait_limit_ns = value;
             drop_graph(h);
             return CUPSO_OK;
         case CUPSO_OPT_CLEAR_STATUS:
@@ -497,7 +635,13 @@ int cupso_step(cupso_handle h, int iters) {
         return CUPSO_OK;
     }
     const int mode = resolved_mode(h);
-    const bool pipelined = mode == CUPSO_MODE_SYNC && sync_stages(h) > 0;
+    if (h->fp64 && mode == CUPSO_MODE_ONCHIP) {
+        cudaError_t e = launch_onchip64(h->dev64, h->fid, iters, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "on-chip launch");
+        h->t_host += (uint32_t)iters;
+        return CUPSO_OK;
+    }
+    const bool pipelined = !h->fp64 && mode == CUPSO_MODE_SYNC && sync_stages(h) > 0;
     if (!pipelined) {
         const int rc = ensure_materialized(h);
         if (rc) return rc;
@@ -534,6 +678,7 @@ int cupso_step(cupso_handle h, int iters) {
 
 int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx_out) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     const int cur = (int)(h->t_host & 1u);
     unsigned long long key = 0;
     unsigned st = 0;
@@ -554,6 +699,7 @@ int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx
 
 int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, float* pbest_fit, uint32_t* t_out) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
     std::vector<float> stage;
     float* outs[3] = {pos, v, pbest_pos};
@@ -577,6 +723,7 @@ int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, floa
 int cupso_set_state(cupso_handle h, const float* pos, const float* v, const float* pbest_pos,
                     const float* pbest_fit, uint32_t t) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     if (!pos || !v || !pbest_pos || !pbest_fit) return fail(CUPSO_ERR_INVALID_ARG, "state array is NULL%s");
     const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
@@ -601,6 +748,7 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
 
 int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M, int precision) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     if (h->fid != CUPSO_LSQ) return fail(CUPSO_ERR_INVALID_ARG, "swarm was not created with CUPSO_LSQ%s");
     if (!A_dev || !b_dev || M < 1) return fail(CUPSO_ERR_INVALID_ARG, "A, b must be device arrays and M >= 1%s");
     if (precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP8) return fail(CUPSO_ERR_INVALID_ARG, "unknown precision%s");
@@ -701,6 +849,79 @@ int cupso_get_gbest_f64(cupso_handle h, double* fit_out) {
     return CUPSO_OK;
 }
 
+int cupso_create_fp64(int D, int N, const cupso_bounds_f64* bounds, double w, double c1, double c2, int fitness_id,
+                      uint64_t seed, cupso_handle* out) {
+    return create_swarm64(D, N, bounds, w, c1, c2, fitness_id, seed, out);
+}
+
+int cupso_get_gbest_fp64(cupso_handle h, double* fit_out, double* pos_out, int64_t* idx_out) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (!h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "not a double-precision swarm%s");
+    const int cur = (int)(h->t_host & 1u);
+    PKey key{};
+    unsigned st = 0;
+    CUPSO_CUDA(cudaMemcpyAsync(&key, h->dev64.gkey + cur, sizeof(key), cudaMemcpyDeviceToHost, h->stream),
+               "cudaMemcpyAsync");
+    if (pos_out)
+        CUPSO_CUDA(cudaMemcpyAsync(pos_out, h->dev64.G + (size_t)cur * h->D, sizeof(double) * (size_t)h->D,
+                                   cudaMemcpyDeviceToHost, h->stream),
+                   "cudaMemcpyAsync");
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (fit_out) *fit_out = key_to_fit64(key.k);
+    if (idx_out) *idx_out = (int64_t)key.i;
+    rc = status_code(st);
+    if (rc) fail(rc, "device status set: %s", cupso_status_string(rc));
+    return rc;
+}
+
+int cupso_get_state_fp64(cupso_handle h, double* pos, double* v, double* pbest_pos, double* pbest_fit,
+                         uint32_t* t_out) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (!h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "not a double-precision swarm%s");
+    const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
+    std::vector<double> stage;
+    double* outs[3] = {pos, v, pbest_pos};
+    const double* srcs[3] = {h->dev64.x, h->dev64.v, h->dev64.pb};
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    for (int a = 0; a < 3; ++a) {
+        if (!outs[a]) continue;
+        stage.resize(D * Np);
+        CUPSO_CUDA(cudaMemcpy(stage.data(), srcs[a], sizeof(double) * D * Np, cudaMemcpyDeviceToHost), "cudaMemcpy");
+        for (size_t i = 0; i < N; ++i)
+            for (size_t d = 0; d < D; ++d) outs[a][i * D + d] = stage[d * Np + i];
+    }
+    if (pbest_fit)
+        CUPSO_CUDA(cudaMemcpy(pbest_fit, h->dev64.pf, sizeof(double) * N, cudaMemcpyDeviceToHost), "cudaMemcpy");
+    if (t_out) *t_out = h->t_host;
+    return CUPSO_OK;
+}
+
+int cupso_set_state_fp64(cupso_handle h, const double* pos, const double* v, const double* pbest_pos,
+                         const double* pbest_fit, uint32_t t) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (!h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "not a double-precision swarm%s");
+    if (!pos || !v || !pbest_pos || !pbest_fit) return fail(CUPSO_ERR_INVALID_ARG, "state array is NULL%s");
+    const size_t N = (size_t)h->N, D = (size_t)h->D, Np = (size_t)h->Np;
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    std::vector<double> stage(D * Np, 0.0);
+    const double* ins[3] = {pos, v, pbest_pos};
+    double* dsts[3] = {h->dev64.x, h->dev64.v, h->dev64.pb};
+    for (int a = 0; a < 3; ++a) {
+        for (size_t i = 0; i < N; ++i)
+            for (size_t d = 0; d < D; ++d) stage[d * Np + i] = ins[a][i * D + d];
+        CUPSO_CUDA(cudaMemcpy(dsts[a], stage.data(), sizeof(double) * D * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
+    }
+    std::vector<double> pf(Np, INFINITY);
+    std::memcpy(pf.data(), pbest_fit, sizeof(double) * N);
+    CUPSO_CUDA(cudaMemcpy(h->dev64.pf, pf.data(), sizeof(double) * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
+    CUPSO_CUDA(cudaMemcpy(h->dev64.t_dev, &t, sizeof(t), cudaMemcpyHostToDevice), "cudaMemcpy");
+    CUPSO_CUDA(launch_recompute64(h->dev64, h->pbufs, h->stream), "recompute launch");
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    h->t_host = t;
+    return CUPSO_OK;
+}
+
 int cupso_get_info(cupso_handle h, cupso_info* info) {
     if (!h || !info) return fail(CUPSO_ERR_INVALID_ARG, "NULL argument%s");
     info->N = h->N;
@@ -708,11 +929,19 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     info->Np = h->Np;
     info->mode = resolved_mode(h);
     info->t = h->t_host;
-    info->sync_grid = sync_grid(h);
-    info->async_grid = async_grid(h);
-    info->onchip_cluster = h->onchip_cluster;
-    info->sync_stages = sync_stages(h);
-    info->sync_ppt = sync_stages(h) ? sync_ppt(h) : 0;
+    if (h->fp64) {
+        info->sync_grid = paper_blocks(h->N);
+        info->async_grid = 0;
+        info->onchip_cluster = h->onchip64 ? 1 : 0;
+        info->sync_stages = 0;
+        info->sync_ppt = 0;
+    } else {
+        info->sync_grid = sync_grid(h);
+        info->async_grid = async_grid(h);
+        info->onchip_cluster = h->onchip_cluster;
+        info->sync_stages = sync_stages(h);
+        info->sync_ppt = sync_stages(h) ? sync_ppt(h) : 0;
+    }
     info->fitness_ms = 0.0f;
     info->fitness_timed = 0;
     if (h->lsq) {

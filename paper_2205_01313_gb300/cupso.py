@@ -24,8 +24,9 @@ CUPSO_ERR_DEVICE_TIMEOUT = -4
 CUPSO_ERR_NAN = -5
 CUPSO_ERR_UNSUPPORTED = -6
 
-CUPSO_MODE_AUTO, CUPSO_MODE_SYNC, CUPSO_MODE_TREE, CUPSO_MODE_TREE_UNROLLED, CUPSO_MODE_ASYNC, CUPSO_MODE_ONCHIP = range(6)
-MODES = {"auto": 0, "sync": 1, "tree": 2, "tree_unrolled": 3, "async": 4, "onchip": 5}
+(CUPSO_MODE_AUTO, CUPSO_MODE_SYNC, CUPSO_MODE_TREE, CUPSO_MODE_TREE_UNROLLED, CUPSO_MODE_ASYNC, CUPSO_MODE_ONCHIP,
+ CUPSO_MODE_QUEUE, CUPSO_MODE_QUEUE_LOCK) = range(8)
+MODES = {"auto": 0, "sync": 1, "tree": 2, "tree_unrolled": 3, "async": 4, "onchip": 5, "queue": 6, "queue_lock": 7}
 
 CUPSO_OPT_MODE = 1
 CUPSO_OPT_GRAPH_CHUNK = 2
@@ -42,7 +43,8 @@ CUPSO_OPT_FAULT_HOLD_LOCK = 100
 ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_step", "cupso_get_gbest",
                  "cupso_get_state", "cupso_set_state", "cupso_get_info", "cupso_solve_batch", "cupso_destroy",
                  "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc", "cupso_lsq_eval",
-                 "cupso_set_lsq", "cupso_get_gbest_f64")
+                 "cupso_set_lsq", "cupso_get_gbest_f64", "cupso_create_fp64", "cupso_get_gbest_fp64",
+                 "cupso_get_state_fp64", "cupso_set_state_fp64")
 
 CUPSO_LSQ = 5
 CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8 = 0, 1, 2
@@ -54,6 +56,10 @@ CUPSO_NOALLOC_MAX_D = 1024
 
 class cupso_bounds(C.Structure):
     _fields_ = [("min_pos", C.c_float), ("max_pos", C.c_float), ("max_v", C.c_float)]
+
+
+class cupso_bounds_f64(C.Structure):
+    _fields_ = [("min_pos", C.c_double), ("max_pos", C.c_double), ("max_v", C.c_double)]
 
 
 class cupso_info(C.Structure):
@@ -105,6 +111,12 @@ def _load():
                                  C.c_void_p, C.c_void_p]
     L.cupso_set_lsq.argtypes = [h, C.c_void_p, C.c_void_p, C.c_int, C.c_int]
     L.cupso_get_gbest_f64.argtypes = [h, C.POINTER(C.c_double)]
+    f64p = C.POINTER(C.c_double)
+    L.cupso_create_fp64.argtypes = [C.c_int, C.c_int, C.POINTER(cupso_bounds_f64), C.c_double, C.c_double,
+                                    C.c_double, C.c_int, C.c_uint64, C.POINTER(h)]
+    L.cupso_get_gbest_fp64.argtypes = [h, f64p, f64p, C.POINTER(C.c_int64)]
+    L.cupso_get_state_fp64.argtypes = [h, f64p, f64p, f64p, f64p, C.POINTER(C.c_uint32)]
+    L.cupso_set_state_fp64.argtypes = [h, f64p, f64p, f64p, f64p, C.c_uint32]
     L.cupso_destroy.argtypes = [h]
     L.cupso_status_string.argtypes = [C.c_int]
     L.cupso_status_string.restype = C.c_char_p
@@ -253,6 +265,45 @@ def cupso_get_gbest_f64(h):
     return float(v.value)
 
 
+def _f64p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def cupso_create_fp64(D, N, bounds, w, c1, c2, fitness_id, seed):
+    """Create a double-precision swarm and initialise it on the device."""
+    h = C.c_void_p()
+    lo, hi, vmax = bounds
+    b = cupso_bounds_f64(float(lo), float(hi), float(vmax))
+    _check(_lib.cupso_create_fp64(int(D), int(N), C.byref(b), float(w), float(c1), float(c2), int(fitness_id),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, C.byref(h)), "cupso_create_fp64")
+    return h
+
+
+def cupso_get_gbest_fp64(h, D, pos_out=None):
+    """Returns (status, fit, idx, pos) of a double-precision swarm (as cupso_get_gbest)."""
+    pos = pos_out if pos_out is not None else np.empty(int(D), np.float64)
+    fit = C.c_double()
+    idx = C.c_int64()
+    rc = _lib.cupso_get_gbest_fp64(h, C.byref(fit), _f64p(pos), C.byref(idx))
+    if rc not in (CUPSO_OK, CUPSO_ERR_DEVICE_TIMEOUT, CUPSO_ERR_NAN):
+        raise CupsoError(rc, "cupso_get_gbest_fp64")
+    return rc, float(fit.value), int(idx.value), pos
+
+
+def cupso_get_state_fp64(h, N, D):
+    pos, v, pb = (np.empty((N, D), np.float64) for _ in range(3))
+    pf = np.empty(N, np.float64)
+    t = C.c_uint32()
+    _check(_lib.cupso_get_state_fp64(h, _f64p(pos), _f64p(v), _f64p(pb), _f64p(pf), C.byref(t)),
+           "cupso_get_state_fp64")
+    return {"pos": pos, "v": v, "pbest_pos": pb, "pbest_fit": pf, "t": int(t.value)}
+
+
+def cupso_set_state_fp64(h, pos, v, pbest_pos, pbest_fit, t):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (pos, v, pbest_pos, pbest_fit)]
+    _check(_lib.cupso_set_state_fp64(h, *[_f64p(a) for a in arrs], int(t)), "cupso_set_state_fp64")
+
+
 def cupso_destroy(h):
     if h is not None and h.value:
         _check(_lib.cupso_destroy(h), "cupso_destroy")
@@ -262,10 +313,14 @@ def cupso_destroy(h):
 class Swarm:
     """Owning wrapper of one handle (marshalling only)."""
 
-    def __init__(self, D, N, bounds, w, c1, c2, fitness, seed, mode=None, stream=None):
+    def __init__(self, D, N, bounds, w, c1, c2, fitness, seed, mode=None, stream=None, dtype="f32"):
+        """dtype "f32" (cupso_create) or "f64" (cupso_create_fp64, the paper's precision)."""
         fid = FITNESS[fitness] if isinstance(fitness, str) else int(fitness)
         self.D, self.N = int(D), int(N)
-        self.h = cupso_create(D, N, bounds, w, c1, c2, fid, seed)
+        self.fp64 = dtype == "f64"
+        if dtype not in ("f32", "f64"):
+            raise ValueError("dtype must be 'f32' or 'f64'")
+        self.h = (cupso_create_fp64 if self.fp64 else cupso_create)(D, N, bounds, w, c1, c2, fid, seed)
         if stream is not None:
             cupso_set_stream(self.h, stream)
         if mode is not None:
@@ -284,13 +339,20 @@ class Swarm:
         cupso_step(self.h, iters)
 
     def gbest(self):
+        if self.fp64:
+            return cupso_get_gbest_fp64(self.h, self.D)
         return cupso_get_gbest(self.h, self.D)
 
     def state(self):
+        if self.fp64:
+            return cupso_get_state_fp64(self.h, self.N, self.D)
         return cupso_get_state(self.h, self.N, self.D)
 
     def set_state(self, pos, v, pbest_pos, pbest_fit, t):
-        cupso_set_state(self.h, pos, v, pbest_pos, pbest_fit, t)
+        if self.fp64:
+            cupso_set_state_fp64(self.h, pos, v, pbest_pos, pbest_fit, t)
+        else:
+            cupso_set_state(self.h, pos, v, pbest_pos, pbest_fit, t)
 
     def info(self):
         return cupso_get_info(self.h)

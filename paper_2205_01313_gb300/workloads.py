@@ -70,3 +70,41 @@ def lsq_problem(M, D, seed=1, noise_std=1e-3):
     xs = rng.uniform(-1.0, 1.0, D).astype(np.float32)
     b = (A.astype(np.float64) @ xs.astype(np.float64) + noise_std * rng.standard_normal(M)).astype(np.float32)
     return A, b, xs
+
+
+# ---------------------------------------------------------------------------
+# The paper's own experiments (Sec. 5.1): Eq. 3 maximised on [-100, 100] in
+# FP64 with w = 1 and c1 = c2 = 2. max_v is not given; 0.1 (max - min) = 20 as
+# for the other workloads. The published times (seconds, GTX 1080 Ti and a
+# serial Xeon E3-1275 v5 run, FP64) are kept beside each shape as context.
+# ---------------------------------------------------------------------------
+PAPER_SETTING = {"fitness_id": 4, "bounds": (-100.0, 100.0, 20.0), "w": 1.0, "c1": 2.0, "c2": 2.0, "seed": 1}
+
+# Table 2: 1D, 100,000 iterations; columns CPU, reduction, loop unrolling, queue, queue lock.
+PAPER_TABLE2 = {
+    "D": 1, "iters": 100000,
+    "columns": ("cpu", "tree", "tree_unrolled", "queue", "queue_lock"),
+    "rows": {32: (0.100, 0.413, 0.394, 0.368, 0.216), 64: (0.187, 0.419, 0.402, 0.368, 0.219),
+             128: (0.385, 0.447, 0.408, 0.371, 0.220), 256: (0.825, 0.455, 0.419, 0.371, 0.222),
+             512: (1.503, 0.467, 0.422, 0.391, 0.223), 1024: (3.042, 0.491, 0.439, 0.394, 0.227),
+             2048: (6.277, 0.508, 0.451, 0.409, 0.230)},
+}
+
+# Table 3: queue lock vs CPU, 1D, 100,000 iterations.
+PAPER_TABLE3 = {
+    "D": 1, "iters": 100000,
+    "columns": ("cpu", "queue_lock"),
+    "rows": {128: (0.385, 0.220), 256: (0.825, 0.222), 512: (1.503, 0.223), 1024: (3.042, 0.227),
+             2048: (6.277, 0.230), 4096: (12.410, 0.265), 8192: (23.850, 0.316), 16384: (47.355, 0.417),
+             32768: (94.629, 0.643), 65536: (200.536, 1.026), 131072: (378.671, 2.759)},
+}
+
+# Table 4: queue vs CPU, 120D; (iterations, cpu, queue) per particle count.
+PAPER_TABLE4 = {
+    "D": 120,
+    "columns": ("iters", "cpu", "queue"),
+    "rows": {128: (5000, 2.392, 0.487), 256: (4000, 3.543, 0.384), 512: (3000, 5.305, 0.288),
+             1024: (2000, 7.078, 0.225), 2048: (2000, 14.214, 0.255), 4096: (1500, 21.593, 0.220),
+             8192: (1000, 29.494, 0.191), 16384: (1000, 59.125, 0.294), 32768: (1000, 128.349, 0.570),
+             65536: (1000, 237.933, 1.169), 131072: (800, 379.820, 1.744)},
+}

@@ -63,11 +63,28 @@ def test_invalid_arguments_rejected_on_host(P, args):
     assert P.last_error() != ""
 
 
+@pytest.mark.parametrize("args,code", [
+    (dict(D=0, N=10), "INVALID_ARG"), (dict(D=3, N=10, bounds=(1.0, -1.0, 1.0)), "INVALID_ARG"),
+    (dict(D=3, N=10, bounds=(-1.0, 1.0, -2.0)), "INVALID_ARG"), (dict(D=3, N=10, fid=9), "INVALID_ARG"),
+    (dict(D=3, N=10, w=float("inf")), "INVALID_ARG"),
+    (dict(D=3, N=10, fid=1), "UNSUPPORTED"), (dict(D=3, N=10, fid=2), "UNSUPPORTED"), (dict(D=3, N=10, fid=5), "UNSUPPORTED"),
+])
+def test_fp64_invalid_arguments_rejected_on_host(P, args, code):
+    b = P.cupso_bounds_f64(*args.get("bounds", (-1.0, 1.0, 0.5)))
+    h = C.c_void_p(1234)
+    rc = P.lib().cupso_create_fp64(args["D"], args["N"], C.byref(b), args.get("w", 1.0), 2.0, 2.0,
+                                   args.get("fid", 4), 1, C.byref(h))
+    assert rc == getattr(P, "CUPSO_ERR_" + code)
+    assert h.value is None
+
+
 def test_null_handle_calls_rejected(P):
     L = P.lib()
     assert L.cupso_step(None, 1) == P.CUPSO_ERR_INVALID_ARG
     assert L.cupso_set_option(None, P.CUPSO_OPT_MODE, 1) == P.CUPSO_ERR_INVALID_ARG
     assert L.cupso_get_gbest(None, None, None, None) == P.CUPSO_ERR_INVALID_ARG
+    assert L.cupso_get_gbest_fp64(None, None, None, None) == P.CUPSO_ERR_INVALID_ARG
+    assert L.cupso_get_state_fp64(None, None, None, None, None, None) == P.CUPSO_ERR_INVALID_ARG
     assert L.cupso_destroy(None) == P.CUPSO_OK
     with pytest.raises(P.CupsoError) as e:
         P.cupso_solve_batch([dict(D=0, N=4, bounds=(-1, 1, 1), w=0.5, c1=1, c2=1, fitness_id=0, seed=1)], 3)

@@ -3,7 +3,8 @@
 Sizes span several 1024-particle tiles with a ragged tail (N = 3000 -> 3 tiles,
 padded to 3072) and odd D (the last Philox call serves a single dimension).
 Every synchronous mode -- fused atomic (SYNC), tree baseline (TREE and its
-unrolled form), on-chip cluster (ONCHIP) -- must give the oracle's trajectory.
+unrolled form), on-chip cluster (ONCHIP), the paper's queue design (QUEUE,
+one particle per thread) -- must give the oracle's trajectory.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, ora
 pytestmark = pytest.mark.gpu
 
 SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "sync_ppt1", "sync_ppt2", "tree", "tree_unrolled",
-              "onchip"]
+              "onchip", "queue"]
 
 
 @pytest.fixture(scope="module")
@@ -119,11 +120,13 @@ def test_modes_interchangeable_mid_run(P):
         s.step(9)
         s.set_mode("tree_unrolled")
         s.step(3)
+        s.set_mode("queue")
+        s.step(4)
         s.set_mode("sync")
         s.step(2)
         st = s.state()
         _, fit, idx, pos = s.gbest()
-    ref = oracle_swarm(fid, N, D, 21).init().step_sync(26)
+    ref = oracle_swarm(fid, N, D, 21).init().step_sync(30)
     assert_state_equal(st, ref)
     assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 
@@ -156,6 +159,48 @@ def test_checkpoint_resume_bit_exact(P):
     for k in ("pos", "v", "pbest_pos", "pbest_fit"):
         assert same_bits(resumed[k], full[k]), k
     assert resumed["t"] == 20
+
+
+@pytest.mark.parametrize("fid", [0, 1, 3])
+@pytest.mark.parametrize("N,D", [(1, 3), (100, 5), (256, 8)])
+def test_queue_lock_single_block_equals_sync(P, fid, N, D):
+    """Alg. 3 with one block (N <= 256): nothing else can update gbest during
+    the launch, so the result is the synchronous trajectory."""
+    with gpu_swarm(P, fid, N, D, 6, "queue_lock") as s:
+        s.step(1)
+        s.step(16)
+        s.step(13)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 6).init().step_sync(30)
+    assert rc == P.CUPSO_OK
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("fid,N,D", [(1, 20000, 6), (3, 5000, 9), (4, 3000, 1)])
+def test_queue_lock_invariants(P, fid, N, D):
+    """Alg. 3 with many blocks: gbest is updated in place during the launch, so
+    the trajectory depends on timing; after every launch gbest is still the
+    lexicographic minimum over pbest, pbest never worsens, the state stays in
+    its box, and every pbest_fit is the fitness of its pbest_pos."""
+    from oracle import oracle as O
+    lo, hi, vmax = BOUNDS[fid]
+    with gpu_swarm(P, fid, N, D, 2, "queue_lock") as s:
+        prev = s.state()
+        for _ in range(4):
+            s.step(10)
+            st = s.state()
+            rc, gfit, gidx, gpos = s.gbest()
+            assert rc == P.CUPSO_OK
+            assert np.all(np.abs(st["v"]) <= np.float32(vmax))
+            assert np.all((st["pos"] >= np.float32(lo)) & (st["pos"] <= np.float32(hi)))
+            assert np.all(st["pbest_fit"] <= prev["pbest_fit"])
+            g = int(np.lexsort((np.arange(N), st["pbest_fit"]))[0])
+            assert gidx == g and same_bits(gfit, st["pbest_fit"][g]) and same_bits(gpos, st["pbest_pos"][g])
+            for i in np.random.default_rng(1).integers(0, N, 64):
+                assert same_bits(O.fitness(fid, st["pbest_pos"][i]), st["pbest_fit"][i])
+            prev = st
 
 
 def test_gbest_ties_go_to_lowest_index(P):

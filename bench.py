@@ -446,6 +446,31 @@ def run_lsq(a):
             ms = e0.elapsed_time(e1)
             runs[prec] = {"seconds": ms / 1e3, "ms_per_iter": ms / T, "final_residual_f64": s.gbest_f64(),
                           "pd_per_s": N * D * T / (ms / 1e3)}
+    # Final FP64 residual over swarm seeds 1..5 per precision: PSO trajectories
+    # diverge as soon as one pbest decision differs, so one run against another
+    # compares two random searches; the spread over seeds says how large that
+    # noise is next to the gap between precisions.
+    seeds = list(range(1, 6))
+    by_seed = {prec: [] for prec in ("bf16", "fp8", "fp32")}
+    for prec in by_seed:
+        for sd in seeds:
+            if sd == cfg["seed"]:
+                by_seed[prec].append(runs[prec]["final_residual_f64"])
+                continue
+            with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, sd,
+                         stream=stream.cuda_stream) as s:
+                s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
+                s.step(T)
+                by_seed[prec].append(s.gbest_f64())
+    seed_study = {"seeds": seeds, "final_residual_f64": by_seed}
+    for prec, vals in by_seed.items():
+        arr = np.array(vals)
+        seed_study[prec] = {"mean": float(arr.mean()), "std": float(arr.std(ddof=1)), "min": float(arr.min()),
+                            "max": float(arr.max())}
+    for prec in ("bf16", "fp8"):
+        m, m32 = seed_study[prec]["mean"], seed_study["fp32"]["mean"]
+        seed_study[prec]["mean_rel_gap_vs_fp32"] = abs(m - m32) / m32
+        seed_study[prec]["gap_in_fp32_std_of_mean"] = abs(m - m32) / (seed_study["fp32"]["std"] / np.sqrt(len(seeds)))
     # the fitness phase alone (operand conversion + tensor-core GEMM + partial sums),
     # timed live with CUDA events inside 50 further iterations of each tensor-core swarm
     fit_ms = {}
@@ -477,6 +502,7 @@ def run_lsq(a):
         "bf16_over_fp32": runs["fp32"]["seconds"] / runs["bf16"]["seconds"],
         "fp8_over_fp32": runs["fp32"]["seconds"] / runs["fp8"]["seconds"],
         "fitness_eval_ms": fit_ms,
+        "seed_study": seed_study,
         "roofline": {"bound": "tensor",
                      "kernel": "fitness phase: operand conversion + lsq_tc_kernel<bf16> + partial sums",
                      "achieved": flops / (fit_ms["bf16"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",

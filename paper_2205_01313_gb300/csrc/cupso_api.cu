@@ -199,11 +199,11 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
 
 cudaError_t launch_one64(cupso_swarm* h, int mode, cudaStream_t st) {
     switch (mode) {
-        case CUPSO_MODE_SYNC: return launch_step64(h->dev64, h->pbufs, h->fid, kAggSyncList, st);
-        case CUPSO_MODE_TREE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduce, st);
-        case CUPSO_MODE_TREE_UNROLLED: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduceUnrolled, st);
-        case CUPSO_MODE_QUEUE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueue, st);
-        case CUPSO_MODE_QUEUE_LOCK: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueueLock, st);
+        case CUPSO_MODE_SYNC: return launch_step64(h->dev64, h->pbufs, h->fid, kAggSyncList, h->num_sms, st);
+        case CUPSO_MODE_TREE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduce, h->num_sms, st);
+        case CUPSO_MODE_TREE_UNROLLED: return launch_step64(h->dev64, h->pbufs, h->fid, kAggReduceUnrolled, h->num_sms, st);
+        case CUPSO_MODE_QUEUE: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueue, h->num_sms, st);
+        case CUPSO_MODE_QUEUE_LOCK: return launch_step64(h->dev64, h->pbufs, h->fid, kAggQueueLock, h->num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -323,7 +323,8 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     const size_t o_aux = off; off = align_up(off + sizeof(unsigned long long) * ntiles, A);
     const size_t o_flag = off; off = align_up(off + (size_t)h->Np, A);
     const size_t o_words = off; off = align_up(off + 128, A);
-    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np), A);
+    const int list_cap = paper_blocks(h->Np);      // one candidate per block of the queue designs
+    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np, list_cap), A);
     h->arena_bytes = off;
     e = cudaMalloc(&h->arena, h->arena_bytes);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
@@ -361,7 +362,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.key1 = (uint32_t)(seed >> 32);
     s.swarm = swarm;
     s.wait_limit_ns = 2000000000ll;
-    h->pbufs = paper_bufs_at(base + o_paper, h->Np);
+    h->pbufs = paper_bufs_at(base + o_paper, h->Np, list_cap);
     // c * 2^-24 is exact unless it would be subnormal; check by scaling back.
     s.c1s = std::ldexp(c1, -24);
     s.c2s = std::ldexp(c2, -24);
@@ -378,7 +379,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.pflag, 0, (size_t)h->Np, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(unsigned long long), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np, list_cap), h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
     const int grid = std::min(tiles_of(h->Np), h->num_sms * 4);
     e = launch_init(s, fid, grid, h->stream);
@@ -387,6 +388,17 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     if (e != cudaSuccess) return bail(cuda_fail(e, "init"));
     *out = h;
     return CUPSO_OK;
+}
+
+// k when c = 2^k exactly with |k| <= 512 (c r is then an exponent shift of a
+// uniform in (2^-53, 1], which stays normal), else kNoExp.
+int pow2_exponent(double c) {
+    if (!(c > 0.0) || !std::isfinite(c)) return kNoExp;
+    int e = 0;
+    const double m = std::frexp(c, &e);   // c = m 2^e, m in [0.5, 1)
+    if (m != 0.5) return kNoExp;
+    const int k = e - 1;
+    return (k >= -512 && k <= 512) ? k : kNoExp;
 }
 
 // A double-precision swarm: arena x, v, pb [D][Np], pf [Np], G [2][D]
@@ -440,7 +452,8 @@ int create_swarm64(int D, int N, const cupso_bounds_f64* b, double w, double c1,
     const size_t o_G = off; off = align_up(off + sizeof(double) * 2 * (size_t)D, A);
     const size_t o_key = off; off = align_up(off + 2 * sizeof(PKey), A);
     const size_t o_words = off; off = align_up(off + 64, A);
-    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np), A);
+    const int list_cap = h->Np;   // the tiled step may run up to one block per particle
+    const size_t o_paper = off; off = align_up(off + paper_bufs_bytes(h->Np, list_cap), A);
     h->arena_bytes = off;
     e = cudaMalloc(&h->arena, h->arena_bytes);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMalloc"));
@@ -468,15 +481,23 @@ int create_swarm64(int D, int N, const cupso_bounds_f64* b, double w, double c1,
     s.key1 = (uint32_t)(seed >> 32);
     s.swarm = 0u;
     s.wait_limit_ns = 2000000000ll;
+    s.w_one = (w == 1.0) ? 1 : 0;
+    s.c1_exp = pow2_exponent(c1);
+    s.c2_exp = pow2_exponent(c2);
+    s.k_lo = order_key64(b->min_pos);
+    s.k_hi = order_key64(b->max_pos);
+    s.k_vlo = order_key64(-b->max_v);
+    s.k_vhi = order_key64(b->max_v);
     h->dev.wait_limit_ns = s.wait_limit_ns;
     h->dev.status = s.status;
-    h->pbufs = paper_bufs_at(base + o_paper, h->Np);
-    h->onchip64 = onchip64_fits(N, D) && prepare_onchip64() == cudaSuccess;
+    h->pbufs = paper_bufs_at(base + o_paper, h->Np, list_cap);
+    h->onchip_cluster = onchip64_cluster(N, D);
+    h->onchip64 = h->onchip_cluster > 0;
     cudaGetLastError();
 
     e = cudaMemsetAsync(base + o_words, 0, 64, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.gkey, 0xFF, 2 * sizeof(PKey), h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_paper, 0, paper_bufs_bytes(h->Np, list_cap), h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaMemsetAsync"));
     e = launch_init64(s, h->pbufs, fid, h->stream);
     if (e != cudaSuccess) return bail(cuda_fail(e, "init launch"));
@@ -494,6 +515,7 @@ int read_status(cupso_swarm* h, unsigned* st) {
 }
 
 int status_code(unsigned st) {
+    if (st & kStatusBadArg) return CUPSO_ERR_CUDA;   // a device-side bound check dropped work
     if (st & kStatusTimeout) return CUPSO_ERR_DEVICE_TIMEOUT;
     if (st & kStatusNaN) return CUPSO_ERR_NAN;
     return CUPSO_OK;
@@ -932,7 +954,7 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
     if (h->fp64) {
         info->sync_grid = paper_blocks(h->N);
         info->async_grid = 0;
-        info->onchip_cluster = h->onchip64 ? 1 : 0;
+        info->onchip_cluster = h->onchip_cluster;
         info->sync_stages = 0;
         info->sync_ppt = 0;
     } else {

@@ -25,12 +25,15 @@
 // (block argmin, a short candidate list, the last block gathers gbest) and an
 // on-chip kernel that keeps a small swarm in one CTA's shared memory for many
 // iterations.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
 #include "paper_kernels.h"
 #include "stream_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cupso {
 
@@ -74,6 +77,14 @@ __device__ __forceinline__ PKey block_min_key(PKey k, PKey* red) {
     return r;
 }
 
+// Appends a block's candidate to the list; a push beyond the capacity is
+// dropped and reported (launchers never start more blocks than list_cap).
+__device__ __forceinline__ void push_candidate(const PaperBufs& b, const PKey& k, unsigned int* status) {
+    const unsigned int slot = atomicAdd(b.list_n, 1u);
+    if (slot < b.list_cap) b.list[slot] = k;
+    else atomicOr(status, kStatusBadArg);
+}
+
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
     return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
@@ -82,20 +93,36 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 // Double precision building blocks
 // ---------------------------------------------------------------------------
 
-// Two words -> (m + 1) 2^-53 with m = hi 2^21 + (lo >> 11), in (0, 1]. The
-// double is assembled from integer parts: exponent from the leading bit of
-// v = m + 1, the bits below it as the fraction (v <= 2^53, so it is exact).
-__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
+// Two words -> (m + 1) 2^-53 with m = hi 2^21 + (lo >> 11), in (0, 1], times
+// 2^k. The double is assembled from integer parts: exponent from the leading
+// bit of v = m + 1 (plus k), the bits below it as the fraction (v <= 2^53, so
+// it is exact; callers keep |k| <= 512, so the result stays normal).
+__device__ __forceinline__ double u53_pow2(uint32_t hi, uint32_t lo, int k) {
     const unsigned long long v = (((unsigned long long)hi << 21) | (unsigned long long)(lo >> 11)) + 1ull;
     const int lz = __clzll((long long)v);
     const unsigned long long frac = ((v << lz) << 1) >> 12;
-    const unsigned long long e = (unsigned long long)(1033 - lz);
+    const unsigned long long e = (unsigned long long)(1033 - lz + k);
     return __longlong_as_double((long long)((e << 52) | frac));
 }
 
-__device__ __forceinline__ double clampd(double a, double lo, double hi) {
-    if (a != a) return lo;
-    return a < lo ? lo : (a > hi ? hi : a);
+__device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) { return u53_pow2(hi, lo, 0); }
+
+// c * u53(hi, lo), rounded once: an exponent shift when c = 2^k (exact).
+__device__ __forceinline__ double c_times_u53(double c, int cexp, uint32_t hi, uint32_t lo) {
+    if (cexp != kNoExp) return u53_pow2(hi, lo, cexp);
+    return __dmul_rn(c, u53(hi, lo));
+}
+
+// Closed clamp to [lo, hi] with a NaN going to lo, as comparisons of the
+// values' order keys (klo, khi: keys of lo, hi). Equal to the floating-point
+// comparison form for every a (-0 and +0 compare equal in both), but it runs
+// on the integer pipes instead of the FP64 one.
+__device__ __forceinline__ double clamp64(double a, double lo, double hi, long long klo, long long khi) {
+    const long long b = __double_as_longlong(a);
+    const long long mag = b & 0x7FFFFFFFFFFFFFFFll;
+    if (mag > 0x7FF0000000000000ll) return lo;
+    const long long k = b >= 0 ? b : -mag;
+    return k < klo ? lo : (k > khi ? hi : a);
 }
 
 __device__ __forceinline__ unsigned long long fit_key64(double f) {
@@ -127,16 +154,17 @@ struct FitAcc64 {
     __device__ __forceinline__ double finish() const { return FIT == kCubicMax ? -acc : acc; }
 };
 
-// Eq. 1 and Eq. 2 in binary64 with the clamps of Alg. 1 (same order as FP32).
-__device__ __forceinline__ void move_one64(double& x, double& v, double pb, double g, double r1, double r2,
-                                           const SwarmDev64& s) {
+// Eq. 1 and Eq. 2 in binary64 with the clamps of Alg. 1 (same order as FP32),
+// from the dimension's Philox words. Products that are exact by construction
+// (w v with w = 1, c r with c a power of two) are formed without the FP64 pipe.
+__device__ __forceinline__ void move_one64(double& x, double& v, double pb, double g, uint4 r, const SwarmDev64& s) {
     const double cognitive = __dsub_rn(pb, x);
     const double social = __dsub_rn(g, x);
-    double vel = __dmul_rn(s.w, v);
-    vel = __fma_rn(__dmul_rn(s.c1, r1), cognitive, vel);
-    vel = __fma_rn(__dmul_rn(s.c2, r2), social, vel);
-    v = clampd(vel, -s.vmax, s.vmax);
-    x = clampd(__dadd_rn(x, v), s.lo, s.hi);
+    double vel = s.w_one ? v : __dmul_rn(s.w, v);
+    vel = __fma_rn(c_times_u53(s.c1, s.c1_exp, r.x, r.y), cognitive, vel);
+    vel = __fma_rn(c_times_u53(s.c2, s.c2_exp, r.z, r.w), social, vel);
+    v = clamp64(vel, -s.vmax, s.vmax, s.k_vlo, s.k_vhi);
+    x = clamp64(__dadd_rn(x, v), s.lo, s.hi, s.k_lo, s.k_hi);
 }
 
 // ---------------------------------------------------------------------------
@@ -190,7 +218,7 @@ struct Fp64 {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, t, s.swarm), s.key0, s.key1);
             const size_t off = (size_t)d * Np + i;
             double x = s.x[off], v = s.v[off];
-            move_one64(x, v, s.pb[off], G[d], u53(r.x, r.y), u53(r.z, r.w), s);
+            move_one64(x, v, s.pb[off], G[d], r, s);
             s.x[off] = x;
             s.v[off] = v;
             acc.add(d, x);
@@ -325,7 +353,7 @@ __global__ void __launch_bounds__(kPaperBlock) paper_step_kernel(const __grid_co
         }
     } else {  // kAggSyncList
         const PKey k = block_min_key(mine, red);
-        if (tid == 0 && k.i != kNoIdx) b.list[atomicAdd(b.list_n, 1u)] = k;
+        if (tid == 0 && k.i != kNoIdx) push_candidate(b, k, s.status);
     }
     if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
 
@@ -343,7 +371,7 @@ __global__ void __launch_bounds__(kPaperBlock) paper_step_kernel(const __grid_co
                 s.G[(size_t)nxt * s.D + d] = __ldcg(s.G + (size_t)cur * s.D + d);
             if (tid == 0) A::store_gkey(s, nxt, A::load_gkey(s, cur));
         } else {
-            const unsigned int n = __ldcg(b.list_n);
+            const unsigned int n = min(__ldcg(b.list_n), b.list_cap);
             PKey k = tid == 0 ? A::load_gkey(s, cur) : key_none();
             for (unsigned int j = tid; j < n; j += blockDim.x) {
                 PKey c;
@@ -455,8 +483,8 @@ __global__ void __launch_bounds__(kPaperBlock) init64_kernel(const __grid_consta
         FitAcc64<FIT> acc;
         for (int d = 0; d < s.D; ++d) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, 0u, s.swarm), s.key0, s.key1);
-            const double x = clampd(__fma_rn(u53(r.x, r.y), span, s.lo), s.lo, s.hi);
-            const double v = clampd(__fma_rn(u53(r.z, r.w), vspan, -s.vmax), -s.vmax, s.vmax);
+            const double x = clamp64(__fma_rn(u53(r.x, r.y), span, s.lo), s.lo, s.hi, s.k_lo, s.k_hi);
+            const double v = clamp64(__fma_rn(u53(r.z, r.w), vspan, -s.vmax), -s.vmax, s.vmax, s.k_vlo, s.k_vhi);
             const size_t off = (size_t)d * Np + i;
             s.x[off] = x;
             s.v[off] = v;
@@ -490,39 +518,113 @@ __global__ void __launch_bounds__(kPaperBlock) pbest_min64_kernel(const __grid_c
 }
 
 // ---------------------------------------------------------------------------
-// On-chip FP64 swarm: x, v, pbest_pos ([D][N]), pbest_fit and gbest stay in
-// one CTA's shared memory for `iters` iterations; the kernel boundary of the
-// paper's designs becomes a block barrier.
+// Fitness from per-dimension terms, for the kernels that spread a particle's
+// dimensions over threads: the terms are formed in parallel, then one thread
+// per particle adds them in order d = 0 .. D-1 (the same operations, in the
+// same order, as FitAcc64).
+// ---------------------------------------------------------------------------
+template <int FIT>
+struct FitTerms64 {
+    static constexpr bool kNeedsNext = (FIT == kRosenbrock);
+    // term of dimension d (x = x_d, xn = x_{d+1}); Rosenbrock: d < D - 1 only
+    __device__ static __forceinline__ double term(double x, double xn) {
+        if constexpr (FIT == kCubicMax) {
+            return __fma_rn(__fma_rn(__dsub_rn(x, 0.8), x, -1000.0), x, 8000.0);
+        } else if constexpr (FIT == kRosenbrock) {
+            const double p = __fma_rn(-x, x, xn);
+            const double q = __dsub_rn(1.0, x);
+            return __fma_rn(__dmul_rn(100.0, p), p, __dmul_rn(q, q));
+        } else {
+            return 0.0;   // sphere: the sum fuses x * x, no separate term
+        }
+    }
+    // sequential sum over d of particle column p (stride P) of X / H
+    __device__ static __forceinline__ double sum(const double* X, const double* H, int P, int p, int D) {
+        double acc = 0.0;
+        if constexpr (FIT == kSphere) {
+            for (int d = 0; d < D; ++d) {
+                const double x = X[(size_t)d * P + p];
+                acc = __fma_rn(x, x, acc);
+            }
+        } else {
+            const int n = FIT == kRosenbrock ? D - 1 : D;
+            for (int d = 0; d < n; ++d) acc = __dadd_rn(acc, H[(size_t)d * P + p]);
+        }
+        return FIT == kCubicMax ? -acc : acc;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// On-chip FP64 swarm: a cluster of C CTAs (1 <= C <= 16). CTA r keeps the
+// particles [r P, r P + n_r) -- x, v, pbest_pos and the fitness terms
+// ([D][P]), pbest_fit and its copy of gbest -- in shared memory for `iters`
+// iterations. Per iteration every CTA pushes its best candidate (key and
+// position) into slot [parity][r] of every CTA of the cluster through
+// distributed shared memory (index first, position after, Sec. 4.3); one
+// cluster barrier replaces the paper's kernel boundary (Sec. 2.2), and every
+// CTA reduces the same slots in the same order, so all hold the same gbest.
 // ---------------------------------------------------------------------------
 constexpr int kOnchip64Threads = 1024;
+constexpr int kMaxCluster64 = 16;
 
-__host__ __device__ inline size_t onchip64_bytes(int N, int D) {
-    return sizeof(double) * (3 * (size_t)N * (size_t)D + (size_t)N + (size_t)D) + sizeof(PKey) * 32;
+struct Onchip64Layout {
+    int P;                                  // particles per CTA
+    size_t o_x, o_v, o_pb, o_h, o_pf, o_G, o_red, o_slots, slot, bytes;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) / 16 * 16; }
+
+__host__ __device__ inline Onchip64Layout onchip64_layout(int N, int D, int C) {
+    Onchip64Layout L;
+    L.P = (N + C - 1) / C;
+    const size_t plane = sizeof(double) * (size_t)L.P * (size_t)D;
+    size_t o = 0;
+    L.o_x = o; o = al16(o + plane);
+    L.o_v = o; o = al16(o + plane);
+    L.o_pb = o; o = al16(o + plane);
+    L.o_h = o; o = al16(o + plane);
+    L.o_pf = o; o = al16(o + sizeof(double) * (size_t)L.P);
+    L.o_G = o; o = al16(o + sizeof(double) * (size_t)D);
+    L.o_red = o; o = al16(o + sizeof(PKey) * 32);
+    L.slot = al16(sizeof(PKey) + sizeof(double) * (size_t)D);
+    L.o_slots = o; o += 2 * (size_t)C * L.slot;
+    L.bytes = o;
+    return L;
 }
 
 template <int FIT>
 __global__ void __launch_bounds__(kOnchip64Threads) onchip64_kernel(const __grid_constant__ SwarmDev64 s, int iters) {
     extern __shared__ __align__(16) unsigned char smem[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
     const int N = s.N, D = s.D;
-    const size_t ND = (size_t)N * (size_t)D;
-    double* x = reinterpret_cast<double*>(smem);   // [D][N]
-    double* v = x + ND;
-    double* pb = v + ND;
-    double* pf = pb + ND;                          // [N]
-    double* G = pf + N;                            // [D]
-    PKey* red = reinterpret_cast<PKey*>(G + D);    // [32]
+    const Onchip64Layout L = onchip64_layout(N, D, C);
+    const int P = L.P;
+    const int base = rank * P;
+    const int n = max(0, min(P, N - base));       // particles of this CTA
+    double* x = reinterpret_cast<double*>(smem + L.o_x);    // [D][P]
+    double* v = reinterpret_cast<double*>(smem + L.o_v);
+    double* pb = reinterpret_cast<double*>(smem + L.o_pb);
+    double* H = reinterpret_cast<double*>(smem + L.o_h);
+    double* pf = reinterpret_cast<double*>(smem + L.o_pf);
+    double* G = reinterpret_cast<double*>(smem + L.o_G);
+    PKey* red = reinterpret_cast<PKey*>(smem + L.o_red);
+    unsigned char* slots = smem + L.o_slots;
     const size_t Np = (size_t)s.Np;
     const int tid = threadIdx.x;
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur0 = (int)(t_prev & 1u);
+    const int nD = n * D;
 
-    for (size_t e = tid; e < ND; e += blockDim.x) {
-        const size_t d = e / (size_t)N, p = e - d * (size_t)N;
-        x[e] = s.x[d * Np + p];
-        v[e] = s.v[d * Np + p];
-        pb[e] = s.pb[d * Np + p];
+    for (int e = tid; e < nD; e += blockDim.x) {
+        const int d = e / n, p = e - d * n;
+        const size_t g = (size_t)d * Np + (size_t)(base + p);
+        x[d * P + p] = s.x[g];
+        v[d * P + p] = s.v[g];
+        pb[d * P + p] = s.pb[g];
     }
-    for (int p = tid; p < N; p += blockDim.x) pf[p] = s.pf[p];
+    for (int p = tid; p < n; p += blockDim.x) pf[p] = s.pf[base + p];
     for (int d = tid; d < D; d += blockDim.x) G[d] = s.G[(size_t)cur0 * D + d];
     PKey K = Fp64::load_gkey(s, cur0);
     __syncthreads();
@@ -530,52 +632,203 @@ __global__ void __launch_bounds__(kOnchip64Threads) onchip64_kernel(const __grid
     bool nan = false;
     for (int k = 0; k < iters; ++k) {
         const uint32_t t = t_prev + 1u + (uint32_t)k;
-        // Step 2 for every (dimension, particle)
-        for (size_t e = tid; e < ND; e += blockDim.x) {
-            const uint32_t d = (uint32_t)(e / (size_t)N), p = (uint32_t)(e - (size_t)d * N);
-            const uint4 r = philox4x32_10(make_uint4(d, p, t, s.swarm), s.key0, s.key1);
-            double xx = x[e], vv = v[e];
-            move_one64(xx, vv, pb[e], G[d], u53(r.x, r.y), u53(r.z, r.w), s);
-            x[e] = xx;
-            v[e] = vv;
+        // Step 2 for every (dimension, particle); the fitness terms that need only x_d
+        for (int e = tid; e < nD; e += blockDim.x) {
+            const int d = e / n, p = e - d * n;
+            const int j = d * P + p;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)d, (uint32_t)(base + p), t, s.swarm), s.key0, s.key1);
+            double xx = x[j], vv = v[j];
+            move_one64(xx, vv, pb[j], G[d], r, s);
+            x[j] = xx;
+            v[j] = vv;
+            if constexpr (!FitTerms64<FIT>::kNeedsNext && FIT != kSphere) H[j] = FitTerms64<FIT>::term(xx, 0.0);
         }
         __syncthreads();
-        // Steps 3-4 per particle; the candidates of Step 5
+        if constexpr (FitTerms64<FIT>::kNeedsNext) {
+            for (int e = tid; e < nD; e += blockDim.x) {
+                const int d = e / n, p = e - d * n;
+                if (d + 1 < D) H[d * P + p] = FitTerms64<FIT>::term(x[d * P + p], x[(d + 1) * P + p]);
+            }
+            __syncthreads();
+        }
+        // Steps 3-4 per particle; this CTA's Step-5 candidate
         PKey cand = key_none();
-        for (int p = tid; p < N; p += blockDim.x) {
-            FitAcc64<FIT> acc;
-            for (int d = 0; d < D; ++d) acc.add(d, x[(size_t)d * N + p]);
-            const double f = acc.finish();
+        for (int p = tid; p < n; p += blockDim.x) {
+            const double f = FitTerms64<FIT>::sum(x, H, P, p, D);
             nan |= (f != f);
             if (f < pf[p]) {
                 pf[p] = f;
-                for (int d = 0; d < D; ++d) pb[(size_t)d * N + p] = x[(size_t)d * N + p];
-                const PKey c = Fp64::key(f, (uint32_t)p);
-                if (key_less(c, cand)) cand = c;
+                for (int d = 0; d < D; ++d) pb[d * P + p] = x[d * P + p];
+                const PKey c = Fp64::key(f, (uint32_t)(base + p));
+                if (key_less(c, K) && key_less(c, cand)) cand = c;
             }
         }
         const PKey best = block_min_key(cand, red);   // barriers inside
-        if (key_less(best, K)) {
-            K = best;
-            for (int d = tid; d < D; d += blockDim.x) G[d] = pb[(size_t)d * N + best.i];
+        // push (key, position) into slot [par][rank] of every CTA
+        const int par = k & 1;
+        const size_t my_slot = ((size_t)par * C + rank) * L.slot;
+        if (tid < C) {
+            unsigned char* remote = cluster.map_shared_rank(slots, tid);
+            *reinterpret_cast<PKey*>(remote + my_slot) = best;
+        }
+        if (best.i != kNoIdx) {
+            const int pc = (int)best.i - base;
+            for (int e = tid; e < C * D; e += blockDim.x) {
+                const int r = e / D, d = e - r * D;
+                unsigned char* remote = cluster.map_shared_rank(slots, r);
+                reinterpret_cast<double*>(remote + my_slot + sizeof(PKey))[d] = pb[d * P + pc];
+            }
+        }
+        cluster.sync();
+        // Step 5: the same reduction over the slots in every CTA
+        PKey bk = K;
+        int win = -1;
+        for (int r = 0; r < C; ++r) {
+            const PKey kk = *reinterpret_cast<const PKey*>(slots + ((size_t)par * C + r) * L.slot);
+            if (key_less(kk, bk)) {
+                bk = kk;
+                win = r;
+            }
+        }
+        if (win >= 0) {
+            const double* row = reinterpret_cast<const double*>(slots + ((size_t)par * C + win) * L.slot + sizeof(PKey));
+            for (int d = tid; d < D; d += blockDim.x) G[d] = row[d];
+            K = bk;
         }
         __syncthreads();
     }
-    for (size_t e = tid; e < ND; e += blockDim.x) {
-        const size_t d = e / (size_t)N, p = e - d * (size_t)N;
-        s.x[d * Np + p] = x[e];
-        s.v[d * Np + p] = v[e];
-        s.pb[d * Np + p] = pb[e];
+    for (int e = tid; e < nD; e += blockDim.x) {
+        const int d = e / n, p = e - d * n;
+        const size_t g = (size_t)d * Np + (size_t)(base + p);
+        s.x[g] = x[d * P + p];
+        s.v[g] = v[d * P + p];
+        s.pb[g] = pb[d * P + p];
     }
-    for (int p = tid; p < N; p += blockDim.x) s.pf[p] = pf[p];
-    const int out = (int)((t_prev + (uint32_t)iters) & 1u);
-    for (int d = tid; d < D; d += blockDim.x) s.G[(size_t)out * D + d] = G[d];
+    for (int p = tid; p < n; p += blockDim.x) s.pf[base + p] = pf[p];
     if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
-    if (tid == 0) {
-        Fp64::store_gkey(s, 0, K);
-        Fp64::store_gkey(s, 1, K);
-        *s.t_dev = t_prev + (uint32_t)iters;
+    if (rank == 0) {
+        const int out = (int)((t_prev + (uint32_t)iters) & 1u);
+        for (int d = tid; d < D; d += blockDim.x) s.G[(size_t)out * D + d] = G[d];
+        if (tid == 0) {
+            Fp64::store_gkey(s, 0, K);
+            Fp64::store_gkey(s, 1, K);
+            *s.t_dev = t_prev + (uint32_t)iters;
+        }
     }
+    // no CTA leaves while another may still read its shared memory
+    cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 synchronous step for many dimensions: a block takes a tile of P
+// particles with all D dimensions and spreads its (dimension, particle) pairs
+// over the threads (the one-particle-per-thread designs leave most SMs idle
+// when N is small and D large). The fitness terms are formed in parallel, the
+// ordered sum by one thread per particle; pbest rows are written by all
+// threads. Step 5 as in the fused one-particle-per-thread step: block argmin,
+// candidate list, the last block gathers gbest.
+// ---------------------------------------------------------------------------
+constexpr int kTileItems = 2048;     // P * D per block at most (32 KB of x' and terms)
+constexpr int kTileMinD = 16;        // below this the one-particle-per-thread step is used
+
+template <int FIT>
+__global__ void __launch_bounds__(256) sync64_tile_kernel(const __grid_constant__ SwarmDev64 s,
+                                                         const __grid_constant__ PaperBufs b, int P) {
+    __shared__ double X[kTileItems];
+    __shared__ double H[kTileItems];
+    __shared__ PKey red[32];
+    __shared__ int imp[32];
+    __shared__ int s_last;
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const uint32_t t = t_prev + 1u;
+    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
+    const int tid = threadIdx.x;
+    const int D = s.D;
+    const size_t Np = (size_t)s.Np;
+    const int base = blockIdx.x * P;
+    const int n = min(P, s.N - base);
+    const int nD = n * D;
+    const double* G = s.G + (size_t)cur * D;
+
+    for (int e = tid; e < nD; e += blockDim.x) {
+        const int d = e / n, p = e - d * n;
+        const uint32_t i = (uint32_t)(base + p);
+        const size_t off = (size_t)d * Np + i;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, t, s.swarm), s.key0, s.key1);
+        double xx = s.x[off], vv = s.v[off];
+        move_one64(xx, vv, s.pb[off], G[d], r, s);
+        s.x[off] = xx;
+        s.v[off] = vv;
+        X[d * P + p] = xx;
+        if constexpr (!FitTerms64<FIT>::kNeedsNext && FIT != kSphere) H[d * P + p] = FitTerms64<FIT>::term(xx, 0.0);
+    }
+    __syncthreads();
+    if constexpr (FitTerms64<FIT>::kNeedsNext) {
+        for (int e = tid; e < nD; e += blockDim.x) {
+            const int d = e / n, p = e - d * n;
+            if (d + 1 < D) H[d * P + p] = FitTerms64<FIT>::term(X[d * P + p], X[(d + 1) * P + p]);
+        }
+        __syncthreads();
+    }
+    PKey cand = key_none();
+    bool nan = false;
+    if (tid < n) {
+        const uint32_t i = (uint32_t)(base + tid);
+        const double f = FitTerms64<FIT>::sum(X, H, P, tid, D);
+        nan = (f != f);
+        const bool better = f < s.pf[i];
+        imp[tid] = better ? 1 : 0;
+        if (better) {
+            s.pf[i] = f;
+            const PKey c = Fp64::key(f, i);
+            if (c.k <= Fp64::gk(s, cur)) cand = c;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nD; e += blockDim.x) {
+        const int d = e / n, p = e - d * n;
+        if (imp[p]) s.pb[(size_t)d * Np + (size_t)(base + p)] = X[d * P + p];
+    }
+    const PKey k = block_min_key(cand, red);
+    if (tid == 0 && k.i != kNoIdx) push_candidate(b, k, s.status);
+    if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
+
+    // the last block to finish closes the iteration
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(b.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const unsigned int nl = min(__ldcg(b.list_n), b.list_cap);
+    PKey m = tid == 0 ? Fp64::load_gkey(s, cur) : key_none();
+    for (unsigned int j = tid; j < nl; j += blockDim.x) {
+        PKey c;
+        c.k = __ldcg(&b.list[j].k);
+        c.i = __ldcg(&b.list[j].i);
+        c.pad = 0u;
+        if (key_less(c, m)) m = c;
+    }
+    const PKey best = block_min_key(m, red);
+    if (best.i < (uint32_t)s.N)
+        for (int d = tid; d < D; d += blockDim.x)
+            s.G[(size_t)nxt * D + d] = __ldcg(s.pb + (size_t)d * Np + best.i);
+    __syncthreads();
+    if (tid == 0) {
+        Fp64::store_gkey(s, nxt, best);
+        Fp64::store_gkey(s, cur, best);
+        *b.list_n = 0u;
+        *b.ticket = 0u;
+        *s.t_dev = t;
+    }
+}
+
+// Particles per tile of sync64_tile_kernel: a power of two, at most 32 and
+// kTileItems / D, and small enough that the tiles cover the SMs twice over.
+int tile_particles(int N, int D, int num_sms) {
+    int P = 32;
+    while (P > 1 && (P * D > kTileItems || (long long)N < 2ll * num_sms * P)) P >>= 1;
+    return P;
 }
 
 #define CUPSO_DISPATCH_FIT32(fid, CALL)            \
@@ -600,19 +853,20 @@ size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-size_t paper_bufs_bytes(int Np) {
+size_t paper_bufs_bytes(int Np, int list_cap) {
     const size_t nb = (size_t)paper_blocks(Np);
-    return 2 * al256(sizeof(PKey) * nb) + 256;
+    return al256(sizeof(PKey) * nb) + al256(sizeof(PKey) * (size_t)list_cap) + 256;
 }
 
-PaperBufs paper_bufs_at(void* base, int Np) {
+PaperBufs paper_bufs_at(void* base, int Np, int list_cap) {
     const size_t nb = (size_t)paper_blocks(Np);
     char* p = static_cast<char*>(base);
     PaperBufs b;
     b.aux = reinterpret_cast<PKey*>(p);
     p += al256(sizeof(PKey) * nb);
     b.list = reinterpret_cast<PKey*>(p);
-    p += al256(sizeof(PKey) * nb);
+    b.list_cap = (unsigned int)list_cap;
+    p += al256(sizeof(PKey) * (size_t)list_cap);
     unsigned int* w = reinterpret_cast<unsigned int*>(p);
     b.lock = w;
     b.ticket = w + 1;
@@ -653,8 +907,17 @@ cudaError_t launch_recompute64(const SwarmDev64& s, const PaperBufs& b, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int agg, cudaStream_t st) {
+cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int agg, int num_sms, cudaStream_t st) {
     const int nb = paper_blocks(s.N);
+    if ((unsigned int)nb > b.list_cap) return cudaErrorInvalidConfiguration;
+    if (agg == kAggSyncList && s.D >= kTileMinD && s.D <= kTileItems) {
+        const int P = tile_particles(s.N, s.D, num_sms);
+        const int tiles = (s.N + P - 1) / P;
+        if ((unsigned int)tiles > b.list_cap) return cudaErrorInvalidConfiguration;
+        const int threads = P * s.D >= 256 ? 256 : (P * s.D + 31) / 32 * 32;
+        CUPSO_DISPATCH_FIT64(fid, (sync64_tile_kernel<F><<<tiles, threads, 0, st>>>(s, b, P)));
+        return cudaGetLastError();
+    }
     switch (agg) {
         case kAggReduce:
             CUPSO_DISPATCH_FIT64(fid, (paper_step_kernel<Fp64, F, kAggReduce><<<nb, kPaperBlock, 0, st>>>(s, b)));
@@ -685,31 +948,106 @@ cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int 
     return cudaGetLastError();
 }
 
-bool onchip64_fits(int N, int D) {
-    int dev = 0, optin = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    return onchip64_bytes(N, D) <= (size_t)optin;
+namespace {
+
+int max_optin_smem64() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return v;
 }
 
-cudaError_t prepare_onchip64() {
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(onchip64_kernel<kSphere>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(onchip64_kernel<kRosenbrock>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(onchip64_kernel<kCubicMax>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+int threads_for(int P, int D) {
+    const long long work = (long long)P * D;
+    int th = (int)((work + 31) / 32 * 32);
+    return th < 32 ? 32 : (th > kOnchip64Threads ? kOnchip64Threads : th);
+}
+
+template <int FIT>
+cudaError_t set_onchip64_attrs(size_t smem, int C) {
+    cudaError_t e = cudaFuncSetAttribute(onchip64_kernel<FIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(onchip64_kernel<FIT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
+cudaLaunchConfig_t onchip64_config(int C, int threads, size_t smem, cudaStream_t st, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+bool cluster64_schedulable(int N, int D, int C) {
+    const Onchip64Layout L = onchip64_layout(N, D, C);
+    if (set_onchip64_attrs<kSphere>(L.bytes, C) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = onchip64_config(C, threads_for(L.P, D), L.bytes, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, onchip64_kernel<kSphere>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return n > 0;
+}
+
+}  // namespace
+
+// CTAs of the on-chip cluster for (N, D), or 0 if the swarm does not fit: the
+// power of two that gives each CTA about 128 (particle, dimension) pairs (so
+// the FP64 work of an iteration spreads over that many SMs), at least the
+// smallest count whose shared memory fits, at most 16.
+int onchip64_cluster(int N, int D) {
+    const int limit = max_optin_smem64() - 1024;   // room for the static shared arrays
+    if (limit <= 0) return 0;
+    const long long pd = (long long)N * D;
+    int C = 1;
+    while (C < kMaxCluster64 && pd > 128ll * C && C < N) C *= 2;
+    while (C <= kMaxCluster64 && onchip64_layout(N, D, C).bytes > (size_t)limit) C *= 2;
+    if (C > kMaxCluster64) return 0;
+    const int C_min = C;
+    while (C >= 1 && !cluster64_schedulable(N, D, C)) C /= 2;
+    if (C < 1 || onchip64_layout(N, D, C).bytes > (size_t)limit) return 0;
+    (void)C_min;
+    return C;
+}
+
+bool onchip64_fits(int N, int D) { return onchip64_cluster(N, D) > 0; }
+
 cudaError_t launch_onchip64(const SwarmDev64& s, int fid, int iters, cudaStream_t st) {
-    const size_t smem = onchip64_bytes(s.N, s.D);
-    const size_t work = (size_t)s.N * (size_t)s.D;
-    int threads = (int)((work + 31) / 32 * 32);
-    if (threads > kOnchip64Threads) threads = kOnchip64Threads;
-    if (threads < 32) threads = 32;
-    CUPSO_DISPATCH_FIT64(fid, (onchip64_kernel<F><<<1, threads, smem, st>>>(s, iters)));
-    return cudaGetLastError();
+    const int C = onchip64_cluster(s.N, s.D);
+    if (C <= 0) return cudaErrorInvalidConfiguration;
+    const Onchip64Layout L = onchip64_layout(s.N, s.D, C);
+    const int threads = threads_for(L.P, s.D);
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = onchip64_config(C, threads, L.bytes, st, attr);
+    switch (fid) {
+        case kSphere: {
+            cudaError_t e = set_onchip64_attrs<kSphere>(L.bytes, C);
+            return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, onchip64_kernel<kSphere>, s, iters);
+        }
+        case kRosenbrock: {
+            cudaError_t e = set_onchip64_attrs<kRosenbrock>(L.bytes, C);
+            return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, onchip64_kernel<kRosenbrock>, s, iters);
+        }
+        case kCubicMax: {
+            cudaError_t e = set_onchip64_attrs<kCubicMax>(L.bytes, C);
+            return e != cudaSuccess ? e : cudaLaunchKernelEx(&cfg, onchip64_kernel<kCubicMax>, s, iters);
+        }
+        default:
+            return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace cupso

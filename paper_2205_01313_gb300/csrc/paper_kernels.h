@@ -26,11 +26,12 @@ constexpr uint32_t kNoIdx = 0xFFFFFFFFu;
 
 // Working storage of the one-particle-per-thread kernels (both precisions).
 struct PaperBufs {
-    PKey* aux;             // [blocks]  best of each block (Sec. 2.2, Alg. 2)
-    PKey* list;            // [blocks]  candidates of the fused FP64 step
+    PKey* aux;             // [blocks]   best of each block (Sec. 2.2, Alg. 2)
+    PKey* list;            // [list_cap] candidates of the fused FP64 steps (one per block at most)
     unsigned int* lock;    // Alg. 3 global lock
     unsigned int* ticket;  // last-block counter of the one-kernel variants
     unsigned int* list_n;  // entries in `list`
+    unsigned int list_cap; // capacity of `list`: no launch may have more blocks
 };
 
 // Device state of a double-precision swarm. Same layouts as SwarmDev:
@@ -48,7 +49,23 @@ struct SwarmDev64 {
     double lo, hi, vmax, w, c1, c2;
     uint32_t key0, key1, swarm;
     long long wait_limit_ns;
+    // Exact shortcuts (each gives the bits of the plain operation):
+    int w_one;                   // w == 1: w v is v
+    int c1_exp, c2_exp;          // c == 2^k: c r is r with k added to its exponent; else kNoExp
+    long long k_lo, k_hi;        // order keys of min_pos, max_pos (clamps as integer compares)
+    long long k_vlo, k_vhi;      // order keys of -max_v, max_v
 };
+
+constexpr int kNoExp = 0x7FFF;
+
+// IEEE-754 order of a binary64 value as a signed integer (-0 and +0 equal);
+// meaningful for non-NaN values.
+__host__ __device__ inline long long order_key64(double a) {
+    long long b;
+    static_assert(sizeof(b) == sizeof(a), "binary64");
+    __builtin_memcpy(&b, &a, 8);
+    return b >= 0 ? b : -(b & 0x7FFFFFFFFFFFFFFFll);
+}
 
 constexpr int kPaperBlock = 256;   // threads (= particles) per block
 
@@ -62,10 +79,11 @@ enum PaperAgg : int {
 
 inline int paper_blocks(int n) { return (n + kPaperBlock - 1) / kPaperBlock; }
 
-// Bytes of PaperBufs storage for a swarm of Np particles (256-byte aligned parts).
-size_t paper_bufs_bytes(int Np);
-// Carves PaperBufs out of `base` (paper_bufs_bytes(Np) bytes, zeroed by the caller).
-PaperBufs paper_bufs_at(void* base, int Np);
+// Bytes of PaperBufs storage for a swarm of Np particles whose candidate list
+// holds list_cap entries (256-byte aligned parts).
+size_t paper_bufs_bytes(int Np, int list_cap);
+// Carves PaperBufs out of `base` (paper_bufs_bytes(Np, list_cap) bytes, zeroed by the caller).
+PaperBufs paper_bufs_at(void* base, int Np, int list_cap);
 
 // FP32 swarm: one iteration of Alg. 2 (two kernels) or Alg. 3 (one kernel).
 cudaError_t launch_queue_step(const SwarmDev& s, const PaperBufs& b, int fid, bool lock, cudaStream_t st);
@@ -73,12 +91,15 @@ cudaError_t launch_queue_step(const SwarmDev& s, const PaperBufs& b, int fid, bo
 // FP64 swarm (fitness: sphere, Rosenbrock, cubic).
 bool fp64_fitness_supported(int fid);
 cudaError_t launch_init64(const SwarmDev64& s, const PaperBufs& b, int fid, cudaStream_t st);
-cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int agg, cudaStream_t st);
+// SYNC (kAggSyncList) with D >= 16 runs the tiled kernel, which spreads a
+// particle's dimensions over threads; num_sms sizes its tiles.
+cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int agg, int num_sms, cudaStream_t st);
 cudaError_t launch_recompute64(const SwarmDev64& s, const PaperBufs& b, cudaStream_t st);
-// On-chip FP64 swarm: the whole swarm in one CTA's shared memory, `iters`
-// iterations per launch. onchip64_fits says whether (N, D) fits.
+// On-chip FP64 swarm: the whole swarm in the shared memory of one CTA cluster
+// (1 to 16 CTAs, chosen from (N, D) by onchip64_cluster), `iters` iterations
+// per launch. onchip64_fits says whether (N, D) fits at all.
 bool onchip64_fits(int N, int D);
-cudaError_t prepare_onchip64();
+int onchip64_cluster(int N, int D);
 cudaError_t launch_onchip64(const SwarmDev64& s, int fid, int iters, cudaStream_t st);
 
 }  // namespace cupso

@@ -97,6 +97,41 @@ def _paper_kw():
     return dict(bounds=PAPER["bounds"], w=PAPER["w"], c1=PAPER["c"], c2=PAPER["c"])
 
 
+@pytest.mark.parametrize("fid,N,D", [(4, 3000, 16), (3, 777, 33), (0, 5000, 120), (3, 129, 64), (4, 40, 2048),
+                                     (0, 9, 2100)])
+def test_sync_many_dimensions_bit_exact_fp64(P, fid, N, D):
+    """D >= 16: the tiled SYNC kernel (a particle's dimensions spread over
+    threads, the ordered sum by one thread); D > 2048 falls back to one
+    particle per thread."""
+    T = 12
+    with gpu64(P, fid, N, D, 12, "sync") as s:
+        s.step(T)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = ora64(fid, N, D, 12).init().step_sync(T)
+    assert rc == P.CUPSO_OK
+    assert_state64(st, ref)
+    assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("fid,N,D,C", [(4, 5, 3, 1), (4, 300, 1, 4), (3, 2048, 1, 16), (0, 100, 20, 16),
+                                       (3, 511, 7, 16), (4, 17, 9, 2)])
+def test_onchip_cluster_bit_exact_fp64(P, fid, N, D, C):
+    """The on-chip kernel over clusters of 1 to 16 CTAs (some CTAs of a
+    cluster may hold no particle)."""
+    T = 40
+    with gpu64(P, fid, N, D, 14, "onchip") as s:
+        assert s.info()["onchip_cluster"] == C
+        s.step(1)
+        s.step(T - 1)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = ora64(fid, N, D, 14).init().step_sync(T)
+    assert rc == P.CUPSO_OK
+    assert_state64(st, ref)
+    assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
+
+
 @pytest.mark.parametrize("N,D", [(1, 2), (200, 3), (256, 1)])
 def test_queue_lock_single_block_equals_sync_fp64(P, N, D):
     fid = 3
@@ -153,7 +188,7 @@ def test_single_step_from_shared_state_fp64(P, mode):
 def test_modes_interchangeable_mid_run_fp64(P):
     fid, N, D = 0, 1500, 3
     with gpu64(P, fid, N, D, 5, "sync") as s:
-        assert s.info()["onchip_cluster"] == 1
+        assert s.info()["onchip_cluster"] == 16
         for mode, k in (("sync", 3), ("tree", 4), ("onchip", 5), ("queue", 2), ("tree_unrolled", 3), ("sync", 2)):
             s.set_mode(mode)
             s.step(k)

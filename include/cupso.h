@@ -122,12 +122,17 @@ typedef enum {
                                        lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
 } cupso_option;
 
-/* The two implementations of the SYNC step; both compute the same bits. */
+/* The implementations of the SYNC step; all compute the same bits. */
 typedef enum {
-    CUPSO_SYNC_KERNEL_AUTO = 0,       /* deepest pipelined ring supported, else register   */
+    CUPSO_SYNC_KERNEL_AUTO = 0,       /* tiled for small swarms, else the deepest pipelined
+                                         ring supported, else register                      */
     CUPSO_SYNC_KERNEL_REGISTER = 1,   /* loads straight into registers, 1024-particle tiles */
     CUPSO_SYNC_KERNEL_PIPELINED3 = 2, /* rows staged through shared memory, 2 pairs ahead   */
-    CUPSO_SYNC_KERNEL_PIPELINED4 = 3  /* the same, 3 pairs ahead                            */
+    CUPSO_SYNC_KERNEL_PIPELINED4 = 3, /* the same, 3 pairs ahead                            */
+    CUPSO_SYNC_KERNEL_TILED = 4       /* a tile of particles with all their dimensions per block,
+                                         the (dimension pair, particle) items spread over threads;
+                                         AUTO uses it for D >= 8 up to about 224 particles per SM
+                                         (896 for Rastrigin and Ackley)                         */
 } cupso_sync_kernel;
 
 typedef struct {
@@ -140,6 +145,7 @@ typedef struct {
     int onchip_cluster;   /* CTAs per cluster if ONCHIP fits, else 0 */
     int sync_stages;      /* ring depth of the SYNC kernel in use, 0 = register kernel */
     int sync_ppt;         /* particles per thread of the pipelined SYNC kernel (0: not in use) */
+    int sync_tile;        /* particles per tile of the tiled SYNC kernel (0: not in use) */
     float fitness_ms;     /* mean fitness-phase time of the timed LSQ iterations, 0 if none */
     int fitness_timed;    /* how many iterations that mean covers */
     uint64_t device_bytes;/* device memory held by the handle        */

@@ -19,6 +19,7 @@
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
 #include "paper_kernels.h"
+#include "tiled_kernels.h"
 
 using namespace cupso;
 
@@ -104,6 +105,28 @@ int resolved_mode(const cupso_swarm* h) {
     if (h->mode != CUPSO_MODE_AUTO) return h->mode;
     if (h->fp64) return h->onchip64 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
     return h->onchip_cluster > 0 ? CUPSO_MODE_ONCHIP : CUPSO_MODE_SYNC;
+}
+
+// Particles per tile when the tiled SYNC kernel runs, else 0. AUTO takes it
+// for D >= 8 up to the crossover measured on a GB300 against the pipelined
+// kernel (which runs over d inside each thread and needs many particles per
+// SM to hide its row latency): about 224 particles per SM, or 896 for the
+// fitness functions with cos(2 pi x), whose extra arithmetic the tiled
+// layout spreads better.
+int sync_tile(const cupso_swarm* h) {
+    if (h->fp64) return 0;
+    if (h->sync_kernel == CUPSO_SYNC_KERNEL_TILED) return tiled_particles(h->N, h->D, h->num_sms);
+    if (h->sync_kernel != CUPSO_SYNC_KERNEL_AUTO || h->D < 8) return 0;
+    const bool has_cos = h->fid == CUPSO_RASTRIGIN || h->fid == CUPSO_ACKLEY;
+    const long long per_sm = has_cos ? 896 : 224;
+    if ((long long)h->N > per_sm * h->num_sms) return 0;
+    return tiled_particles(h->N, h->D, h->num_sms);
+}
+
+// Blocks of the tiled kernel: one wave of resident blocks (or the grid option).
+int tiled_grid(const cupso_swarm* h, int P) {
+    if (h->grid_override > 0) return h->grid_override;
+    return h->num_sms * tiled_blocks_per_sm(h->fid, P, h->D);
 }
 
 // Ring depth of the pipelined SYNC kernel, or 0 for the register kernel.
@@ -213,6 +236,8 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
     switch (mode) {
         case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
+            if (const int P = sync_tile(h))
+                return launch_sync_tiled(h->dev, h->fid, P, tiled_grid(h, P), st);
             const int stages = sync_stages(h);
             if (stages) return launch_sync_pipelined(h->dev, h->fid, stages, sync_ppt(h), sync_grid(h), st);
             return launch_sync_step(h->dev, h->fid, sync_grid(h), st);
@@ -606,7 +631,7 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             drop_graph(h);
             return CUPSO_OK;
         case CUPSO_OPT_SYNC_KERNEL:
-            if (value < CUPSO_SYNC_KERNEL_AUTO || value > CUPSO_SYNC_KERNEL_PIPELINED4)
+            if (value < CUPSO_SYNC_KERNEL_AUTO || value > CUPSO_SYNC_KERNEL_TILED)
                 return fail(CUPSO_ERR_INVALID_ARG, "unknown sync kernel%s");
             h->sync_kernel = (int)value;
             drop_graph(h);
@@ -663,7 +688,7 @@ int cupso_step(cupso_handle h, int iters) {
         h->t_host += (uint32_t)iters;
         return CUPSO_OK;
     }
-    const bool pipelined = !h->fp64 && mode == CUPSO_MODE_SYNC && sync_stages(h) > 0;
+    const bool pipelined = !h->fp64 && mode == CUPSO_MODE_SYNC && sync_tile(h) == 0 && sync_stages(h) > 0;
     if (!pipelined) {
         const int rc = ensure_materialized(h);
         if (rc) return rc;
@@ -957,12 +982,15 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
         info->onchip_cluster = h->onchip_cluster;
         info->sync_stages = 0;
         info->sync_ppt = 0;
+        info->sync_tile = 0;
     } else {
-        info->sync_grid = sync_grid(h);
+        const int tile = sync_tile(h);
+        info->sync_grid = tile ? std::min(tiled_grid(h, tile), (h->N + tile - 1) / tile) : sync_grid(h);
         info->async_grid = async_grid(h);
         info->onchip_cluster = h->onchip_cluster;
-        info->sync_stages = sync_stages(h);
-        info->sync_ppt = sync_stages(h) ? sync_ppt(h) : 0;
+        info->sync_stages = tile ? 0 : sync_stages(h);
+        info->sync_ppt = (!tile && sync_stages(h)) ? sync_ppt(h) : 0;
+        info->sync_tile = tile;
     }
     info->fitness_ms = 0.0f;
     info->fitness_timed = 0;

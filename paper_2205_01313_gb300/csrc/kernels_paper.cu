@@ -730,6 +730,7 @@ __global__ void __launch_bounds__(kOnchip64Threads) onchip64_kernel(const __grid
 // ---------------------------------------------------------------------------
 constexpr int kTileItems = 2048;     // P * D per block at most (32 KB of x' and terms)
 constexpr int kTileMinD = 16;        // below this the one-particle-per-thread step is used
+constexpr int kChunk64 = 4;          // items whose loads a thread issues together
 
 template <int FIT>
 __global__ void __launch_bounds__(256) sync64_tile_kernel(const __grid_constant__ SwarmDev64 s,
@@ -750,17 +751,35 @@ __global__ void __launch_bounds__(256) sync64_tile_kernel(const __grid_constant_
     const int nD = n * D;
     const double* G = s.G + (size_t)cur * D;
 
-    for (int e = tid; e < nD; e += blockDim.x) {
-        const int d = e / n, p = e - d * n;
-        const uint32_t i = (uint32_t)(base + p);
-        const size_t off = (size_t)d * Np + i;
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, t, s.swarm), s.key0, s.key1);
-        double xx = s.x[off], vv = s.v[off];
-        move_one64(xx, vv, s.pb[off], G[d], r, s);
-        s.x[off] = xx;
-        s.v[off] = vv;
-        X[d * P + p] = xx;
-        if constexpr (!FitTerms64<FIT>::kNeedsNext && FIT != kSphere) H[d * P + p] = FitTerms64<FIT>::term(xx, 0.0);
+    // a thread loads the rows of kChunk64 items before it computes any of them
+    for (int e0 = tid; e0 < nD; e0 += kChunk64 * blockDim.x) {
+        double xs[kChunk64], vs[kChunk64], ps[kChunk64];
+#pragma unroll
+        for (int c = 0; c < kChunk64; ++c) {
+            const int e = e0 + c * blockDim.x;
+            if (e < nD) {
+                const int d = e / n, p = e - d * n;
+                const size_t off = (size_t)d * Np + (size_t)(base + p);
+                xs[c] = s.x[off];
+                vs[c] = s.v[off];
+                ps[c] = s.pb[off];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChunk64; ++c) {
+            const int e = e0 + c * blockDim.x;
+            if (e >= nD) break;
+            const int d = e / n, p = e - d * n;
+            const uint32_t i = (uint32_t)(base + p);
+            const size_t off = (size_t)d * Np + i;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, t, s.swarm), s.key0, s.key1);
+            double xx = xs[c], vv = vs[c];
+            move_one64(xx, vv, ps[c], G[d], r, s);
+            s.x[off] = xx;
+            s.v[off] = vv;
+            X[d * P + p] = xx;
+            if constexpr (!FitTerms64<FIT>::kNeedsNext && FIT != kSphere) H[d * P + p] = FitTerms64<FIT>::term(xx, 0.0);
+        }
     }
     __syncthreads();
     if constexpr (FitTerms64<FIT>::kNeedsNext) {

@@ -101,6 +101,7 @@ def test_async_after_pipelined_sync_steps(P):
     kernel that reads pbest_pos directly must see them written back."""
     fid, N, D = 3, 3000, 9
     with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 4, mode="sync") as s:
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
         assert s.info()["sync_stages"] > 0
         s.step(6)
         s.set_mode("async")

@@ -13,8 +13,8 @@ from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, ora
 
 pytestmark = pytest.mark.gpu
 
-SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "sync_ppt1", "sync_ppt2", "tree", "tree_unrolled",
-              "onchip", "queue"]
+SYNC_MODES = ["sync", "sync_register", "sync_pipelined3", "sync_ppt1", "sync_ppt2", "sync_tiled", "tree",
+              "tree_unrolled", "onchip", "queue"]
 
 
 @pytest.fixture(scope="module")
@@ -50,6 +50,14 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_stages"] == 3
     with gpu_swarm(P, 3, 5000, 2, 1, "sync_pipelined4") as s:   # too few dimension pairs: register kernel
         assert s.info()["sync_stages"] == 0
+    with gpu_swarm(P, 1, 20000, 16, 1, "sync") as s:            # few particles per SM, D >= 8: tiled
+        assert s.info()["sync_tile"] == 32 and s.info()["sync_stages"] == 0
+    with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:
+        assert s.info()["sync_tile"] == 32
+    with gpu_swarm(P, 3, 65536, 128, 1, "sync") as s:           # no cos: streaming from ~224 per SM
+        assert s.info()["sync_tile"] == 0
+    with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming
+        assert s.info()["sync_tile"] == 0
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])
@@ -110,6 +118,23 @@ def test_single_step_from_shared_state(P, mode):
     assert idx == ref.gbest_idx and st["t"] == 42
 
 
+@pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("N,D", [(1, 1), (37, 2), (600, 9), (3000, 128), (200, 300), (33, 4096)])
+def test_tiled_kernel_bit_exact(P, fid, N, D):
+    """The tiled SYNC kernel over tile sizes from 1 to 32 particles (D up to
+    4096), ragged last tiles and odd D."""
+    T = 9
+    with gpu_swarm(P, fid, N, D, 23, "sync_tiled") as s:
+        assert s.info()["sync_tile"] > 0
+        s.step(T)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 23).init().step_sync(T)
+    assert rc == P.CUPSO_OK
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
 def test_modes_interchangeable_mid_run(P):
     fid, N, D = 1, 2048, 12
     with gpu_swarm(P, fid, N, D, 21, "sync") as s:
@@ -123,10 +148,13 @@ def test_modes_interchangeable_mid_run(P):
         s.set_mode("queue")
         s.step(4)
         s.set_mode("sync")
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["tiled"])
+        s.step(3)
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
         s.step(2)
         st = s.state()
         _, fit, idx, pos = s.gbest()
-    ref = oracle_swarm(fid, N, D, 21).init().step_sync(30)
+    ref = oracle_swarm(fid, N, D, 21).init().step_sync(33)
     assert_state_equal(st, ref)
     assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 

@@ -50,6 +50,10 @@ def parse():
                     choices=sorted(workloads.CONFIGS) + ["batch512", "lsq8192", "modes:sphere_1024x32",
                                                          "modes:rastrigin_65536x128", "paper:table2",
                                                          "paper:table3", "paper:table4"])
+    ap.add_argument("--batch-swarms", type=int, default=512, help="batch512: number of swarms (a smaller batch for profiling)")
+    ap.add_argument("--paper-rows", default="", help="paper:*: comma-separated particle counts to run (default: all rows)")
+    ap.add_argument("--paper-modes", default="", help="paper:*: comma-separated modes (default: the table's designs and ours)")
+    ap.add_argument("--paper-iters", type=int, default=0, help="paper:*: cap on the iterations per row (0: the table's)")
     ap.add_argument("--plain-sample", type=int, default=1,
                     help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto",
@@ -79,6 +83,12 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units all ranks processed / the slowest rank's time (weak scaling: each
+    rank runs its own replica of the workload)."""
+    return units_per_rank * world / seconds
 
 
 def max_over_ranks(x, world, device=None):
@@ -203,8 +213,11 @@ def run_ours(a):
     info = sw.info()
     mode_used = {v: k for k, v in P.MODES.items()}[info["mode"]]
     if mode_used == "sync":
-        mode_used = "sync (%s kernel)" % ("pipelined, %d-stage ring" % info["sync_stages"]
-                                          if info["sync_stages"] else "register")
+        if info["sync_tile"]:
+            mode_used = "sync (tiled kernel, %d particles per tile)" % info["sync_tile"]
+        else:
+            mode_used = "sync (%s kernel)" % ("pipelined, %d-stage ring" % info["sync_stages"]
+                                              if info["sync_stages"] else "register")
 
     for _ in range(a.warmup):
         sw.step(1)
@@ -243,7 +256,7 @@ def run_ours(a):
     sw.close()
 
     work = float(N) * D * K * world
-    value = work / (total_ms / 1e3)
+    value = whole_job_rate(float(N) * D * K, world, total_ms / 1e3)
     bpl = algorithmic_bytes(N, D)
     achieved = bpl / (per_launch_ms / 1e3) / 1e9
     peak, peak_src = hbm_peak()
@@ -263,7 +276,8 @@ def run_ours(a):
         "gpu_launches": K,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": measured_traffic(a.workload),
-                     "kernel": "sync_pipelined_kernel" if info["sync_stages"] else "sync_step_kernel",
+                     "kernel": ("sync_tiled_kernel" if info["sync_tile"] else
+                                "sync_pipelined_kernel" if info["sync_stages"] else "sync_step_kernel"),
                      "algorithmic_bytes_per_launch": bpl,
                      "launch_ms": per_launch_ms, "peak_source": peak_src},
         "clocks": clk,
@@ -304,6 +318,9 @@ REF_SAMPLE_N = 1 << 14
 def run_reference(a):
     world, rank, _ = dist_setup("gloo")
     if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
         return
     from oracle import build as OB
     OB.build_oracle()
@@ -331,6 +348,9 @@ def run_reference(a):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # --------------------------------------------------------------------------- #
@@ -355,7 +375,7 @@ def run_batch(a):
     B.build()
     from paper_2205_01313_gb300 import cupso as P
 
-    probs = workloads.batch_problems()
+    probs = workloads.batch_problems(n_swarms=a.batch_swarms)
     iters = BATCH_ITERS
     total_pd = sum(p["N"] * p["D"] for p in probs) * iters
     stream = torch.cuda.Stream()
@@ -566,6 +586,12 @@ def run_modes(a, name):
     print(json.dumps(out), flush=True)
 
 
+def spec_iters(spec, N):
+    """Iterations of the paper's row for N (Table 4 gives one per row)."""
+    cols = dict(zip(spec["columns"], spec["rows"][N]))
+    return int(cols.get("iters", spec.get("iters", 0)))
+
+
 def run_paper(a, table):
     """The paper's own experiments in its precision (FP64): Eq. 3 maximised,
     w = 1, c1 = c2 = 2, the shapes of Table 2 (1D, N = 32..2048, 100,000
@@ -591,14 +617,21 @@ def run_paper(a, table):
     modes = {"table2": ["tree", "tree_unrolled", "queue", "queue_lock", "sync", "onchip"],
              "table3": ["queue_lock", "sync", "onchip"],
              "table4": ["queue", "sync", "onchip"]}[table]
+    if a.paper_modes:
+        modes = [m for m in a.paper_modes.split(",") if m]
+    want_rows = {int(x) for x in a.paper_rows.split(",") if x}
     S = workloads.PAPER_SETTING
     D = spec["D"]
     stream = torch.cuda.Stream()
     rows = []
     cpu_total = 0.0
     for N, paper in spec["rows"].items():
+        if want_rows and N not in want_rows:
+            continue
         cols = dict(zip(spec["columns"], paper))
         T = int(cols.pop("iters", spec.get("iters", 0)))
+        if a.paper_iters > 0:
+            T = min(T, a.paper_iters)
         row = {"N": N, "D": D, "iters": T, "paper_seconds": cols, "seconds": {}, "final_gbest_fit": {}}
         for mode in modes:
             with P.Swarm(D, N, S["bounds"], S["w"], S["c1"], S["c2"], S["fitness_id"], S["seed"],
@@ -617,11 +650,11 @@ def run_paper(a, table):
                 row["seconds"][mode] = e0.elapsed_time(e1) / 1e3
                 rc, fit, _, _ = s.gbest()
                 row["final_gbest_fit"][mode] = fit if rc == P.CUPSO_OK else "status %d" % rc
-        ours = {m: row["seconds"][m] for m in ("sync", "onchip") if m in row["seconds"]}
+        ours = {m: row["seconds"][m] for m in ("sync", "onchip") if m in row["seconds"]} or dict(row["seconds"])
         best_mode = min(ours, key=ours.get)
         row["ours_best"] = best_mode
         paper_best_gpu = min(v for k, v in cols.items() if k != "cpu")
-        row["paper_best_gpu_over_ours"] = paper_best_gpu / ours[best_mode]
+        row["paper_best_gpu_over_ours"] = paper_best_gpu * (T / spec_iters(spec, N)) / ours[best_mode]
         # this box's serial FP64 baseline: a bounded prefix of the same run, scaled
         k = max(1, min(T, int(2e6 // (N * D))))
         o = O.Swarm64(N, D, *S["bounds"], S["w"], S["c1"], S["c2"], S["fitness_id"], S["seed"]).init()

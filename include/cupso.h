@@ -266,7 +266,10 @@ typedef struct {
  * included) on `cuda_stream` (NULL: an internal stream) and wait. Each
  * swarm's result equals what cupso_create with seed and swarm_id, then
  * cupso_step(iters), would give. Returns CUPSO_OK if every swarm succeeded,
- * else the first failing status; results[k].status holds each swarm's. */
+ * else the first failing status; results[k].status holds each swarm's.
+ * Every iteration of all swarms is one launch; the kernel and launch shape
+ * are tuned on the first iterations (the environment variable
+ * CUPSO_BATCH_KERNEL=tiled or =streaming fixes the kernel instead). */
 CUPSO_API int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters,
                       cupso_result* results, void* cuda_stream);
 

@@ -3,11 +3,15 @@
 // All swarms of a batch live in one device arena. Each is initialised by the
 // ordinary Step-1 kernel, then every iteration is ONE launch of
 // batch_step_kernel covering the units of all swarms (kernels_batch.cu); the
-// `iters` launches are replayed from captured CUDA graphs. The launch shape
-// (ring depth, CTAs per SM) is chosen online: the first iterations of the
-// real run are timed under each candidate shape and the fastest one runs the
-// rest -- every shape computes the same bits, so tuning costs no extra work.
-// Choices are remembered per batch shape for the life of the process.
+// `iters` launches are replayed from captured CUDA graphs. Two kernels can
+// run the step: the streaming one (kernels_batch.cu: 128-particle units per
+// warp, rows staged through a cp.async ring) and the tiled one
+// (kernels_tiled.cu: tiles of P particles with all their dimensions per CTA,
+// P chosen per swarm so that tiles cost about the same). The launch shape
+// (kernel, ring depth, CTAs per SM) is chosen online: the first iterations of
+// the real run are timed under each candidate shape and the fastest one runs
+// the rest -- every shape computes the same bits, so tuning costs no extra
+// work. Choices are remembered per batch shape for the life of the process.
 //
 // Swarms with fewer than three dimensions (too few dimension pairs for the
 // ring's look-ahead) are solved one by one through their own handles.
@@ -17,6 +21,7 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -26,6 +31,7 @@
 #include "../../include/cupso.h"
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "tiled_kernels.h"
 
 using namespace cupso;
 
@@ -34,7 +40,7 @@ namespace {
 size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Shape {
-    int stages;
+    int stages;          // ring depth of the streaming kernel; 0: the tiled kernel
     int minb;            // register budget: CTAs per SM
     int blocks_per_sm;   // CTAs per SM launched
 };
@@ -46,6 +52,7 @@ std::map<std::tuple<int, long long, int, int>, Shape> g_tuned;
 struct BatchRun {
     cudaStream_t st = nullptr;
     BatchDev dev{};
+    BatchTiles tiles{};
     int num_sms = 1;
     cudaGraphExec_t graph = nullptr;
     Shape graph_shape{0, 0, 0};
@@ -55,8 +62,11 @@ struct BatchRun {
         if (graph) cudaGraphExecDestroy(graph);
     }
 
-    cudaError_t launch(const Shape& sh) {
-        return launch_batch_step(dev, sh.stages, sh.minb, num_sms * sh.blocks_per_sm, st);
+    cudaError_t launch(const Shape& sh) { return launch_on(sh, st); }
+
+    cudaError_t launch_on(const Shape& sh, cudaStream_t s) {
+        if (sh.stages == 0) return launch_batch_tiled(dev, tiles, num_sms * sh.blocks_per_sm, s);
+        return launch_batch_step(dev, sh.stages, sh.minb, num_sms * sh.blocks_per_sm, s);
     }
 
     // `n` iterations with shape `sh`, through a captured graph of up to 32 launches.
@@ -72,7 +82,7 @@ struct BatchRun {
             e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
             cudaError_t le = cudaSuccess;
             for (int k = 0; k < L && e == cudaSuccess && le == cudaSuccess; ++k)
-                le = launch_batch_step(dev, sh.stages, sh.minb, num_sms * sh.blocks_per_sm, cap);
+                le = launch_on(sh, cap);
             cudaGraph_t g = nullptr;
             cudaError_t ee = e == cudaSuccess ? cudaStreamEndCapture(cap, &g) : e;
             cudaStreamDestroy(cap);
@@ -170,7 +180,9 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         const size_t A = 256;
         std::vector<size_t> o_state(nb), o_G(nb), o_flag(nb);
         std::vector<int> Np(nb);
-        size_t off = 0, total_units = 0, sumG = 0, sumFlag = 0;
+        size_t off = 0, total_units = 0, sumG = 0, sumFlag = 0, total_tiles = 0;
+        std::vector<int> tileP(nb);
+        std::vector<unsigned> ntiles(nb);
         int minD = 1 << 30, maxD = 0;
         long long total_pd = 0;
         for (int j = 0; j < nb; ++j) {
@@ -183,6 +195,9 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
             o_flag[j] = sumFlag;
             sumFlag += (size_t)Np[j];
             total_units += (size_t)Np[j] / 128;
+            tileP[j] = batch_tile_particles(p.D);
+            ntiles[j] = tileP[j] > 0 ? (unsigned)((p.N + tileP[j] - 1) / tileP[j]) : 0u;
+            total_tiles += ntiles[j];
             minD = std::min(minD, p.D);
             maxD = std::max(maxD, p.D);
             total_pd += (long long)p.N * p.D;
@@ -193,6 +208,9 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         const size_t o_flags = off; off = up(off + sumFlag, A);
         const size_t o_desc = off; off = up(off + sizeof(BatchSwarm) * nb, A);
         const size_t o_units = off; off = up(off + sizeof(uint2) * total_units, A);
+        const size_t o_tunits = off; off = up(off + sizeof(uint2) * std::max<size_t>(total_tiles, 1), A);
+        const size_t o_tileP = off; off = up(off + sizeof(int) * nb, A);
+        const size_t o_ntiles = off; off = up(off + sizeof(unsigned) * nb, A);
         const size_t o_ctr = off; off = up(off + 64, A);
         e = cudaMalloc(&arena, off);
         if (e != cudaSuccess) { set_cuda_error(e, "cudaMalloc (batch arena)"); rc = e == cudaErrorMemoryAllocation ? CUPSO_ERR_OOM : CUPSO_ERR_CUDA; break; }
@@ -285,11 +303,42 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         run.dev.ticket = ctr + 2;
         run.dev.t_dev = ctr + 3;
 
+        // The tiled kernel's units: tiles of the swarms with the most dimensions
+        // first, swarms of equal D interleaved.
+        const bool tiled_ok = maxD <= kTiledItems;
+        if (tiled_ok) {
+            std::vector<uint2> tunits;
+            tunits.reserve(total_tiles);
+            for (size_t pos = 0; pos < (size_t)nb;) {
+                size_t endg = pos;
+                while (endg < (size_t)nb && desc[order[endg]].D == desc[order[pos]].D) ++endg;
+                unsigned most = 0;
+                for (size_t q = pos; q < endg; ++q) most = std::max(most, ntiles[order[q]]);
+                for (unsigned u = 0; u < most; ++u)
+                    for (size_t q = pos; q < endg; ++q)
+                        if (u < ntiles[order[q]]) tunits.push_back(make_uint2((unsigned)order[q], u));
+                pos = endg;
+            }
+            e = cudaMemcpyAsync(base + o_tunits, tunits.data(), sizeof(uint2) * tunits.size(), cudaMemcpyHostToDevice,
+                                run.st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(base + o_tileP, tileP.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, run.st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(base + o_ntiles, ntiles.data(), sizeof(unsigned) * nb, cudaMemcpyHostToDevice,
+                                    run.st);
+            if (e != cudaSuccess) { set_cuda_error(e, "cudaMemcpyAsync"); rc = CUPSO_ERR_CUDA; break; }
+            run.tiles.units = reinterpret_cast<const uint2*>(base + o_tunits);
+            run.tiles.nunits = (unsigned)tunits.size();
+            run.tiles.P = reinterpret_cast<const int*>(base + o_tileP);
+            run.tiles.ntiles = reinterpret_cast<const unsigned*>(base + o_ntiles);
+        }
+
         // Launch shapes to try: ring depth 4 needs three dimension pairs everywhere.
         std::vector<Shape> cand;
         if ((minD + 1) / 2 >= 3) cand.push_back(Shape{4, 2, batch_blocks_per_sm(4, 2)});
         cand.push_back(Shape{3, 2, batch_blocks_per_sm(3, 2)});
         cand.push_back(Shape{3, 3, batch_blocks_per_sm(3, 3)});
+        if (tiled_ok) cand.push_back(Shape{0, 0, batch_tiled_blocks_per_sm()});
         const auto key = std::make_tuple(nb, total_pd, minD, maxD);
         Shape best = cand[0];
         bool known = false;
@@ -297,6 +346,18 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
             std::lock_guard<std::mutex> lk(g_tune_mutex);
             auto it = g_tuned.find(key);
             if (it != g_tuned.end()) { best = it->second; known = true; }
+        }
+        // CUPSO_BATCH_KERNEL=tiled|streaming fixes the kernel instead of tuning
+        // (for tests and measurements; both kernels give the same bits).
+        if (const char* force = std::getenv("CUPSO_BATCH_KERNEL")) {
+            const bool want_tiled = std::strcmp(force, "tiled") == 0;
+            const bool want_stream = std::strcmp(force, "streaming") == 0;
+            if (want_tiled && !tiled_ok) { set_last_error("CUPSO_BATCH_KERNEL=tiled: D too large"); rc = CUPSO_ERR_UNSUPPORTED; break; }
+            if (want_tiled || want_stream) {
+                for (const Shape& sh : cand)
+                    if ((sh.stages == 0) == want_tiled) { best = sh; break; }
+                known = true;
+            }
         }
         int done_iters = 0;
         const int probe = 2;

@@ -88,6 +88,49 @@ __device__ __forceinline__ void move_w(float& x, float& v, float pb, float g, ui
     }
 }
 
+// FitAcc with the fitness chosen at run time (uniform for a unit): the same
+// operations in the same order as FitAcc<FIT>, so the batch kernel carries one
+// copy of the unit loop instead of one per fitness function.
+struct FitAccRT {
+    float acc = 0.0f, acc2 = 0.0f, prev = 0.0f;
+    __device__ __forceinline__ void add(int fid, int d, float x) {
+        switch (fid) {
+            case kSphere: acc = __fmaf_rn(x, x, acc); break;
+            case kRastrigin: {
+                const float ten_minus = __fmaf_rn(-10.0f, cos2pi(x), 10.0f);
+                acc = __fadd_rn(acc, __fmaf_rn(x, x, ten_minus));
+                break;
+            }
+            case kAckley:
+                acc = __fmaf_rn(x, x, acc);
+                acc2 = __fadd_rn(acc2, cos2pi(x));
+                break;
+            case kRosenbrock:
+                if (d > 0) {
+                    const float p = __fmaf_rn(-prev, prev, x);
+                    const float q = __fsub_rn(1.0f, prev);
+                    acc = __fadd_rn(acc, __fmaf_rn(__fmul_rn(100.0f, p), p, __fmul_rn(q, q)));
+                }
+                prev = x;
+                break;
+            default: {
+                const float h = __fmaf_rn(__fmaf_rn(__fsub_rn(x, 0.8f), x, -1000.0f), x, 8000.0f);
+                acc = __fadd_rn(acc, h);
+                break;
+            }
+        }
+    }
+    __device__ __forceinline__ float finish(int fid, int D) const {
+        if (fid == kAckley) {
+            FitAcc<kAckley> a;
+            a.acc = acc;
+            a.acc2 = acc2;
+            return a.finish(D);
+        }
+        return fid == kCubicMax ? -acc : acc;
+    }
+};
+
 // The per-warp pipeline state carried from one unit to the next.
 struct Pipe {
     Unit nxt;        // the unit after the current one (fetched when first needed)
@@ -97,10 +140,12 @@ struct Pipe {
 };
 
 // Process unit `cu` of the batch at iteration t; keeps STAGES-1 pairs in flight.
-template <int FIT, bool FAST, int STAGES>
+template <int STAGES>
 __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, float4* my, Unit cu, Pipe& pp,
                                          uint32_t t, int lane_id) {
     const BatchSwarm& w = b.swarms[cu.sw];
+    const int fid = w.fid;
+    const bool fast = w.fast != 0;
     const int D = w.D, npairs = (D + 1) >> 1;
     const size_t Np = (size_t)w.Np;
     const int cur = (int)((t - 1u) & 1u), nxt = cur ^ 1;
@@ -108,7 +153,7 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     const unsigned long long K = __ldcg(w.gkey + cur);
     const uint32_t i0 = cu.u * kUnitB + (uint32_t)lane_id * 4;
     const uint32_t fl = __ldcg(reinterpret_cast<const unsigned int*>(w.pflag + i0));
-    FitAcc<FIT> acc[4];
+    FitAccRT acc[4];
     float4 PF = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int g = 0; g < npairs; ++g) {
         {
@@ -152,10 +197,11 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float xj = lane(X, j), vj = lane(V, j);
-                move_w<FAST>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
+                if (fast) move_w<true>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
+                else move_w<false>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
                 set_lane(X, j, xj);
                 set_lane(V, j, vj);
-                acc[j].add(d, xj);
+                acc[j].add(fid, d, xj);
             }
             st4(w.x + off, X);
             st4(w.v + off, V);
@@ -168,7 +214,7 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     bool nan = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float f = acc[j].finish(D);
+        const float f = acc[j].finish(fid, D);
         const bool real = (i0 + j) < (uint32_t)w.N;
         nan |= real && (f != f);
         if (real && f < lane(PF, j)) {
@@ -213,13 +259,6 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     pp.ig -= npairs;
 }
 
-template <int FIT, int STAGES>
-__device__ __forceinline__ void run_unit_any(const BatchDev& b, unsigned* work, float4* my, Unit cu, Pipe& pp,
-                                             uint32_t t, int lane_id) {
-    if (b.swarms[cu.sw].fast) run_unit<FIT, true, STAGES>(b, work, my, cu, pp, t, lane_id);
-    else run_unit<FIT, false, STAGES>(b, work, my, cu, pp, t, lane_id);
-}
-
 }  // namespace
 
 // One iteration of every swarm of the batch. Iteration t = *t_dev + 1.
@@ -243,13 +282,7 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_step_kernel(const __grid_c
     for (int j = 0; j < STAGES - 1; ++j) issue(b, my, cu, j, j, lane_id);
     pp.ig = STAGES - 1;
     while (cu.sw != 0xFFFFFFFFu) {
-        switch (b.swarms[cu.sw].fid) {
-            case kSphere: run_unit_any<kSphere, STAGES>(b, work, my, cu, pp, t, lane_id); break;
-            case kRastrigin: run_unit_any<kRastrigin, STAGES>(b, work, my, cu, pp, t, lane_id); break;
-            case kAckley: run_unit_any<kAckley, STAGES>(b, work, my, cu, pp, t, lane_id); break;
-            case kRosenbrock: run_unit_any<kRosenbrock, STAGES>(b, work, my, cu, pp, t, lane_id); break;
-            default: run_unit_any<kCubicMax, STAGES>(b, work, my, cu, pp, t, lane_id); break;
-        }
+        run_unit<STAGES>(b, work, my, cu, pp, t, lane_id);
         if (!pp.have_nxt) {
             pp.nxt = fetch(b, work, lane_id);
         }

@@ -23,7 +23,7 @@ namespace cupso {
 namespace {
 
 constexpr int kTiledThreads = 256;
-constexpr int kChunk = 4;     // items whose loads a thread issues together
+constexpr int kChunk = 4;     // dimension pairs whose loads a thread issues together
 
 // Fitness from per-dimension terms; sum() equals FitAcc<FIT> over d in order.
 template <int FIT>
@@ -72,104 +72,265 @@ struct FitTerms {
     }
 };
 
+// Fitness chosen at run time (a batch mixes them): FIT = kAnyFit dispatches on
+// `fid`, uniformly for a whole tile; a fixed FIT compiles to its own code.
+constexpr int kAnyFit = -1;
+
+template <int FIT>
+__device__ __forceinline__ bool needs_next(int fid) {
+    if constexpr (FIT != kAnyFit) return FitTerms<FIT>::kNeedsNext;
+    else return fid == kRosenbrock;
+}
+
+template <int FIT>
+__device__ __forceinline__ bool has_term(int fid) {
+    if constexpr (FIT != kAnyFit) return !FitTerms<FIT>::kNoTerm;
+    else return fid != kSphere;
+}
+
+template <int FIT>
+__device__ __forceinline__ float tile_term(int fid, float x, float xn) {
+    if constexpr (FIT != kAnyFit) {
+        return FitTerms<FIT>::term(x, xn);
+    } else {
+        switch (fid) {
+            case kRastrigin: return FitTerms<kRastrigin>::term(x, xn);
+            case kAckley: return FitTerms<kAckley>::term(x, xn);
+            case kRosenbrock: return FitTerms<kRosenbrock>::term(x, xn);
+            case kCubicMax: return FitTerms<kCubicMax>::term(x, xn);
+            default: return 0.0f;
+        }
+    }
+}
+
+template <int FIT>
+__device__ __forceinline__ float tile_sum(int fid, const float* X, const float* H, int P, int p, int D) {
+    if constexpr (FIT != kAnyFit) {
+        return FitTerms<FIT>::sum(X, H, P, p, D);
+    } else {
+        switch (fid) {
+            case kSphere: return FitTerms<kSphere>::sum(X, H, P, p, D);
+            case kRastrigin: return FitTerms<kRastrigin>::sum(X, H, P, p, D);
+            case kAckley: return FitTerms<kAckley>::sum(X, H, P, p, D);
+            case kRosenbrock: return FitTerms<kRosenbrock>::sum(X, H, P, p, D);
+            default: return FitTerms<kCubicMax>::sum(X, H, P, p, D);
+        }
+    }
+}
+
+// A swarm as the tile step sees it (one swarm of SwarmDev, or of a batch).
+struct TileSwarm {
+    float *x, *v, *pb, *pf;
+    unsigned char* pflag;   // lazy-pbest flags left by the streaming kernels, or null
+    const float* G;         // gbest_pos at the end of the previous iteration [D]
+    int N, D, Np;
+    float lo, hi, vmax, w, c1, c2, c1s, c2s;
+    uint32_t key0, key1, swarm;
+};
+
+// Eq. 1 and Eq. 2 for one element; FAST: c * r as one FMA of c 2^-24 with the
+// 24-bit integer of the draw and min/max clamps (bit-identical when valid).
+template <bool FAST>
+__device__ __forceinline__ void move_tile(float& x, float& v, float pb, float g, uint32_t w1, uint32_t w2,
+                                          const TileSwarm& s) {
+    const float cognitive = __fsub_rn(pb, x);
+    const float social = __fsub_rn(g, x);
+    float vel = __fmul_rn(s.w, v);
+    if constexpr (FAST) {
+        vel = __fmaf_rn(__fmaf_rn(s.c1s, hi24(w1), s.c1s), cognitive, vel);
+        vel = __fmaf_rn(__fmaf_rn(s.c2s, hi24(w2), s.c2s), social, vel);
+        v = clampf_minmax(vel, -s.vmax, s.vmax);
+        x = clampf_minmax(__fadd_rn(x, v), s.lo, s.hi);
+    } else {
+        vel = __fmaf_rn(__fmul_rn(s.c1, u01(w1)), cognitive, vel);
+        vel = __fmaf_rn(__fmul_rn(s.c2, u01(w2)), social, vel);
+        v = clampf(vel, -s.vmax, s.vmax);
+        x = clampf(__fadd_rn(x, v), s.lo, s.hi);
+    }
+}
+
+// Steps 2-4 for the tile of P particles starting at `base` (all D dimensions)
+// at iteration t; the tile's Step-5 candidates (improved and below K) are
+// folded into `best`. Every thread of the block calls it; it ends with a
+// barrier, so X, H and imp can be reused at once.
+template <int FIT, bool FAST>
+__device__ __forceinline__ void process_tile(const TileSwarm& s, int fid, int P, int base, uint32_t t,
+                                             unsigned long long K, float* X, float* H, int* imp,
+                                             unsigned long long& best, bool& nan) {
+    const int tid = threadIdx.x;
+    const int D = s.D, npairs = (D + 1) >> 1;
+    const size_t Np = (size_t)s.Np;
+    // every thread keeps one particle lane p; P (a power of two) divides blockDim
+    const int p = tid & (P - 1);
+    const int row0 = tid / P, rows = blockDim.x / P;
+    const int n = min(P, s.N - base);
+    const bool live = p < n;
+    const uint32_t i = (uint32_t)(base + p);
+    // a particle flagged by the lazy write-back has pbest_pos == pos: use and write it
+    const bool lazy = live && s.pflag && s.pflag[i];
+    // Step 2 (Eq. 1, Eq. 2): one Philox call per (dimension pair, particle). A
+    // thread loads the rows of kChunk pairs before it computes any of them, so
+    // that all of those loads are in flight together.
+    for (int g0 = row0; g0 < npairs; g0 += kChunk * rows) {
+        float xs[kChunk][2], vs[kChunk][2], ps[kChunk][2];
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            const int g = g0 + c * rows;
+            if (live && g < npairs) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int d = min(2 * g + h, D - 1);
+                    const size_t off = (size_t)d * Np + i;
+                    xs[c][h] = s.x[off];
+                    vs[c][h] = s.v[off];
+                    ps[c][h] = lazy ? xs[c][h] : s.pb[off];
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+            const int g = g0 + c * rows;
+            if (!live || g >= npairs) break;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)g, i, t, s.swarm), s.key0, s.key1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int d = 2 * g + h;
+                if (d >= D) break;
+                const size_t off = (size_t)d * Np + i;
+                if (lazy) s.pb[off] = ps[c][h];
+                float x = xs[c][h], v = vs[c][h];
+                move_tile<FAST>(x, v, ps[c][h], s.G[d], word(r, 2 * h), word(r, 2 * h + 1), s);
+                s.x[off] = x;
+                s.v[off] = v;
+                X[d * P + p] = x;
+                if (!needs_next<FIT>(fid) && has_term<FIT>(fid)) H[d * P + p] = tile_term<FIT>(fid, x, 0.0f);
+            }
+        }
+    }
+    __syncthreads();
+    if (needs_next<FIT>(fid)) {
+        if (live)
+            for (int d = row0; d + 1 < D; d += rows)
+                H[d * P + p] = tile_term<FIT>(fid, X[d * P + p], X[(d + 1) * P + p]);
+        __syncthreads();
+    }
+    // Steps 3-4: the ordered sum, strict improvement, the candidate
+    if (tid < n) {
+        const float f = tile_sum<FIT>(fid, X, H, P, tid, D);
+        const uint32_t ip = (uint32_t)(base + tid);
+        nan |= (f != f);
+        const bool better = f < s.pf[ip];
+        imp[tid] = better ? 1 : 0;
+        if (better) {
+            s.pf[ip] = f;
+            const unsigned long long k = pack_key(f, ip);
+            if (k < K && k < best) best = k;
+        }
+        if (s.pflag && s.pflag[ip]) s.pflag[ip] = 0;
+    }
+    __syncthreads();
+    if (live && imp[p])
+        for (int d = row0; d < D; d += rows) s.pb[(size_t)d * Np + i] = X[d * P + p];
+    __syncthreads();
+}
+
 template <int FIT, bool FAST>
 __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_constant__ SwarmDev s, int P) {
     __shared__ float X[kTiledItems];
     __shared__ float H[kTiledItems];
     __shared__ unsigned long long red[kTiledThreads / 32];
-    __shared__ int imp[32];
+    __shared__ int imp[kTiledMaxP];
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
     const unsigned long long K = __ldcg(s.gkey + cur);   // gbest at the end of t-1
-    const int tid = threadIdx.x;
-    const int D = s.D, npairs = (D + 1) >> 1;
-    const size_t Np = (size_t)s.Np;
-    const float* G = s.G + (size_t)cur * D;
-    // Every thread keeps one particle lane p of the tile; blockDim is a
-    // multiple of 32, so P (a power of two up to 32) divides it.
-    const int p = tid & (P - 1);
-    const int row0 = tid / P, rows = blockDim.x / P;
+    const TileSwarm ts{s.x, s.v, s.pb, s.pf, nullptr, s.G + (size_t)cur * s.D, s.N, s.D, s.Np, s.lo, s.hi, s.vmax,
+                       s.w, s.c1, s.c2, s.c1s, s.c2s, s.key0, s.key1, s.swarm};
     const int ntiles = (s.N + P - 1) / P;
-
     unsigned long long best = kKeyNone;
     bool nan = false;
     // persistent: the block walks the tiles with a stride of the grid
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int base = tile * P;
-        const int n = min(P, s.N - base);
-        const bool live = p < n;
-        const uint32_t i = (uint32_t)(base + p);
-        // Steps 2 (Eq. 1, Eq. 2): one Philox call per (dimension pair, particle).
-        // A thread loads the rows of kChunk pairs before it computes any of them,
-        // so that all of those loads are in flight together.
-        for (int g0 = row0; g0 < npairs; g0 += kChunk * rows) {
-            float xs[kChunk][2], vs[kChunk][2], ps[kChunk][2];
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) {
-                const int g = g0 + c * rows;
-                if (live && g < npairs) {
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int d = min(2 * g + h, D - 1);
-                        const size_t off = (size_t)d * Np + i;
-                        xs[c][h] = s.x[off];
-                        vs[c][h] = s.v[off];
-                        ps[c][h] = s.pb[off];
-                    }
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < kChunk; ++c) {
-                const int g = g0 + c * rows;
-                if (!live || g >= npairs) break;
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)g, i, t, s.swarm), s.key0, s.key1);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int d = 2 * g + h;
-                    if (d >= D) break;
-                    const size_t off = (size_t)d * Np + i;
-                    float x = xs[c][h], v = vs[c][h];
-                    if constexpr (FAST)
-                        move_one_fast(x, v, ps[c][h], G[d], hi24(word(r, 2 * h)), hi24(word(r, 2 * h + 1)), s);
-                    else
-                        move_one(x, v, ps[c][h], G[d], u01(word(r, 2 * h)), u01(word(r, 2 * h + 1)), s);
-                    s.x[off] = x;
-                    s.v[off] = v;
-                    X[d * P + p] = x;
-                    if constexpr (!FitTerms<FIT>::kNeedsNext && !FitTerms<FIT>::kNoTerm)
-                        H[d * P + p] = FitTerms<FIT>::term(x, 0.0f);
-                }
-            }
-        }
-        __syncthreads();
-        if constexpr (FitTerms<FIT>::kNeedsNext) {
-            if (live)
-                for (int d = row0; d + 1 < D; d += rows) H[d * P + p] = FitTerms<FIT>::term(X[d * P + p], X[(d + 1) * P + p]);
-            __syncthreads();
-        }
-        // Steps 3-4; the candidates of Step 5 (improved and below the current gbest key)
-        if (tid < n) {
-            const float f = FitTerms<FIT>::sum(X, H, P, tid, D);
-            const uint32_t ip = (uint32_t)(base + tid);
-            nan |= (f != f);
-            const bool better = f < s.pf[ip];
-            imp[tid] = better ? 1 : 0;
-            if (better) {
-                s.pf[ip] = f;
-                const unsigned long long k = pack_key(f, ip);
-                if (k < K && k < best) best = k;
-            }
-        }
-        __syncthreads();
-        if (live && imp[p])
-            for (int d = row0; d < D; d += rows) s.pb[(size_t)d * Np + i] = X[d * P + p];
-        __syncthreads();   // X, H and imp are reused by the next tile
-    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+        process_tile<FIT, FAST>(ts, FIT, P, tile * P, t, K, X, H, imp, best, nan);
     best = block_min(best, red);
-    if (tid == 0 && best != kKeyNone) atomicMin(s.gkey + nxt, best);
-    if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
+    if (threadIdx.x == 0 && best != kKeyNone) atomicMin(s.gkey + nxt, best);
+    if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
     finish_iteration(s, cur, nxt, t);
+}
+
+// One iteration of every swarm of a batch, in tiles: CTAs take (swarm, tile)
+// units from a counter (the order is the host's: costliest first); each unit
+// ends with the swarm's conditional atomicMin, and the CTA that completes a
+// swarm's last tile gathers that swarm's gbest_pos. The kernel boundary is the
+// only barrier between iterations, so every swarm follows its own
+// synchronous trajectory.
+__global__ void __launch_bounds__(kTiledThreads, 3) batch_tiled_kernel(const __grid_constant__ BatchDev b,
+                                                                   const __grid_constant__ BatchTiles bt) {
+    __shared__ float X[kTiledItems];
+    __shared__ float H[kTiledItems];
+    __shared__ unsigned long long red[kTiledThreads / 32];
+    __shared__ int imp[kTiledMaxP];
+    __shared__ uint2 s_unit;
+    __shared__ int s_last;
+    const uint32_t t_prev = __ldcg(b.t_dev);
+    const uint32_t t = t_prev + 1u;
+    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
+    unsigned* work = b.work + (t & 1u);
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) {
+            const unsigned k = atomicAdd(work, 1u);
+            s_unit = k < bt.nunits ? bt.units[k] : make_uint2(0xFFFFFFFFu, 0u);
+        }
+        __syncthreads();
+        const uint2 un = s_unit;
+        if (un.x == 0xFFFFFFFFu) break;
+        const BatchSwarm& w = b.swarms[un.x];
+        const int P = bt.P[un.x];
+        const unsigned long long K = __ldcg(w.gkey + cur);
+        const TileSwarm ts{w.x, w.v, w.pb, w.pf, w.pflag, w.G + (size_t)cur * w.D, w.N, w.D, w.Np, w.lo, w.hi,
+                           w.vmax, w.w, w.c1, w.c2, w.c1s, w.c2s, w.key0, w.key1, w.swarm};
+        unsigned long long best = kKeyNone;
+        bool nan = false;
+        if (w.fast) process_tile<kAnyFit, true>(ts, w.fid, P, (int)un.y * P, t, K, X, H, imp, best, nan);
+        else process_tile<kAnyFit, false>(ts, w.fid, P, (int)un.y * P, t, K, X, H, imp, best, nan);
+        best = block_min(best, red);
+        const bool any_nan = __syncthreads_or(nan);
+        // publish, then count the tile; the CTA that completes the swarm gathers its gbest
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            if (best < K) atomicMin(w.gkey + nxt, best);
+            if (any_nan) atomicOr(w.status, kStatusNaN);
+            __threadfence();
+            s_last = atomicAdd(w.done, 1u) == bt.ntiles[un.x] - 1u;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            const unsigned long long knew = __ldcg(w.gkey + nxt);
+            const uint32_t gi = (uint32_t)(knew & 0xFFFFFFFFull);
+            if (gi < (uint32_t)w.N)
+                for (int d = tid; d < w.D; d += blockDim.x)
+                    w.G[(size_t)nxt * w.D + d] = __ldcg(w.pb + (size_t)d * w.Np + gi);
+            __syncthreads();
+            if (tid == 0) {
+                w.gkey[cur] = knew;
+                *w.done = 0u;
+            }
+        }
+        __syncthreads();
+    }
+    // The last CTA rolls the batch forward: the next launch counts on the other counter.
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(b.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (s_last && tid == 0) {
+        b.work[(t + 1u) & 1u] = 0u;
+        *b.ticket = 0u;
+        *b.t_dev = t;
+    }
 }
 
 #define CUPSO_TILED_DISPATCH(fid, FASTV, CALL)                                   \
@@ -186,16 +347,32 @@ __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_
 
 int tiled_particles(int N, int D, int num_sms) {
     if (D > kTiledItems) return 0;
-    int P = 32;
+    int P = kTiledMaxP;
     while (P > 1 && (P * D > kTiledItems || (P > 4 && (long long)N < 2ll * num_sms * P))) P >>= 1;
     return P;
 }
 
+int batch_tile_particles(int D) {
+    if (D > kTiledItems) return 0;
+    int P = kTiledMaxP;
+    while (P > 1 && P * D > kTiledItems) P >>= 1;
+    return P;
+}
+
+namespace {
+// Threads of a tile block: enough for the tile's (pair, particle) items, a
+// multiple of 32 (so that P divides it) and at least P.
+int tile_threads(int P, int D) {
+    const int work = P * ((D + 1) / 2);
+    int th = work >= kTiledThreads ? kTiledThreads : (work + 31) / 32 * 32;
+    return th < P ? P : th;
+}
+}  // namespace
+
 cudaError_t launch_sync_tiled(const SwarmDev& s, int fid, int P, int grid, cudaStream_t st) {
-    if (P < 1 || P > 32 || P * s.D > kTiledItems) return cudaErrorInvalidValue;
+    if (P < 1 || P > kTiledMaxP || (P & (P - 1)) || P * s.D > kTiledItems) return cudaErrorInvalidValue;
     const int tiles = (s.N + P - 1) / P;
-    const int work = P * ((s.D + 1) / 2);
-    const int threads = work >= kTiledThreads ? kTiledThreads : (work + 31) / 32 * 32;
+    const int threads = tile_threads(P, s.D);
     const int g = grid < 1 ? 1 : (grid < tiles ? grid : tiles);
     if (s.fast_cr && s.fast_clamp) {
         CUPSO_TILED_DISPATCH(fid, true, (sync_tiled_kernel<F, true><<<g, threads, 0, st>>>(s, P)));
@@ -206,8 +383,7 @@ cudaError_t launch_sync_tiled(const SwarmDev& s, int fid, int P, int grid, cudaS
 }
 
 int tiled_blocks_per_sm(int fid, int P, int D) {
-    const int work = P * ((D + 1) / 2);
-    const int threads = work >= kTiledThreads ? kTiledThreads : (work + 31) / 32 * 32;
+    const int threads = tile_threads(P, D);
     int n = 0;
     cudaError_t e = cudaSuccess;
     switch (fid) {
@@ -222,6 +398,20 @@ int tiled_blocks_per_sm(int fid, int P, int D) {
         return 1;
     }
     return n < 1 ? 1 : n;
+}
+
+int batch_tiled_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_tiled_kernel, kTiledThreads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_batch_tiled(const BatchDev& b, const BatchTiles& bt, int grid, cudaStream_t st) {
+    batch_tiled_kernel<<<grid, kTiledThreads, 0, st>>>(b, bt);
+    return cudaGetLastError();
 }
 
 }  // namespace cupso

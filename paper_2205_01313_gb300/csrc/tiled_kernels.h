@@ -9,11 +9,29 @@
 namespace cupso {
 
 constexpr int kTiledItems = 4096;   // P * D per tile at most (x' and the fitness terms in shared memory)
+constexpr int kTiledMaxP = 256;     // particles per tile at most (one per thread)
 
-// Particles per tile for (N, D) on num_sms SMs: a power of two up to 32, at
-// most kTiledItems / D, and (down to 4) small enough that the tiles cover the
-// SMs twice over. 0 when D > kTiledItems.
+// The tiles of a batch: (swarm, tile) units in hand-out order, and per swarm
+// its particles per tile and tile count.
+struct BatchTiles {
+    const uint2* units;
+    unsigned int nunits;
+    const int* P;
+    const unsigned int* ntiles;
+};
+
+// Particles per tile for (N, D) on num_sms SMs: a power of two up to
+// kTiledMaxP, at most kTiledItems / D, and (down to 4) small enough that the
+// tiles cover the SMs twice over. 0 when D > kTiledItems.
 int tiled_particles(int N, int D, int num_sms);
+
+// Particles per tile of a batch swarm with D dimensions: the largest power of
+// two up to kTiledMaxP with P * D <= kTiledItems (tiles of similar cost).
+int batch_tile_particles(int D);
+
+// One iteration of every swarm of a batch, in tiles; `grid` CTAs.
+cudaError_t launch_batch_tiled(const BatchDev& b, const BatchTiles& bt, int grid, cudaStream_t st);
+int batch_tiled_blocks_per_sm();
 
 // One iteration (Steps 2-5) with tiles of P particles; `grid` blocks walk the
 // tiles (at most one block per tile).

@@ -51,7 +51,7 @@ def test_sync_kernel_selection(P):
     with gpu_swarm(P, 3, 5000, 2, 1, "sync_pipelined4") as s:   # too few dimension pairs: register kernel
         assert s.info()["sync_stages"] == 0
     with gpu_swarm(P, 1, 20000, 16, 1, "sync") as s:            # few particles per SM, D >= 8: tiled
-        assert s.info()["sync_tile"] == 32 and s.info()["sync_stages"] == 0
+        assert s.info()["sync_tile"] == 64 and s.info()["sync_stages"] == 0   # 64 x 16 items, 313 tiles
     with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:
         assert s.info()["sync_tile"] == 32
     with gpu_swarm(P, 3, 65536, 128, 1, "sync") as s:           # no cos: streaming from ~224 per SM
@@ -332,6 +332,36 @@ def test_batched_solve_matches_oracle(P, iters):
         assert res[k]["status"] == P.CUPSO_OK
         assert res[k]["idx"] == ref.gbest_idx, k
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "streaming"])
+def test_batched_solve_each_kernel_matches_oracle(P, kernel, monkeypatch):
+    """Both batch kernels, fixed instead of tuned: every swarm equals its oracle
+    run (tiles of 1 to 256 particles with D from 3 to 300)."""
+    monkeypatch.setenv("CUPSO_BATCH_KERNEL", kernel)
+    probs = _mixed_batch(20, 11, (40, 3000), (3, 300))
+    rc, res = P.cupso_solve_batch(probs, 12)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"]).init().step_sync(12)
+        assert res[k]["status"] == P.CUPSO_OK
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
+def test_batched_kernels_interchange_with_lazy_pbest(P, monkeypatch):
+    """The tuner may switch kernels between iterations of one solve; the
+    streaming kernel leaves pbest rows pending (lazy write-back) and the tiled
+    kernel must take them over. Forcing a long enough solve to tune covers
+    the hand-over; the results must still be the oracle's."""
+    monkeypatch.delenv("CUPSO_BATCH_KERNEL", raising=False)
+    probs = _mixed_batch(12, 13, (100, 2000), (6, 64))
+    rc, res = P.cupso_solve_batch(probs, 40)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"]).init().step_sync(40)
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["pos"], ref.gbest_pos), k
 
 
 def test_batched_solve_repeatable(P):

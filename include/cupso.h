@@ -131,8 +131,8 @@ typedef enum {
     CUPSO_SYNC_KERNEL_PIPELINED4 = 3, /* the same, 3 pairs ahead                            */
     CUPSO_SYNC_KERNEL_TILED = 4       /* a tile of particles with all their dimensions per block,
                                          the (dimension pair, particle) items spread over threads;
-                                         AUTO uses it for D >= 8 up to about 224 particles per SM
-                                         (896 for Rastrigin and Ackley)                         */
+                                         AUTO uses it for D >= 8 up to about 896 particles per SM
+                                         (224 for D > 64 without cos(2 pi x) in the fitness)     */
 } cupso_sync_kernel;
 
 typedef struct {

@@ -110,15 +110,15 @@ int resolved_mode(const cupso_swarm* h) {
 // Particles per tile when the tiled SYNC kernel runs, else 0. AUTO takes it
 // for D >= 8 up to the crossover measured on a GB300 against the pipelined
 // kernel (which runs over d inside each thread and needs many particles per
-// SM to hide its row latency): about 224 particles per SM, or 896 for the
-// fitness functions with cos(2 pi x), whose extra arithmetic the tiled
-// layout spreads better.
+// SM to hide its row latency): about 896 particles per SM, or 224 when the
+// tiles are narrow (D > 64, so at most 32 particles per tile) and the fitness
+// is cheap (no cos(2 pi x) to spread over the threads).
 int sync_tile(const cupso_swarm* h) {
     if (h->fp64) return 0;
     if (h->sync_kernel == CUPSO_SYNC_KERNEL_TILED) return tiled_particles(h->N, h->D, h->num_sms);
     if (h->sync_kernel != CUPSO_SYNC_KERNEL_AUTO || h->D < 8) return 0;
     const bool has_cos = h->fid == CUPSO_RASTRIGIN || h->fid == CUPSO_ACKLEY;
-    const long long per_sm = has_cos ? 896 : 224;
+    const long long per_sm = (has_cos || h->D <= 64) ? 896 : 224;
     if ((long long)h->N > per_sm * h->num_sms) return 0;
     return tiled_particles(h->N, h->D, h->num_sms);
 }

@@ -273,15 +273,19 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
 }
 
 // FP64 Gram form of the rescoring, for D <= M: with Gm = A^T A, c = A^T b,
-// bb = b^T b (all FP64, computed once), f(x) = x^T Gm x - 2 c^T x + bb.
-// Block (group, chunk) handles 4 candidates (group 4g..4g+3) and the rows
-// r of the chunk: partial[cand][chunk] = sum_r x_r ((Gm x)_r - 2 c_r)
-// (+ bb in chunk 0). Rows in order per warp, warps in a fixed order.
+// bb = b^T b (all FP64, computed once), f(x) = x^T Gm x - 2 c^T x + bb. Gm is
+// symmetric, so only its upper triangle is read:
+//   f(x) = sum_r x_r (Gm_rr x_r + 2 sum_{c>r} Gm_rc x_c - 2 c_r) + bb.
+// Rows are taken in pairs (q, D-1-q), whose upper parts hold D-1 entries
+// together, so every warp gets the same work. Block (group, chunk) handles 4
+// candidates (group 4g..4g+3) and the pairs of its chunk:
+// partial[cand][chunk] = its rows' terms (+ bb in chunk 0), pairs in order per
+// warp, warps in a fixed order.
 __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_constant__ SwarmDev s,
                                                                const double* __restrict__ Gm,
                                                                const double* __restrict__ cvec, double bb,
                                                                const unsigned long long* __restrict__ top,
-                                                               int rows_per_chunk, int chunks,
+                                                               int pairs_per_chunk, int chunks,
                                                                double* __restrict__ partial) {
     extern __shared__ double xg[];            // [4][D]
     __shared__ double wsum[8][4];
@@ -298,21 +302,30 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = chunk * rows_per_chunk, r1 = min(D, r0 + rows_per_chunk);
+    const int npairs = (D + 1) / 2;
+    const int p0 = chunk * pairs_per_chunk, p1 = min(npairs, p0 + pairs_per_chunk);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};   // lane 0: this warp's rows, in order
-    for (int r = r0 + warp; r < r1; r += 8) {
-        const double* row = Gm + (size_t)r * D;
-        double y[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int d = lane; d < D; d += 32) {
-            const double g = row[d];
+    for (int pr = p0 + warp; pr < p1; pr += 8) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) y[q] = fma(g, xg[q * D + d], y[q]);
-        }
+        for (int side = 0; side < 2; ++side) {
+            const int r = side == 0 ? pr : D - 1 - pr;
+            if (side == 1 && r == pr) break;   // the middle row of an odd D
+            const double* row = Gm + (size_t)r * D;
+            double y[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int c = r + 1 + lane; c < D; c += 32) {
+                const double g = row[c];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double v = y[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-            acc[q] = fma(xg[q * D + r], v - 2.0 * cvec[r], acc[q]);
+                for (int q = 0; q < 4; ++q) y[q] = fma(g, xg[q * D + c], y[q]);
+            }
+            const double grr = row[r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                double v = y[q];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                const double xr = xg[q * D + r];
+                const double inner = fma(grr, xr, fma(2.0, v, -2.0 * cvec[r]));
+                acc[q] = fma(xr, inner, acc[q]);
+            }
         }
     }
     if (lane == 0)
@@ -486,9 +499,9 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (gram.Gm) {
-        const int rows = (s.D + chunks - 1) / chunks;
+        const int pairs = ((s.D + 1) / 2 + chunks - 1) / chunks;
         lsq_rescore_gram_kernel<<<dim3(kCand / 4, chunks), 256, sizeof(double) * 4 * (size_t)s.D, st>>>(
-            s, gram.Gm, gram.cvec, gram.bb, top, rows, chunks, partial);
+            s, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial);
     } else {
         const int rows = (M + chunks - 1) / chunks;
         lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, A, b, M, top, rows,

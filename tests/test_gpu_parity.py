@@ -54,8 +54,10 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_tile"] == 64 and s.info()["sync_stages"] == 0   # 64 x 16 items, 313 tiles
     with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:
         assert s.info()["sync_tile"] == 32
-    with gpu_swarm(P, 3, 65536, 128, 1, "sync") as s:           # no cos: streaming from ~224 per SM
+    with gpu_swarm(P, 3, 65536, 128, 1, "sync") as s:           # narrow tiles, no cos: streaming from ~224 per SM
         assert s.info()["sync_tile"] == 0
+    with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to ~896 per SM
+        assert s.info()["sync_tile"] == 128
     with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming
         assert s.info()["sync_tile"] == 0
 

@@ -312,7 +312,20 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
             if (side == 1 && r == pr) break;   // the middle row of an odd D
             const double* row = Gm + (size_t)r * D;
             double y[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int c = r + 1 + lane; c < D; c += 32) {
+            int c = r + 1 + lane;
+            // four row loads in flight per lane (the loop is bound by their latency)
+            for (; c + 96 < D; c += 128) {
+                const double g0 = row[c], g1 = row[c + 32], g2 = row[c + 64], g3 = row[c + 96];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const double* xq = xg + q * D + c;
+                    y[q] = fma(g0, xq[0], y[q]);
+                    y[q] = fma(g1, xq[32], y[q]);
+                    y[q] = fma(g2, xq[64], y[q]);
+                    y[q] = fma(g3, xq[96], y[q]);
+                }
+            }
+            for (; c < D; c += 32) {
                 const double g = row[c];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) y[q] = fma(g, xg[q * D + c], y[q]);

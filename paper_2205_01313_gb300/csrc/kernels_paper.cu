@@ -31,6 +31,7 @@
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
 #include "paper_kernels.h"
+#include "pdl.cuh"
 #include "stream_common.cuh"
 
 namespace cg = cooperative_groups;
@@ -283,6 +284,8 @@ __global__ void __launch_bounds__(kPaperBlock) paper_step_kernel(const __grid_co
     __shared__ PKey red[kPaperBlock];   // tree operands, or the queue
     __shared__ unsigned int qn;
     __shared__ int s_last;
+    pdl_wait();
+    pdl_launch_next();
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
@@ -411,6 +414,8 @@ __global__ void __launch_bounds__(1024) paper_finish_kernel(const __grid_constan
                                                             const __grid_constant__ PaperBufs b, int nblocks) {
     __shared__ PKey red[1024];
     __shared__ unsigned int qn;
+    pdl_wait();
+    pdl_launch_next();
     const int tid = threadIdx.x;
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur = (int)(t_prev & 1u);
@@ -740,6 +745,8 @@ __global__ void __launch_bounds__(256) sync64_tile_kernel(const __grid_constant_
     __shared__ PKey red[32];
     __shared__ int imp[32];
     __shared__ int s_last;
+    pdl_wait();
+    pdl_launch_next();
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
@@ -896,14 +903,14 @@ PaperBufs paper_bufs_at(void* base, int Np, int list_cap) {
 cudaError_t launch_queue_step(const SwarmDev& s, const PaperBufs& b, int fid, bool lock, cudaStream_t st) {
     const int nb = paper_blocks(s.N);
     if (lock) {
-        CUPSO_DISPATCH_FIT32(fid, (paper_step_kernel<Fp32, F, kAggQueueLock><<<nb, kPaperBlock, 0, st>>>(s, b)));
-        return cudaGetLastError();
+        CUPSO_DISPATCH_FIT32(fid, return launch_pdl(paper_step_kernel<Fp32, F, kAggQueueLock>, dim3(nb),
+                                                    dim3(kPaperBlock), 0, st, s, b));
     }
-    CUPSO_DISPATCH_FIT32(fid, (paper_step_kernel<Fp32, F, kAggQueue><<<nb, kPaperBlock, 0, st>>>(s, b)));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    CUPSO_DISPATCH_FIT32(fid, e = launch_pdl(paper_step_kernel<Fp32, F, kAggQueue>, dim3(nb), dim3(kPaperBlock), 0, st,
+                                             s, b));
     if (e != cudaSuccess) return e;
-    paper_finish_kernel<Fp32, kAggQueue, true><<<1, 1024, 0, st>>>(s, b, nb);
-    return cudaGetLastError();
+    return launch_pdl(paper_finish_kernel<Fp32, kAggQueue, true>, dim3(1), dim3(1024), 0, st, s, b, nb);
 }
 
 bool fp64_fitness_supported(int fid) { return fid == kSphere || fid == kRosenbrock || fid == kCubicMax; }
@@ -934,37 +941,30 @@ cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int 
         const int tiles = (s.N + P - 1) / P;
         if ((unsigned int)tiles > b.list_cap) return cudaErrorInvalidConfiguration;
         const int threads = P * s.D >= 256 ? 256 : (P * s.D + 31) / 32 * 32;
-        CUPSO_DISPATCH_FIT64(fid, (sync64_tile_kernel<F><<<tiles, threads, 0, st>>>(s, b, P)));
-        return cudaGetLastError();
+        CUPSO_DISPATCH_FIT64(fid, return launch_pdl(sync64_tile_kernel<F>, dim3(tiles), dim3(threads), 0, st, s, b, P));
     }
+    const dim3 g1(nb), b1(kPaperBlock), g2(1), b2(1024);
+    cudaError_t e = cudaSuccess;
     switch (agg) {
         case kAggReduce:
-            CUPSO_DISPATCH_FIT64(fid, (paper_step_kernel<Fp64, F, kAggReduce><<<nb, kPaperBlock, 0, st>>>(s, b)));
-            break;
+            CUPSO_DISPATCH_FIT64(fid, e = launch_pdl(paper_step_kernel<Fp64, F, kAggReduce>, g1, b1, 0, st, s, b));
+            if (e != cudaSuccess) return e;
+            return launch_pdl(paper_finish_kernel<Fp64, kAggReduce, true>, g2, b2, 0, st, s, b, nb);
         case kAggReduceUnrolled:
-            CUPSO_DISPATCH_FIT64(fid,
-                                 (paper_step_kernel<Fp64, F, kAggReduceUnrolled><<<nb, kPaperBlock, 0, st>>>(s, b)));
-            break;
+            CUPSO_DISPATCH_FIT64(fid, e = launch_pdl(paper_step_kernel<Fp64, F, kAggReduceUnrolled>, g1, b1, 0, st, s, b));
+            if (e != cudaSuccess) return e;
+            return launch_pdl(paper_finish_kernel<Fp64, kAggReduceUnrolled, true>, g2, b2, 0, st, s, b, nb);
         case kAggQueue:
-            CUPSO_DISPATCH_FIT64(fid, (paper_step_kernel<Fp64, F, kAggQueue><<<nb, kPaperBlock, 0, st>>>(s, b)));
-            break;
+            CUPSO_DISPATCH_FIT64(fid, e = launch_pdl(paper_step_kernel<Fp64, F, kAggQueue>, g1, b1, 0, st, s, b));
+            if (e != cudaSuccess) return e;
+            return launch_pdl(paper_finish_kernel<Fp64, kAggQueue, true>, g2, b2, 0, st, s, b, nb);
         case kAggQueueLock:
-            CUPSO_DISPATCH_FIT64(fid, (paper_step_kernel<Fp64, F, kAggQueueLock><<<nb, kPaperBlock, 0, st>>>(s, b)));
-            return cudaGetLastError();
+            CUPSO_DISPATCH_FIT64(fid, return launch_pdl(paper_step_kernel<Fp64, F, kAggQueueLock>, g1, b1, 0, st, s, b));
         case kAggSyncList:
-            CUPSO_DISPATCH_FIT64(fid, (paper_step_kernel<Fp64, F, kAggSyncList><<<nb, kPaperBlock, 0, st>>>(s, b)));
-            return cudaGetLastError();
+            CUPSO_DISPATCH_FIT64(fid, return launch_pdl(paper_step_kernel<Fp64, F, kAggSyncList>, g1, b1, 0, st, s, b));
         default:
             return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    switch (agg) {
-        case kAggReduce: paper_finish_kernel<Fp64, kAggReduce, true><<<1, 1024, 0, st>>>(s, b, nb); break;
-        case kAggReduceUnrolled: paper_finish_kernel<Fp64, kAggReduceUnrolled, true><<<1, 1024, 0, st>>>(s, b, nb); break;
-        default: paper_finish_kernel<Fp64, kAggQueue, true><<<1, 1024, 0, st>>>(s, b, nb); break;
-    }
-    return cudaGetLastError();
 }
 
 namespace {

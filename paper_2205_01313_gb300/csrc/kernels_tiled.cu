@@ -15,6 +15,7 @@
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "pdl.cuh"
 #include "stream_common.cuh"
 #include "tiled_kernels.h"
 
@@ -240,6 +241,8 @@ __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_
     __shared__ float H[kTiledItems];
     __shared__ unsigned long long red[kTiledThreads / 32];
     __shared__ int imp[kTiledMaxP];
+    pdl_wait();
+    pdl_launch_next();
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
@@ -375,11 +378,11 @@ cudaError_t launch_sync_tiled(const SwarmDev& s, int fid, int P, int grid, cudaS
     const int threads = tile_threads(P, s.D);
     const int g = grid < 1 ? 1 : (grid < tiles ? grid : tiles);
     if (s.fast_cr && s.fast_clamp) {
-        CUPSO_TILED_DISPATCH(fid, true, (sync_tiled_kernel<F, true><<<g, threads, 0, st>>>(s, P)));
+        CUPSO_TILED_DISPATCH(fid, true, return launch_pdl(sync_tiled_kernel<F, true>, dim3(g), dim3(threads), 0, st, s, P));
     } else {
-        CUPSO_TILED_DISPATCH(fid, false, (sync_tiled_kernel<F, false><<<g, threads, 0, st>>>(s, P)));
+        CUPSO_TILED_DISPATCH(fid, false, return launch_pdl(sync_tiled_kernel<F, false>, dim3(g), dim3(threads), 0, st, s, P));
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 int tiled_blocks_per_sm(int fid, int P, int D) {

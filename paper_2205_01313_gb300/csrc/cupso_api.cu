@@ -177,7 +177,18 @@ int async_block(const cupso_swarm* h) {
     return (h->Np / kTile >= 2 * h->num_sms) ? kBlock : 32;
 }
 
+// Particles per tile of the tiled asynchronous kernel (0: the streaming one).
+int async_tile(const cupso_swarm* h) {
+    if (h->fp64 || h->D < 2) return 0;
+    return tiled_particles(h->N, h->D, h->num_sms);
+}
+
 int async_grid(const cupso_swarm* h) {
+    if (const int P = async_tile(h)) {
+        const int tiles = (h->N + P - 1) / P;
+        const int g = h->grid_override > 0 ? h->grid_override : h->num_sms * async_tiled_blocks_per_sm(P, h->D);
+        return g < tiles ? g : tiles;
+    }
     const int tile = async_block(h) * kPerThread;
     const int ntiles = (h->Np + tile - 1) / tile;
     const int per_sm = async_blocks_per_sm(h->fid, h->D) * (kBlock / async_block(h));
@@ -695,8 +706,11 @@ int cupso_step(cupso_handle h, int iters) {
     }
     cudaError_t e = cudaSuccess;
     if (mode == CUPSO_MODE_ASYNC) {
-        e = launch_async(h->dev, h->fid, async_grid(h), async_block(h), h->t_host + 1u, iters, h->hold_lock,
-                         h->stream);
+        if (const int P = async_tile(h))
+            e = launch_async_tiled(h->dev, h->fid, P, async_grid(h), h->t_host + 1u, iters, h->hold_lock, h->stream);
+        else
+            e = launch_async(h->dev, h->fid, async_grid(h), async_block(h), h->t_host + 1u, iters, h->hold_lock,
+                             h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "async launch");
     } else if (mode == CUPSO_MODE_ONCHIP) {
         e = launch_onchip(h->dev, h->fid, iters, h->stream);

@@ -13,6 +13,7 @@
 // conditional atomicMin on the packed key, the last CTA gathers gbest_pos.
 #include <cuda_runtime.h>
 
+#include "async_common.cuh"
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
 #include "pdl.cuh"
@@ -261,6 +262,67 @@ __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_
     finish_iteration(s, cur, nxt, t);
 }
 
+// The asynchronous variant in tiles (Sec. 3.2 taken to its end, Sec. 6): a
+// persistent CTA owns the tiles blockIdx.x, blockIdx.x + gridDim.x, ... and
+// iterates over them with no grid barrier. Each of its iterations reads the
+// latest gbest record (sequence lock), runs the tile step over its tiles and
+// publishes its best improvement under the lock. Random draws stay keyed on
+// (t, particle), so only the gbest each particle sees depends on timing; with
+// one CTA the run is the synchronous one.
+template <int FIT, bool FAST>
+__global__ void __launch_bounds__(kTiledThreads) async_tiled_kernel(const __grid_constant__ SwarmDev s, int P,
+                                                                   uint32_t t_first, int iters) {
+    __shared__ float X[kTiledItems];
+    __shared__ float H[kTiledItems];
+    __shared__ unsigned long long red[kTiledThreads / 32];
+    __shared__ int imp[kTiledMaxP];
+    __shared__ int s_stop;
+    __shared__ int s_last;
+    extern __shared__ float Gs[];   // [D] the gbest this CTA's iteration uses
+    const int tid = threadIdx.x;
+    const int ntiles = (s.N + P - 1) / P;
+    const TileSwarm ts{s.x, s.v, s.pb, s.pf, nullptr, Gs, s.N, s.D, s.Np, s.lo, s.hi, s.vmax,
+                       s.w, s.c1, s.c2, s.c1s, s.c2s, s.key0, s.key1, s.swarm};
+    for (int k = 0; k < iters; ++k) {
+        const uint32_t t = t_first + (uint32_t)k;
+        if (tid == 0) s_stop = (__ldcg(s.status) & kStatusTimeout) != 0u;
+        __syncthreads();
+        if (s_stop) break;
+        if (!read_record(s, Gs)) {
+            if (tid == 0) atomicOr(s.status, kStatusTimeout);
+            break;
+        }
+        const unsigned long long K = __ldcg(s.claim);
+        unsigned long long best = kKeyNone;
+        bool nan = false;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+            process_tile<FIT, FAST>(ts, FIT, P, tile * P, t, K, X, H, imp, best, nan);
+        if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
+        best = block_min(best, red);   // ends with a barrier: the pbest writes are visible
+        if (best != kKeyNone && tid < 32) {
+            if (!publish(s, best) && tid == 0) atomicOr(s.status, kStatusTimeout);
+        }
+        __syncthreads();
+    }
+    // The last CTA to finish hands the record back to the synchronous state.
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(s.ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const uint32_t t_end = t_first - 1u + (uint32_t)iters;
+    const int cur = (int)(t_end & 1u);
+    for (int d = tid; d < s.D; d += blockDim.x) s.G[(size_t)cur * s.D + d] = __ldcg(s.Grec + d);
+    if (tid == 0) {
+        const unsigned long long kk = __ldcg(s.reckey);
+        s.gkey[0] = kk;
+        s.gkey[1] = kk;
+        *s.t_dev = t_end;
+        *s.ticket = 0u;
+    }
+}
+
 // One iteration of every swarm of a batch, in tiles: CTAs take (swarm, tile)
 // units from a counter (the order is the host's: costliest first); each unit
 // ends with the swarm's conditional atomicMin, and the CTA that completes a
@@ -397,6 +459,33 @@ int tiled_blocks_per_sm(int fid, int P, int D) {
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sync_tiled_kernel<kCubicMax, true>, threads, 0); break;
     }
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n < 1 ? 1 : n;
+}
+
+cudaError_t launch_async_tiled(const SwarmDev& s, int fid, int P, int grid, uint32_t t_first, int iters,
+                               int hold_lock, cudaStream_t st) {
+    if (P < 1 || P > kTiledMaxP || (P & (P - 1)) || P * s.D > kTiledItems) return cudaErrorInvalidValue;
+    cudaError_t e = launch_async_prologue(s, hold_lock, st);
+    if (e != cudaSuccess) return e;
+    const int tiles = (s.N + P - 1) / P;
+    const int threads = tile_threads(P, s.D);
+    const int g = grid < 1 ? 1 : (grid < tiles ? grid : tiles);
+    const size_t smem = sizeof(float) * (size_t)s.D;
+    if (s.fast_cr && s.fast_clamp) {
+        CUPSO_TILED_DISPATCH(fid, true, (async_tiled_kernel<F, true><<<g, threads, smem, st>>>(s, P, t_first, iters)));
+    } else {
+        CUPSO_TILED_DISPATCH(fid, false, (async_tiled_kernel<F, false><<<g, threads, smem, st>>>(s, P, t_first, iters)));
+    }
+    return cudaGetLastError();
+}
+
+int async_tiled_blocks_per_sm(int P, int D) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, async_tiled_kernel<kRastrigin, true>, tile_threads(P, D),
+                                                      sizeof(float) * (size_t)D) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -29,6 +29,16 @@ int tiled_particles(int N, int D, int num_sms);
 // two up to kTiledMaxP with P * D <= kTiledItems (tiles of similar cost).
 int batch_tile_particles(int D);
 
+// The asynchronous mode in tiles: the record prologue, then `iters`
+// iterations of persistent CTAs with no grid barrier (iterations t_first ...).
+cudaError_t launch_async_tiled(const SwarmDev& s, int fid, int P, int grid, uint32_t t_first, int iters,
+                               int hold_lock, cudaStream_t st);
+int async_tiled_blocks_per_sm(int P, int D);
+
+// The record prologue of the asynchronous kernels (kernels_stream.cu):
+// gbest into the lock-protected record, lock released (or held, a test hook).
+cudaError_t launch_async_prologue(const SwarmDev& s, int hold_lock, cudaStream_t st);
+
 // One iteration of every swarm of a batch, in tiles; `grid` CTAs.
 cudaError_t launch_batch_tiled(const BatchDev& b, const BatchTiles& bt, int grid, cudaStream_t st);
 int batch_tiled_blocks_per_sm();

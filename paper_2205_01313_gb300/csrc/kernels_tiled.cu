@@ -243,7 +243,6 @@ __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_
     __shared__ unsigned long long red[kTiledThreads / 32];
     __shared__ int imp[kTiledMaxP];
     pdl_wait();
-    pdl_launch_next();
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
@@ -256,6 +255,9 @@ __global__ void __launch_bounds__(kTiledThreads) sync_tiled_kernel(const __grid_
     // persistent: the block walks the tiles with a stride of the grid
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
         process_tile<FIT, FAST>(ts, FIT, P, tile * P, t, K, X, H, imp, best, nan);
+    // The next iteration may start launching now: its blocks would otherwise
+    // take SM slots while this one still has tiles to run.
+    pdl_launch_next();
     best = block_min(best, red);
     if (threadIdx.x == 0 && best != kKeyNone) atomicMin(s.gkey + nxt, best);
     if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);

@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kOnchip64Threads) onchip64_kernel(const __grid
 // ---------------------------------------------------------------------------
 constexpr int kTileItems = 2048;     // P * D per block at most (32 KB of x' and terms)
 constexpr int kTileMinD = 16;        // below this the one-particle-per-thread step is used
-constexpr int kChunk64 = 4;          // items whose loads a thread issues together
+constexpr int kChunk64 = 1;          // items whose loads a thread issues together (more only costs occupancy: FP64-bound)
 
 template <int FIT>
 __global__ void __launch_bounds__(256) sync64_tile_kernel(const __grid_constant__ SwarmDev64 s,

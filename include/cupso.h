@@ -101,10 +101,13 @@ typedef enum {
     CUPSO_MODE_ONCHIP = 5, /* whole swarm in one CTA cluster's shared memory, many iterations per launch */
     CUPSO_MODE_QUEUE = 6,  /* the paper's queue design (Alg. 2): one particle per thread, a
                               shared-memory queue of the particles that beat gbest, a second kernel */
-    CUPSO_MODE_QUEUE_LOCK = 7 /* the paper's queue-lock design (Alg. 3): the queue, then thread 0 of
+    CUPSO_MODE_QUEUE_LOCK = 7, /* the paper's queue-lock design (Alg. 3): the queue, then thread 0 of
                               each block updates gbest in place under a global lock; one kernel. Blocks
                               later in the same launch may see an earlier block's update, so with more
                               than one block (N > 256) the trajectory depends on timing. */
+    CUPSO_MODE_PERSISTENT = 8 /* double-precision swarms: one cooperative launch runs all iterations of a
+                              cupso_step call, a grid-wide barrier per iteration in place of the kernel
+                              boundary (synchronous PSO, one particle per thread) */
 } cupso_mode;
 
 typedef enum {
@@ -225,8 +228,9 @@ CUPSO_API int cupso_get_gbest_f64(cupso_handle h, double* fit_out);
  * SYNC (one fused launch per iteration: block argmin, a candidate list, the
  * last block gathers gbest), TREE, TREE_UNROLLED, QUEUE, QUEUE_LOCK (the
  * paper's four designs, one particle per thread), ONCHIP (one CTA holds the
- * swarm in shared memory; only when it fits); AUTO picks ONCHIP when it
- * fits, else SYNC. ASYNC is not available. Use cupso_step, cupso_set_option,
+ * swarm in shared memory; only when it fits), PERSISTENT (one cooperative
+ * launch per cupso_step call); AUTO picks ONCHIP when it fits, else SYNC.
+ * ASYNC is not available. Use cupso_step, cupso_set_option,
  * cupso_get_info and cupso_destroy as for any handle, and the _fp64 accessors
  * below: the float accessors return CUPSO_ERR_UNSUPPORTED on such a handle. */
 CUPSO_API int cupso_create_fp64(int D, int N, const cupso_bounds_f64* bounds, double w, double c1, double c2,

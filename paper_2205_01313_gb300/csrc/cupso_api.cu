@@ -606,8 +606,10 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
     switch (key) {
         case CUPSO_OPT_MODE:
-            if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_QUEUE_LOCK)
+            if (value < CUPSO_MODE_AUTO || value > CUPSO_MODE_PERSISTENT)
                 return fail(CUPSO_ERR_INVALID_ARG, "unknown mode%s");
+            if (value == CUPSO_MODE_PERSISTENT && (!h->fp64 || h->D > 4096))
+                return fail(CUPSO_ERR_UNSUPPORTED, "the persistent mode serves double-precision swarms with D <= 4096%s");
             if (h->fp64) {
                 if (value == CUPSO_MODE_ASYNC)
                     return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarms have no ASYNC mode%s");
@@ -696,6 +698,12 @@ int cupso_step(cupso_handle h, int iters) {
     if (h->fp64 && mode == CUPSO_MODE_ONCHIP) {
         cudaError_t e = launch_onchip64(h->dev64, h->fid, iters, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "on-chip launch");
+        h->t_host += (uint32_t)iters;
+        return CUPSO_OK;
+    }
+    if (h->fp64 && mode == CUPSO_MODE_PERSISTENT) {
+        cudaError_t e = launch_persist64(h->dev64, h->pbufs, h->fid, iters, h->num_sms, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent launch");
         h->t_host += (uint32_t)iters;
         return CUPSO_OK;
     }

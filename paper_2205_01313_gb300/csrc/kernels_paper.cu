@@ -857,6 +857,113 @@ int tile_particles(int N, int D, int num_sms) {
     return P;
 }
 
+// ---------------------------------------------------------------------------
+// Persistent FP64 swarm (a cooperative launch, so every block is resident):
+// `iters` iterations, each ending with a grid barrier instead of a kernel
+// boundary. A block's Step-5 candidate goes to its own slot of a list
+// double-buffered by parity; after the barrier every block reduces the same
+// slots in the same order, so all hold the same gbest.
+// ---------------------------------------------------------------------------
+constexpr int kPersistThreads = 128;
+
+// Bounded grid barrier: thread 0 of every block arrives on a counter; the last
+// one resets it and advances the generation the others wait on. A wait past
+// the limit sets the timeout status and returns false.
+__device__ bool grid_barrier(const PaperBufs& b, unsigned int nblocks, long long limit_ns, unsigned int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int g = *reinterpret_cast<volatile unsigned int*>(b.bar_gen);
+        __threadfence();
+        if (atomicAdd(b.bar_count, 1u) == nblocks - 1u) {
+            *reinterpret_cast<volatile unsigned int*>(b.bar_count) = 0u;
+            __threadfence();
+            atomicAdd(b.bar_gen, 1u);
+        } else {
+            const long long deadline = global_ns() + limit_ns;
+            while (*reinterpret_cast<volatile unsigned int*>(b.bar_gen) == g) {
+                if (global_ns() > deadline) {
+                    ok = 0;
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int FIT>
+__global__ void __launch_bounds__(kPersistThreads) persist64_kernel(const __grid_constant__ SwarmDev64 s,
+                                                                   const __grid_constant__ PaperBufs b, int iters) {
+    extern __shared__ double Gsh[];   // [D] the current gbest
+    __shared__ PKey red[32];
+    const int tid = threadIdx.x;
+    const size_t Np = (size_t)s.Np;
+    const unsigned int nblk = gridDim.x;
+    const uint32_t stride = nblk * blockDim.x;
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const int cur0 = (int)(t_prev & 1u);
+    PKey K = Fp64::load_gkey(s, cur0);
+    for (int d = tid; d < s.D; d += blockDim.x) Gsh[d] = s.G[(size_t)cur0 * s.D + d];
+    __syncthreads();
+    bool nan = false;
+    int done = 0;
+    for (int k = 0; k < iters; ++k) {
+        const uint32_t t = t_prev + 1u + (uint32_t)k;
+        PKey cand = key_none();
+        for (uint32_t i = blockIdx.x * blockDim.x + tid; i < (uint32_t)s.N; i += stride) {
+            const double f = Fp64::step_particle<FIT>(s, i, t, Gsh);   // Steps 2-3
+            nan |= (f != f);
+            if (f < s.pf[i]) {                                          // Step 4
+                s.pf[i] = f;
+                for (int d = 0; d < s.D; ++d) s.pb[(size_t)d * Np + i] = s.x[(size_t)d * Np + i];
+                const PKey c = Fp64::key(f, i);
+                if (key_less(c, K) && key_less(c, cand)) cand = c;
+            }
+        }
+        const PKey mine = block_min_key(cand, red);
+        PKey* slots = b.list + (size_t)(k & 1) * nblk;
+        if (tid == 0) {
+            slots[blockIdx.x].k = mine.k;
+            slots[blockIdx.x].i = mine.i;
+        }
+        if (!grid_barrier(b, nblk, s.wait_limit_ns, s.status)) break;
+        // Step 5: the same reduction in every block
+        PKey m = K;
+        for (unsigned int j = tid; j < nblk; j += blockDim.x) {
+            PKey c;
+            c.k = __ldcg(&slots[j].k);
+            c.i = __ldcg(&slots[j].i);
+            c.pad = 0u;
+            if (key_less(c, m)) m = c;
+        }
+        const PKey nbest = block_min_key(m, red);
+        if (key_less(nbest, K)) {
+            K = nbest;
+            for (int d = tid; d < s.D; d += blockDim.x) Gsh[d] = __ldcg(s.pb + (size_t)d * Np + nbest.i);
+        }
+        __syncthreads();
+        done = k + 1;
+    }
+    if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
+    if (blockIdx.x == 0) {
+        const uint32_t t_end = t_prev + (uint32_t)done;
+        const int out = (int)(t_end & 1u);
+        for (int d = tid; d < s.D; d += blockDim.x) s.G[(size_t)out * s.D + d] = Gsh[d];
+        if (tid == 0) {
+            Fp64::store_gkey(s, 0, K);
+            Fp64::store_gkey(s, 1, K);
+            *s.t_dev = t_end;
+        }
+    }
+}
+
 #define CUPSO_DISPATCH_FIT32(fid, CALL)            \
     switch (fid) {                                 \
         case kSphere: { constexpr int F = kSphere; CALL; break; }         \
@@ -897,6 +1004,8 @@ PaperBufs paper_bufs_at(void* base, int Np, int list_cap) {
     b.lock = w;
     b.ticket = w + 1;
     b.list_n = w + 2;
+    b.bar_count = w + 3;
+    b.bar_gen = w + 4;
     return b;
 }
 
@@ -962,6 +1071,53 @@ cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int 
             CUPSO_DISPATCH_FIT64(fid, return launch_pdl(paper_step_kernel<Fp64, F, kAggQueueLock>, g1, b1, 0, st, s, b));
         case kAggSyncList:
             CUPSO_DISPATCH_FIT64(fid, return launch_pdl(paper_step_kernel<Fp64, F, kAggSyncList>, g1, b1, 0, st, s, b));
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+int persist64_grid(int fid, int N, int D, int num_sms) {
+    int per_sm = 0;
+    const size_t smem = sizeof(double) * (size_t)D;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (fid) {
+        case kSphere: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist64_kernel<kSphere>, kPersistThreads, smem); break;
+        case kRosenbrock: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist64_kernel<kRosenbrock>, kPersistThreads, smem); break;
+        case kCubicMax: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persist64_kernel<kCubicMax>, kPersistThreads, smem); break;
+        default: break;
+    }
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long want = ((long long)N + kPersistThreads - 1) / kPersistThreads;
+    const long long cap = (long long)per_sm * num_sms;
+    return (int)(want < cap ? want : cap);
+}
+
+cudaError_t launch_persist64(const SwarmDev64& s, const PaperBufs& b, int fid, int iters, int num_sms,
+                             cudaStream_t st) {
+    if (s.D > 4096) return cudaErrorInvalidValue;
+    const int grid = persist64_grid(fid, s.N, s.D, num_sms);
+    if (2u * (unsigned)grid > b.list_cap) return cudaErrorInvalidConfiguration;
+    // a barrier abandoned by a timed-out launch must not leave arrivals behind
+    cudaError_t me = cudaMemsetAsync(b.bar_count, 0, sizeof(unsigned int), st);
+    if (me != cudaSuccess) return me;
+    const size_t smem = sizeof(double) * (size_t)s.D;
+    int iters_arg = iters;
+    SwarmDev64 s_arg = s;
+    PaperBufs b_arg = b;
+    void* args[] = {&s_arg, &b_arg, &iters_arg};
+    switch (fid) {
+        case kSphere:
+            return cudaLaunchCooperativeKernel((const void*)persist64_kernel<kSphere>, dim3(grid), dim3(kPersistThreads),
+                                               args, smem, st);
+        case kRosenbrock:
+            return cudaLaunchCooperativeKernel((const void*)persist64_kernel<kRosenbrock>, dim3(grid),
+                                               dim3(kPersistThreads), args, smem, st);
+        case kCubicMax:
+            return cudaLaunchCooperativeKernel((const void*)persist64_kernel<kCubicMax>, dim3(grid),
+                                               dim3(kPersistThreads), args, smem, st);
         default:
             return cudaErrorInvalidValue;
     }

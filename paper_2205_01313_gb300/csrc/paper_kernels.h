@@ -32,6 +32,8 @@ struct PaperBufs {
     unsigned int* ticket;  // last-block counter of the one-kernel variants
     unsigned int* list_n;  // entries in `list`
     unsigned int list_cap; // capacity of `list`: no launch may have more blocks
+    unsigned int* bar_count;  // grid barrier of the persistent kernel: arrivals
+    unsigned int* bar_gen;    // and generation
 };
 
 // Device state of a double-precision swarm. Same layouts as SwarmDev:
@@ -95,6 +97,14 @@ cudaError_t launch_init64(const SwarmDev64& s, const PaperBufs& b, int fid, cuda
 // particle's dimensions over threads; num_sms sizes its tiles.
 cudaError_t launch_step64(const SwarmDev64& s, const PaperBufs& b, int fid, int agg, int num_sms, cudaStream_t st);
 cudaError_t launch_recompute64(const SwarmDev64& s, const PaperBufs& b, cudaStream_t st);
+// Persistent FP64 swarm: one cooperative launch runs `iters` synchronous
+// iterations, one particle per thread (looping when N exceeds the resident
+// threads), with a bounded grid barrier per iteration in place of the kernel
+// boundary.
+cudaError_t launch_persist64(const SwarmDev64& s, const PaperBufs& b, int fid, int iters, int num_sms,
+                             cudaStream_t st);
+int persist64_grid(int fid, int N, int D, int num_sms);
+
 // On-chip FP64 swarm: the whole swarm in the shared memory of one CTA cluster
 // (1 to 16 CTAs, chosen from (N, D) by onchip64_cluster), `iters` iterations
 // per launch. onchip64_fits says whether (N, D) fits at all.

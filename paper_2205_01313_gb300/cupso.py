@@ -25,8 +25,9 @@ CUPSO_ERR_NAN = -5
 CUPSO_ERR_UNSUPPORTED = -6
 
 (CUPSO_MODE_AUTO, CUPSO_MODE_SYNC, CUPSO_MODE_TREE, CUPSO_MODE_TREE_UNROLLED, CUPSO_MODE_ASYNC, CUPSO_MODE_ONCHIP,
- CUPSO_MODE_QUEUE, CUPSO_MODE_QUEUE_LOCK) = range(8)
-MODES = {"auto": 0, "sync": 1, "tree": 2, "tree_unrolled": 3, "async": 4, "onchip": 5, "queue": 6, "queue_lock": 7}
+ CUPSO_MODE_QUEUE, CUPSO_MODE_QUEUE_LOCK, CUPSO_MODE_PERSISTENT) = range(9)
+MODES = {"auto": 0, "sync": 1, "tree": 2, "tree_unrolled": 3, "async": 4, "onchip": 5, "queue": 6, "queue_lock": 7,
+         "persistent": 8}
 
 CUPSO_OPT_MODE = 1
 CUPSO_OPT_GRAPH_CHUNK = 2

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 PAPER = dict(bounds=(-100.0, 100.0, 20.0), w=1.0, c=2.0)          # Sec. 5.1: Eq. 3, w = 1, c1 = c2 = 2
 BOUNDS = {0: (-100.0, 100.0, 20.0), 3: (-30.0, 30.0, 6.0), 4: (-100.0, 100.0, 20.0)}
 W, C12 = 0.729, 1.49445
-STREAM_MODES = ["sync", "tree", "tree_unrolled", "queue"]
+STREAM_MODES = ["sync", "tree", "tree_unrolled", "queue", "persistent"]
 
 
 @pytest.fixture(scope="module")
@@ -227,6 +227,23 @@ def test_paper_workload_reaches_the_maximiser(P, mode):
     assert idx == int(np.flatnonzero(st["pbest_pos"][:, 0] == 100.0)[0])
 
 
+@pytest.mark.parametrize("N,D", [(1, 1), (129, 3), (8192, 1), (20000, 2), (300000, 1)])
+def test_persistent_bit_exact_fp64(P, N, D):
+    """The cooperative persistent kernel: all iterations of a cupso_step call in
+    one launch, a grid barrier per iteration (N = 300000 makes threads loop
+    over several particles)."""
+    fid, T = 4, 15
+    with gpu64(P, fid, N, D, 21, "persistent", **_paper_kw()) as s:
+        s.step(7)
+        s.step(T - 7)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = ora64(fid, N, D, 21, **_paper_kw()).init().step_sync(T)
+    assert rc == P.CUPSO_OK
+    assert_state64(st, ref)
+    assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
+
+
 def test_fp64_handle_rejections(P):
     with gpu64(P, 0, 300, 2, 1) as s:
         assert s.info()["mode"] == P.CUPSO_MODE_ONCHIP            # AUTO: the swarm fits one CTA
@@ -244,6 +261,9 @@ def test_fp64_handle_rejections(P):
             big.set_mode("onchip")
         assert e.value.code == P.CUPSO_ERR_UNSUPPORTED
     with P.Swarm(2, 300, (-1.0, 1.0, 0.5), W, C12, C12, 0, 1) as s32:
+        with pytest.raises(P.CupsoError) as e:
+            s32.set_mode("persistent")
+        assert e.value.code == P.CUPSO_ERR_UNSUPPORTED
         import ctypes as C
         d = C.c_double()
         assert P.lib().cupso_get_gbest_fp64(s32.h, C.byref(d), None, None) == P.CUPSO_ERR_UNSUPPORTED

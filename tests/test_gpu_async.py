@@ -22,9 +22,10 @@ def P():
     return load_cupso()
 
 
-@pytest.mark.parametrize("fid", [0, 1, 3])
-def test_async_single_cta_equals_sync(P, fid):
-    N, D, T = 700, 5, 30
+@pytest.mark.parametrize("fid,D", [(0, 5), (1, 5), (3, 5), (4, 1), (1, 1)])
+def test_async_single_cta_equals_sync(P, fid, D):
+    """D = 1 runs the streaming asynchronous kernel, D >= 2 the tiled one."""
+    N, T = 700, 30
     with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 9, mode="async") as s:
         s.set_option(P.CUPSO_OPT_GRID, 1)
         s.step(T)
@@ -36,7 +37,7 @@ def test_async_single_cta_equals_sync(P, fid):
     assert idx == ref.gbest_idx and same_bits(pos, ref.gbest_pos)
 
 
-@pytest.mark.parametrize("fid,N,D", [(1, 20000, 16), (3, 70000, 8), (2, 4096, 30)])
+@pytest.mark.parametrize("fid,N,D", [(1, 20000, 16), (3, 70000, 8), (2, 4096, 30), (4, 50000, 1)])
 def test_async_invariants(P, fid, N, D):
     lo, hi, vmax = BOUNDS[fid]
     with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 2, mode="async") as s:

@@ -466,6 +466,33 @@ def run_lsq(a):
             ms = e0.elapsed_time(e1)
             runs[prec] = {"seconds": ms / 1e3, "ms_per_iter": ms / T, "final_residual_f64": s.gbest_f64(),
                           "pd_per_s": N * D * T / (ms / 1e3)}
+    # The fitness error itself, against FP64, along a run: at iterations 0, 100,
+    # 200 and 300 of each reduced-precision swarm, the fitness of 1024 of its
+    # current positions (every 8th particle) through cupso_lsq_eval in that
+    # precision, against the same sum in FP64 on the host.
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    fit_err = {}
+    for prec in ("bf16", "fp8"):
+        pts = []
+        with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
+                     stream=stream.cuda_stream) as s:
+            s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
+            done = 0
+            for at in (0, 100, 200, 300):
+                s.step(at - done)
+                done = at
+                X = np.ascontiguousarray(s.state()["pos"][::8])
+                dX = torch.from_numpy(X).cuda()
+                df = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+                P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, dX.data_ptr(), X.shape[0],
+                                 P.LSQ_PRECISIONS[prec], df.data_ptr(), stream.cuda_stream)
+                torch.cuda.synchronize()
+                R = X.astype(np.float64) @ A64.T - b64[None, :]
+                f64 = np.sum(R * R, axis=1)
+                rel = np.abs(df.cpu().numpy().astype(np.float64) - f64) / f64
+                pts.append({"iteration": at, "particles": int(X.shape[0]), "median_rel_err": float(np.median(rel)),
+                            "max_rel_err": float(rel.max())})
+        fit_err[prec] = pts
     # Final FP64 residual over swarm seeds 1..5 per precision: PSO trajectories
     # diverge as soon as one pbest decision differs, so one run against another
     # compares two random searches; the spread over seeds says how large that
@@ -523,6 +550,7 @@ def run_lsq(a):
         "fp8_over_fp32": runs["fp32"]["seconds"] / runs["fp8"]["seconds"],
         "fitness_eval_ms": fit_ms,
         "seed_study": seed_study,
+        "fitness_rel_err_vs_fp64": fit_err,
         "roofline": {"bound": "tensor",
                      "kernel": "fitness phase: operand conversion + lsq_tc_kernel<bf16> + partial sums",
                      "achieved": flops / (fit_ms["bf16"] / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",

@@ -97,6 +97,9 @@ struct cupso_swarm {
         int fitness_timed = 0;
     };
     Lsq* lsq = nullptr;
+    // pinned host staging of the gbest reads (allocated on first use)
+    void* pinned = nullptr;
+    size_t pinned_bytes = 0;
 };
 
 namespace {
@@ -543,6 +546,18 @@ int create_swarm64(int D, int N, const cupso_bounds_f64* b, double w, double c1,
     return CUPSO_OK;
 }
 
+// Pinned staging for small reads: async copies into pinned memory need no
+// host-side staging and finish with one stream synchronisation.
+int ensure_pinned(cupso_swarm* h, size_t bytes) {
+    if (h->pinned_bytes >= bytes) return CUPSO_OK;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    h->pinned = nullptr;
+    h->pinned_bytes = 0;
+    CUPSO_CUDA(cudaMallocHost(&h->pinned, bytes), "cudaMallocHost");
+    h->pinned_bytes = bytes;
+    return CUPSO_OK;
+}
+
 int read_status(cupso_swarm* h, unsigned* st) {
     CUPSO_CUDA(cudaMemcpyAsync(st, h->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
                "cudaMemcpyAsync");
@@ -749,16 +764,21 @@ int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
     if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     const int cur = (int)(h->t_host & 1u);
-    unsigned long long key = 0;
-    unsigned st = 0;
-    CUPSO_CUDA(cudaMemcpyAsync(&key, h->dev.gkey + cur, sizeof(key), cudaMemcpyDeviceToHost, h->stream),
-               "cudaMemcpyAsync");
+    int rc = ensure_pinned(h, 32 + sizeof(float) * (size_t)h->D);
+    if (rc) return rc;
+    char* pin = static_cast<char*>(h->pinned);
+    CUPSO_CUDA(cudaMemcpyAsync(pin, h->dev.gkey + cur, 8, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaMemcpyAsync(pin + 8, h->dev.status, 4, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
     if (pos_out)
-        CUPSO_CUDA(cudaMemcpyAsync(pos_out, h->dev.G + (size_t)cur * h->D, sizeof(float) * (size_t)h->D,
+        CUPSO_CUDA(cudaMemcpyAsync(pin + 32, h->dev.G + (size_t)cur * h->D, sizeof(float) * (size_t)h->D,
                                    cudaMemcpyDeviceToHost, h->stream),
                    "cudaMemcpyAsync");
-    int rc = read_status(h, &st);
-    if (rc) return rc;
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    unsigned long long key = 0;
+    unsigned st = 0;
+    std::memcpy(&key, pin, 8);
+    std::memcpy(&st, pin + 8, 4);
+    if (pos_out) std::memcpy(pos_out, pin + 32, sizeof(float) * (size_t)h->D);
     if (fit_out) *fit_out = key_to_fit(key);
     if (idx_out) *idx_out = (int64_t)(key & 0xFFFFFFFFull);
     rc = status_code(st);
@@ -927,16 +947,22 @@ int cupso_get_gbest_fp64(cupso_handle h, double* fit_out, double* pos_out, int64
     if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
     if (!h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "not a double-precision swarm%s");
     const int cur = (int)(h->t_host & 1u);
-    PKey key{};
-    unsigned st = 0;
-    CUPSO_CUDA(cudaMemcpyAsync(&key, h->dev64.gkey + cur, sizeof(key), cudaMemcpyDeviceToHost, h->stream),
+    int rc = ensure_pinned(h, 32 + sizeof(double) * (size_t)h->D);
+    if (rc) return rc;
+    char* pin = static_cast<char*>(h->pinned);
+    CUPSO_CUDA(cudaMemcpyAsync(pin, h->dev64.gkey + cur, sizeof(PKey), cudaMemcpyDeviceToHost, h->stream),
                "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaMemcpyAsync(pin + 16, h->dev64.status, 4, cudaMemcpyDeviceToHost, h->stream), "cudaMemcpyAsync");
     if (pos_out)
-        CUPSO_CUDA(cudaMemcpyAsync(pos_out, h->dev64.G + (size_t)cur * h->D, sizeof(double) * (size_t)h->D,
+        CUPSO_CUDA(cudaMemcpyAsync(pin + 32, h->dev64.G + (size_t)cur * h->D, sizeof(double) * (size_t)h->D,
                                    cudaMemcpyDeviceToHost, h->stream),
                    "cudaMemcpyAsync");
-    int rc = read_status(h, &st);
-    if (rc) return rc;
+    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
+    PKey key{};
+    unsigned st = 0;
+    std::memcpy(&key, pin, sizeof(PKey));
+    std::memcpy(&st, pin + 16, 4);
+    if (pos_out) std::memcpy(pos_out, pin + 32, sizeof(double) * (size_t)h->D);
     if (fit_out) *fit_out = key_to_fit64(key.k);
     if (idx_out) *idx_out = (int64_t)key.i;
     rc = status_code(st);
@@ -1057,6 +1083,7 @@ int cupso_destroy(cupso_handle h) {
         h->lsq = nullptr;
     }
     if (h->arena) cudaFree(h->arena);
+    if (h->pinned) cudaFreeHost(h->pinned);
     if (h->capture) cudaStreamDestroy(h->capture);
     if (h->own) cudaStreamDestroy(h->own);
     delete h;

@@ -180,9 +180,14 @@ int async_block(const cupso_swarm* h) {
     return (h->Np / kTile >= 2 * h->num_sms) ? kBlock : 32;
 }
 
-// Particles per tile of the tiled asynchronous kernel (0: the streaming one).
+// Particles per tile of the tiled asynchronous kernel (0: the streaming one),
+// by the crossover of the synchronous kernels: tiles where the tiled SYNC
+// kernel is the faster one, else the streaming layout, which large swarms fill.
 int async_tile(const cupso_swarm* h) {
     if (h->fp64 || h->D < 2) return 0;
+    const bool has_cos = h->fid == CUPSO_RASTRIGIN || h->fid == CUPSO_ACKLEY;
+    const long long per_sm = (has_cos || h->D <= 64) ? 896 : 224;
+    if ((long long)h->N > per_sm * h->num_sms) return 0;
     return tiled_particles(h->N, h->D, h->num_sms);
 }
 

@@ -18,7 +18,9 @@
 //  * async_kernel       Sec. 3.2 (Alg. 3) taken to its asynchronous end (the
 //                       future work of Sec. 6): persistent CTAs iterate on
 //                       their own particles with no grid barrier, against a
-//                       lock-protected global best read under a sequence lock.
+//                       lock-protected global best read under a sequence lock
+//                       (async_common.cuh). Large swarms and D = 1; smaller
+//                       ones run the tiled form (kernels_tiled.cu).
 //  * recompute_kernel   gbest from pbest after the host loads a state.
 #include <cuda_runtime.h>
 

@@ -1,4 +1,4 @@
-// kernels_tiled.cu -- the synchronous FP32 iteration for swarms too small to
+// kernels_tiled.cu -- the FP32 iteration in tiles, for swarms too small to
 // fill the GPU when each thread walks a particle's dimensions in order.
 //
 // The streaming kernels give each thread whole particles and run over d
@@ -9,8 +9,14 @@
 // every load of a tile is in flight at once. The fitness (Step 3) keeps its
 // order: the per-dimension terms are formed in parallel, and one thread per
 // particle adds them for d = 0 .. D-1 with the same operations as the
-// streaming kernels. Steps 4-5 as in the fused step: strict pbest, the
-// conditional atomicMin on the packed key, the last CTA gathers gbest_pos.
+// streaming kernels. The tile step serves three kernels:
+//  * sync_tiled_kernel   SYNC: Steps 4-5 as in the fused step (strict pbest,
+//                        conditional atomicMin on the packed key, the last
+//                        CTA gathers gbest_pos);
+//  * async_tiled_kernel  ASYNC: persistent CTAs own fixed tiles and iterate
+//                        with no grid barrier against the lock-protected
+//                        gbest record;
+//  * batch_tiled_kernel  a batch: (swarm, tile) units of all swarms per launch.
 #include <cuda_runtime.h>
 
 #include "async_common.cuh"

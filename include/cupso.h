@@ -273,7 +273,9 @@ typedef struct {
  * else the first failing status; results[k].status holds each swarm's.
  * Every iteration of all swarms is one launch; the kernel and launch shape
  * are tuned on the first iterations (the environment variable
- * CUPSO_BATCH_KERNEL=tiled or =streaming fixes the kernel instead). */
+ * CUPSO_BATCH_KERNEL=tiled or =streaming fixes the kernel instead).
+ * CUPSO_ERR_INVALID_ARG (before any device work) for a bad argument in any
+ * problem, and for CUPSO_LSQ, which needs the matrices of cupso_set_lsq. */
 CUPSO_API int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int iters,
                       cupso_result* results, void* cuda_stream);
 

@@ -140,6 +140,11 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         const cupso_problem& p = problems[k];
         const int rc = check_problem_args(p.D, p.N, &p.bounds, p.w, p.c1, p.c2, p.fitness_id);
         if (rc) return rc;
+        if (p.fitness_id == CUPSO_LSQ) {
+            // the least-squares fitness needs A and b (cupso_set_lsq); a problem record has neither
+            set_last_error("the least-squares fitness is not available in a batch");
+            return CUPSO_ERR_INVALID_ARG;
+        }
     }
     if (n_swarms == 0) return CUPSO_OK;
 
@@ -275,15 +280,24 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         }
         if (rc != CUPSO_OK) break;
 
-        // Hand-out order: the units with the most dimensions first; swarms interleaved.
+        // Hand-out order: swarms that run the same code (fitness function and
+        // arithmetic path) together, so that the warps of an SM share their
+        // instructions; within such a class the units with the most dimensions
+        // first, swarms of equal D interleaved. The smallest units come last
+        // and fill the tail.
         std::vector<uint2> units;
         units.reserve(total_units);
         std::vector<int> order(nb);
         for (int j = 0; j < nb; ++j) order[j] = j;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return desc[a].D > desc[b].D; });
+        auto code_of = [&](int j) { return desc[j].fid * 2 + desc[j].fast; };
+        auto same_group = [&](int a, int b) { return code_of(a) == code_of(b) && desc[a].D == desc[b].D; };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (code_of(a) != code_of(b)) return code_of(a) < code_of(b);
+            return desc[a].D > desc[b].D;
+        });
         for (size_t pos = 0; pos < (size_t)nb;) {
             size_t endg = pos;
-            while (endg < (size_t)nb && desc[order[endg]].D == desc[order[pos]].D) ++endg;
+            while (endg < (size_t)nb && same_group(order[endg], order[pos])) ++endg;
             unsigned most = 0;
             for (size_t q = pos; q < endg; ++q) most = std::max(most, desc[order[q]].nunits);
             for (unsigned u = 0; u < most; ++u)
@@ -303,15 +317,14 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         run.dev.ticket = ctr + 2;
         run.dev.t_dev = ctr + 3;
 
-        // The tiled kernel's units: tiles of the swarms with the most dimensions
-        // first, swarms of equal D interleaved.
+        // The tiled kernel's units in the same order.
         const bool tiled_ok = maxD <= kTiledItems;
         if (tiled_ok) {
             std::vector<uint2> tunits;
             tunits.reserve(total_tiles);
             for (size_t pos = 0; pos < (size_t)nb;) {
                 size_t endg = pos;
-                while (endg < (size_t)nb && desc[order[endg]].D == desc[order[pos]].D) ++endg;
+                while (endg < (size_t)nb && same_group(order[endg], order[pos])) ++endg;
                 unsigned most = 0;
                 for (size_t q = pos; q < endg; ++q) most = std::max(most, ntiles[order[q]]);
                 for (unsigned u = 0; u < most; ++u)

@@ -3,10 +3,11 @@
 //
 // Each launch advances every swarm of the batch by one synchronous iteration
 // (Steps 2-5 of Alg. 1). The work is the union of all swarms' 128-particle
-// units, handed to warps from one counter in a fixed order (the costliest
-// units, those with the most dimensions, first, so that the short ones fill
-// the tail). A unit is processed exactly like one unit of the pipelined
-// single-swarm kernel: rows staged through a per-thread cp.async ring in shared
+// units, handed to warps from one counter in a fixed order (swarms with the
+// same fitness function together; within those the units with the most
+// dimensions first, so that the short ones fill the tail). A unit is
+// processed exactly like one unit of the pipelined single-swarm kernel, by a
+// copy of the unit loop compiled for its swarm's fitness function: rows staged through a per-thread cp.async ring in shared
 // memory, lazy pbest write-back, conditional atomicMin on the swarm's packed
 // gbest key. Each swarm keeps its own gbest key and position; the warp that
 // finishes a swarm's last unit gathers that swarm's gbest_pos. The kernel
@@ -49,23 +50,27 @@ __device__ __forceinline__ Unit fetch(const BatchDev& b, unsigned* work, int lan
     return Unit{e.x, e.y};
 }
 
-// Copies of pair g of unit `un` into ring stage `stage` (an empty group if none).
-__device__ __forceinline__ void issue(const BatchDev& b, float4* my, Unit un, int g, int stage, int lane_id) {
-    if (un.sw != 0xFFFFFFFFu) {
-        const BatchSwarm& w = b.swarms[un.sw];
-        const size_t col = (size_t)un.u * kUnitB + (size_t)lane_id * 4;
+// Copies of pair g of unit u of swarm w into ring stage `stage`.
+__device__ __forceinline__ void issue_rows(const BatchSwarm& w, float4* my, uint32_t u, int g, int stage,
+                                           int lane_id) {
+    const size_t col = (size_t)u * kUnitB + (size_t)lane_id * 4;
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int d = 2 * g + r;
-            if (d < w.D) {
-                const size_t off = (size_t)d * (size_t)w.Np + col;
-                cp_async16b(my + (stage * 6 + 0 + r) * kBlock, w.x + off);
-                cp_async16b(my + (stage * 6 + 2 + r) * kBlock, w.v + off);
-                cp_async16b(my + (stage * 6 + 4 + r) * kBlock, w.pb + off);
-            }
+    for (int r = 0; r < 2; ++r) {
+        const int d = 2 * g + r;
+        if (d < w.D) {
+            const size_t off = (size_t)d * (size_t)w.Np + col;
+            cp_async16b(my + (stage * 6 + 0 + r) * kBlock, w.x + off);
+            cp_async16b(my + (stage * 6 + 2 + r) * kBlock, w.v + off);
+            cp_async16b(my + (stage * 6 + 4 + r) * kBlock, w.pb + off);
         }
     }
     cp_commit_b();
+}
+
+// The same for unit `un` of the batch (an empty group if there is none).
+__device__ __forceinline__ void issue(const BatchDev& b, float4* my, Unit un, int g, int stage, int lane_id) {
+    if (un.sw != 0xFFFFFFFFu) issue_rows(b.swarms[un.sw], my, un.u, g, stage, lane_id);
+    else cp_commit_b();
 }
 
 // Eq. 1 and Eq. 2 for one element with the parameters of swarm w.
@@ -88,49 +93,6 @@ __device__ __forceinline__ void move_w(float& x, float& v, float pb, float g, ui
     }
 }
 
-// FitAcc with the fitness chosen at run time (uniform for a unit): the same
-// operations in the same order as FitAcc<FIT>, so the batch kernel carries one
-// copy of the unit loop instead of one per fitness function.
-struct FitAccRT {
-    float acc = 0.0f, acc2 = 0.0f, prev = 0.0f;
-    __device__ __forceinline__ void add(int fid, int d, float x) {
-        switch (fid) {
-            case kSphere: acc = __fmaf_rn(x, x, acc); break;
-            case kRastrigin: {
-                const float ten_minus = __fmaf_rn(-10.0f, cos2pi(x), 10.0f);
-                acc = __fadd_rn(acc, __fmaf_rn(x, x, ten_minus));
-                break;
-            }
-            case kAckley:
-                acc = __fmaf_rn(x, x, acc);
-                acc2 = __fadd_rn(acc2, cos2pi(x));
-                break;
-            case kRosenbrock:
-                if (d > 0) {
-                    const float p = __fmaf_rn(-prev, prev, x);
-                    const float q = __fsub_rn(1.0f, prev);
-                    acc = __fadd_rn(acc, __fmaf_rn(__fmul_rn(100.0f, p), p, __fmul_rn(q, q)));
-                }
-                prev = x;
-                break;
-            default: {
-                const float h = __fmaf_rn(__fmaf_rn(__fsub_rn(x, 0.8f), x, -1000.0f), x, 8000.0f);
-                acc = __fadd_rn(acc, h);
-                break;
-            }
-        }
-    }
-    __device__ __forceinline__ float finish(int fid, int D) const {
-        if (fid == kAckley) {
-            FitAcc<kAckley> a;
-            a.acc = acc;
-            a.acc2 = acc2;
-            return a.finish(D);
-        }
-        return fid == kCubicMax ? -acc : acc;
-    }
-};
-
 // The per-warp pipeline state carried from one unit to the next.
 struct Pipe {
     Unit nxt;        // the unit after the current one (fetched when first needed)
@@ -139,13 +101,15 @@ struct Pipe {
     int stage;       // ring stage of the pair being computed
 };
 
-// Process unit `cu` of the batch at iteration t; keeps STAGES-1 pairs in flight.
-template <int STAGES>
-__device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, float4* my, Unit cu, Pipe& pp,
-                                         uint32_t t, int lane_id) {
-    const BatchSwarm& w = b.swarms[cu.sw];
-    const int fid = w.fid;
-    const bool fast = w.fast != 0;
+// Process unit `cu` of the batch at iteration t; keeps STAGES-1 pairs in
+// flight. One copy per (fitness, fast path), so the loop body carries no
+// per-element branch and a thread's four particles interleave freely.
+template <int STAGES, int FIT, bool FAST>
+__device__ __forceinline__ void run_unit_t(const BatchDev& b, unsigned* work, float4* my, Unit cu, Pipe& pp,
+                                           uint32_t t, int lane_id) {
+    // A private copy of the descriptor: the unit's own stores cannot alias it,
+    // so its fields stay in registers.
+    const BatchSwarm w = b.swarms[cu.sw];
     const int D = w.D, npairs = (D + 1) >> 1;
     const size_t Np = (size_t)w.Np;
     const int cur = (int)((t - 1u) & 1u), nxt = cur ^ 1;
@@ -153,14 +117,14 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     const unsigned long long K = __ldcg(w.gkey + cur);
     const uint32_t i0 = cu.u * kUnitB + (uint32_t)lane_id * 4;
     const uint32_t fl = __ldcg(reinterpret_cast<const unsigned int*>(w.pflag + i0));
-    FitAccRT acc[4];
+    FitAcc<FIT> acc[4];
     float4 PF = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int g = 0; g < npairs; ++g) {
         {
             int ws = pp.stage + STAGES - 1;
             if (ws >= STAGES) ws -= STAGES;
             if (pp.ig < npairs) {
-                issue(b, my, cu, pp.ig, ws, lane_id);
+                issue_rows(w, my, cu.u, pp.ig, ws, lane_id);
                 ++pp.ig;
             } else {
                 if (!pp.have_nxt) {
@@ -197,11 +161,10 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float xj = lane(X, j), vj = lane(V, j);
-                if (fast) move_w<true>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
-                else move_w<false>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
+                move_w<FAST>(xj, vj, lane(P, j), gd, word(rr[j], 2 * h), word(rr[j], 2 * h + 1), w);
                 set_lane(X, j, xj);
                 set_lane(V, j, vj);
-                acc[j].add(fid, d, xj);
+                acc[j].add(d, xj);
             }
             st4(w.x + off, X);
             st4(w.v + off, V);
@@ -214,7 +177,7 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     bool nan = false;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float f = acc[j].finish(fid, D);
+        const float f = acc[j].finish(D);
         const bool real = (i0 + j) < (uint32_t)w.N;
         nan |= real && (f != f);
         if (real && f < lane(PF, j)) {
@@ -257,6 +220,35 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
         }
     }
     pp.ig -= npairs;
+}
+
+template <int STAGES>
+__device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, float4* my, Unit cu, Pipe& pp,
+                                         uint32_t t, int lane_id) {
+    const BatchSwarm& w = b.swarms[cu.sw];
+    const bool fast = w.fast != 0;
+    switch (w.fid) {
+        case kSphere:
+            if (fast) run_unit_t<STAGES, kSphere, true>(b, work, my, cu, pp, t, lane_id);
+            else run_unit_t<STAGES, kSphere, false>(b, work, my, cu, pp, t, lane_id);
+            break;
+        case kRastrigin:
+            if (fast) run_unit_t<STAGES, kRastrigin, true>(b, work, my, cu, pp, t, lane_id);
+            else run_unit_t<STAGES, kRastrigin, false>(b, work, my, cu, pp, t, lane_id);
+            break;
+        case kAckley:
+            if (fast) run_unit_t<STAGES, kAckley, true>(b, work, my, cu, pp, t, lane_id);
+            else run_unit_t<STAGES, kAckley, false>(b, work, my, cu, pp, t, lane_id);
+            break;
+        case kRosenbrock:
+            if (fast) run_unit_t<STAGES, kRosenbrock, true>(b, work, my, cu, pp, t, lane_id);
+            else run_unit_t<STAGES, kRosenbrock, false>(b, work, my, cu, pp, t, lane_id);
+            break;
+        default:  // kCubicMax (the host admits nothing else)
+            if (fast) run_unit_t<STAGES, kCubicMax, true>(b, work, my, cu, pp, t, lane_id);
+            else run_unit_t<STAGES, kCubicMax, false>(b, work, my, cu, pp, t, lane_id);
+            break;
+    }
 }
 
 }  // namespace

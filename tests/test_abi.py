@@ -89,6 +89,9 @@ def test_null_handle_calls_rejected(P):
     with pytest.raises(P.CupsoError) as e:
         P.cupso_solve_batch([dict(D=0, N=4, bounds=(-1, 1, 1), w=0.5, c1=1, c2=1, fitness_id=0, seed=1)], 3)
     assert e.value.code == P.CUPSO_ERR_INVALID_ARG
+    with pytest.raises(P.CupsoError) as e:   # least squares needs A and b: no batch form
+        P.cupso_solve_batch([dict(D=4, N=64, bounds=(-1, 1, 1), w=0.5, c1=1, c2=1, fitness_id=P.CUPSO_LSQ, seed=1)], 3)
+    assert e.value.code == P.CUPSO_ERR_INVALID_ARG
 
 
 def _cuh_floats(pattern):

@@ -351,6 +351,28 @@ def test_batched_solve_each_kernel_matches_oracle(P, kernel, monkeypatch):
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
 
 
+@pytest.mark.parametrize("kernel", ["tiled", "streaming"])
+def test_batched_solve_general_path_matches_oracle(P, kernel, monkeypatch):
+    """Swarms that cannot take the fast path (a bound at 0, so min/max clamps
+    could meet a signed zero; c1 too small for the fused c*r) next to ones
+    that can, every fitness function: each equals its oracle run."""
+    monkeypatch.setenv("CUPSO_BATCH_KERNEL", kernel)
+    probs = _mixed_batch(10, 17, (100, 1500), (4, 48))
+    for k, p in enumerate(probs):
+        if k % 3 == 0:
+            p["bounds"] = (0.0, 10.0, 2.0)
+        elif k % 3 == 1:
+            p["c1"] = 1e-38
+    rc, res = P.cupso_solve_batch(probs, 10)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"], bounds=p["bounds"],
+                           c1=p["c1"]).init().step_sync(10)
+        assert res[k]["status"] == P.CUPSO_OK
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
 def test_batched_kernels_interchange_with_lazy_pbest(P, monkeypatch):
     """The tuner may switch kernels between iterations of one solve; the
     streaming kernel leaves pbest rows pending (lazy write-back) and the tiled

@@ -1,7 +1,7 @@
 // cupso_batch.cu -- cupso_solve_batch: many independent swarms at once.
 //
-// All swarms of a batch live in one device arena. Each is initialised by the
-// ordinary Step-1 kernel, then every iteration is ONE launch of
+// All swarms of a batch live in one device arena. One launch runs Step 1 of
+// every swarm (batch_init_kernel), then every iteration is ONE launch of
 // batch_step_kernel covering the units of all swarms (kernels_batch.cu); the
 // `iters` launches are replayed from captured CUDA graphs. Two kernels can
 // run the step: the streaming one (kernels_batch.cu: 128-particle units per
@@ -222,7 +222,7 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         char* base = static_cast<char*>(arena);
         float* Gall = reinterpret_cast<float*>(base + o_Gall);
         unsigned long long* keys = reinterpret_cast<unsigned long long*>(base + o_keys);
-        unsigned int* words = reinterpret_cast<unsigned int*>(base + o_words);   // done, status, ticket, t
+        unsigned int* words = reinterpret_cast<unsigned int*>(base + o_words);   // done, status, 2 spare
         unsigned char* flags = reinterpret_cast<unsigned char*>(base + o_flags);
         unsigned int* ctr = reinterpret_cast<unsigned int*>(base + o_ctr);       // work[2], ticket, t
         e = cudaMemsetAsync(keys, 0xFF, sizeof(unsigned long long) * 2 * nb, run.st);
@@ -230,53 +230,35 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, 64, run.st);
         if (e != cudaSuccess) { set_cuda_error(e, "cudaMemsetAsync"); rc = CUPSO_ERR_CUDA; break; }
 
-        // Step 1 of every swarm, and its descriptor.
+        // The descriptor of every swarm.
         std::vector<BatchSwarm> desc(nb);
-        for (int j = 0; j < nb && rc == CUPSO_OK; ++j) {
+        for (int j = 0; j < nb; ++j) {
             const cupso_problem& p = problems[batched[j]];
             float* st = reinterpret_cast<float*>(base + o_state[j]);
             const size_t plane = (size_t)p.D * Np[j];
-            SwarmDev s{};
-            s.x = st;
-            s.v = st + plane;
-            s.pb = st + 2 * plane;
-            s.pf = st + 3 * plane;
-            s.G = Gall + o_G[j];
-            s.gkey = keys + 2 * j;
-            s.status = words + 4 * j + 1;
-            s.ticket = words + 4 * j + 2;
-            s.t_dev = words + 4 * j + 3;
-            s.N = p.N;
-            s.D = p.D;
-            s.Np = Np[j];
-            s.lo = p.bounds.min_pos;
-            s.hi = p.bounds.max_pos;
-            s.vmax = p.bounds.max_v;
-            s.w = p.w;
-            s.c1 = p.c1;
-            s.c2 = p.c2;
-            s.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
-            s.key1 = (uint32_t)(p.seed >> 32);
-            s.swarm = p.swarm_id;
-            e = launch_init(s, p.fitness_id, std::min(tiles_of(Np[j]), run.num_sms * 4), run.st);
-            if (e != cudaSuccess) { set_cuda_error(e, "batch init launch"); rc = CUPSO_ERR_CUDA; break; }
             BatchSwarm& w = desc[j];
-            w.x = s.x; w.v = s.v; w.pb = s.pb; w.pf = s.pf;
+            w.x = st;
+            w.v = st + plane;
+            w.pb = st + 2 * plane;
+            w.pf = st + 3 * plane;
             w.pflag = flags + o_flag[j];
-            w.G = s.G;
-            w.gkey = s.gkey;
+            w.G = Gall + o_G[j];
+            w.gkey = keys + 2 * j;
             w.done = words + 4 * j + 0;
-            w.status = s.status;
+            w.status = words + 4 * j + 1;
             w.N = p.N; w.D = p.D; w.Np = Np[j]; w.fid = p.fitness_id;
             w.nunits = (unsigned)(Np[j] / 128);
-            w.lo = s.lo; w.hi = s.hi; w.vmax = s.vmax; w.w = p.w; w.c1 = p.c1; w.c2 = p.c2;
+            w.lo = p.bounds.min_pos; w.hi = p.bounds.max_pos; w.vmax = p.bounds.max_v;
+            w.w = p.w; w.c1 = p.c1; w.c2 = p.c2;
             w.c1s = std::ldexp(p.c1, -24);
             w.c2s = std::ldexp(p.c2, -24);
             const bool fast_cr = std::ldexp(w.c1s, 24) == p.c1 && std::ldexp(w.c2s, 24) == p.c2 &&
                                  (p.c1 == 0.0f || std::fabs(w.c1s) >= FLT_MIN) &&
                                  (p.c2 == 0.0f || std::fabs(w.c2s) >= FLT_MIN);
             w.fast = fast_cr && p.bounds.min_pos != 0.0f && p.bounds.max_pos != 0.0f;
-            w.key0 = s.key0; w.key1 = s.key1; w.swarm = p.swarm_id;
+            w.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+            w.key1 = (uint32_t)(p.seed >> 32);
+            w.swarm = p.swarm_id;
         }
         if (rc != CUPSO_OK) break;
 
@@ -316,6 +298,10 @@ extern "C" int cupso_solve_batch(int n_swarms, const cupso_problem* problems, in
         run.dev.work = ctr;
         run.dev.ticket = ctr + 2;
         run.dev.t_dev = ctr + 3;
+
+        // Step 1 of every swarm, one launch.
+        e = launch_batch_init(run.dev, run.num_sms * 4, run.st);
+        if (e != cudaSuccess) { set_cuda_error(e, "batch init launch"); rc = CUPSO_ERR_CUDA; break; }
 
         // The tiled kernel's units in the same order.
         const bool tiled_ok = maxD <= kTiledItems;

@@ -42,6 +42,10 @@ cudaError_t prepare_batch();
 // register budget is sized for.
 int batch_blocks_per_sm(int stages, int minb);
 cudaError_t launch_batch_step(const BatchDev& b, int stages, int minb, int grid, cudaStream_t st);
+// Step 1 (t = 0) of every swarm of a batch in one launch, over the same units;
+// per swarm the same bits as launch_init. Needs gkey = all ones, done and
+// pflag zero.
+cudaError_t launch_batch_init(const BatchDev& b, int grid, cudaStream_t st);
 
 // Least-squares fitness (kernels_lsq.cu).
 struct LsqTcPlan {

@@ -251,6 +251,82 @@ __device__ __forceinline__ void run_unit(const BatchDev& b, unsigned* work, floa
     }
 }
 
+// Step 1 (t = 0) for unit u of swarm w: each lane draws its four particles'
+// positions and velocities over all dimensions, scores them, and the unit's
+// best key competes for the swarm's gbest. The same arithmetic, in the same
+// order, as the single-swarm init kernel.
+template <int FIT>
+__device__ __forceinline__ void init_unit(const BatchSwarm& wg, uint32_t u, int lane_id) {
+    const BatchSwarm w = wg;
+    const size_t Np = (size_t)w.Np;
+    const float span = __fsub_rn(w.hi, w.lo);
+    const float vspan = __fmul_rn(2.0f, w.vmax);
+    const uint32_t i0 = u * kUnitB + (uint32_t)lane_id * 4;
+    FitAcc<FIT> acc[4];
+    for (int d0 = 0; d0 < w.D; d0 += 2) {
+        uint4 r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            r[j] = philox4x32_10(make_uint4((uint32_t)(d0 >> 1), i0 + j, 0u, w.swarm), w.key0, w.key1);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int d = d0 + h;
+            if (h == 1 && d >= w.D) break;
+            float4 X, V;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float xj = clampf(__fmaf_rn(u01(word(r[j], 2 * h)), span, w.lo), w.lo, w.hi);
+                const float vj = clampf(__fmaf_rn(u01(word(r[j], 2 * h + 1)), vspan, -w.vmax), -w.vmax, w.vmax);
+                set_lane(X, j, xj);
+                set_lane(V, j, vj);
+                acc[j].add(d, xj);
+            }
+            const size_t off = (size_t)d * Np + i0;
+            st4(w.x + off, X);
+            st4(w.v + off, V);
+            st4(w.pb + off, X);
+        }
+    }
+    float4 PF;
+    unsigned long long best = kKeyNone;
+    bool nan = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float f = acc[j].finish(w.D);
+        set_lane(PF, j, f);
+        if (i0 + j < (uint32_t)w.N) {
+            const unsigned long long k = pack_key(f, i0 + j);
+            best = k < best ? k : best;
+            nan |= (f != f);
+        }
+    }
+    st4(w.pf + i0, PF);
+    best = warp_min_u64(best);
+    const bool any_nan = __any_sync(0xFFFFFFFFu, nan);
+    __threadfence();
+    __syncwarp();
+    int last = 0;
+    if (lane_id == 0) {
+        if (best != kKeyNone) atomicMin(w.gkey + 0, best);
+        if (any_nan) atomicOr(w.status, kStatusNaN);
+        __threadfence();
+        last = atomicAdd(w.done, 1u) == w.nunits - 1u;
+        if (last) __threadfence();
+    }
+    last = __shfl_sync(0xFFFFFFFFu, last, 0);
+    if (last) {
+        // t = 0 lives in slot 0; slot 1 gets the same key (the step's invariant)
+        const unsigned long long k0 = __ldcg(w.gkey + 0);
+        const uint32_t g = (uint32_t)(k0 & 0xFFFFFFFFull);
+        for (int d = lane_id; d < w.D; d += 32) w.G[d] = __ldcg(w.pb + (size_t)d * Np + g);
+        __syncwarp();
+        if (lane_id == 0) {
+            w.gkey[1] = k0;
+            *w.done = 0u;
+        }
+    }
+}
+
 }  // namespace
 
 // One iteration of every swarm of the batch. Iteration t = *t_dev + 1.
@@ -295,6 +371,23 @@ __global__ void __launch_bounds__(kBlock, MINB) batch_step_kernel(const __grid_c
     }
 }
 
+// Step 1 of every swarm: the batch's units dealt to warps round-robin.
+__global__ void __launch_bounds__(kBlock) batch_init_kernel(const __grid_constant__ BatchDev b) {
+    const int lane_id = threadIdx.x & 31;
+    const unsigned nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < b.nunits; k += nwarps) {
+        const uint2 e = __ldg(b.units + k);
+        const BatchSwarm& w = b.swarms[e.x];
+        switch (w.fid) {
+            case kSphere: init_unit<kSphere>(w, e.y, lane_id); break;
+            case kRastrigin: init_unit<kRastrigin>(w, e.y, lane_id); break;
+            case kAckley: init_unit<kAckley>(w, e.y, lane_id); break;
+            case kRosenbrock: init_unit<kRosenbrock>(w, e.y, lane_id); break;
+            default: init_unit<kCubicMax>(w, e.y, lane_id); break;   // the host admits nothing else
+        }
+    }
+}
+
 namespace {
 template <int STAGES>
 size_t batch_smem() {
@@ -327,6 +420,12 @@ int batch_blocks_per_sm(int stages, int minb) {
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBlock, batch_smem_of(stages)) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batch_init(const BatchDev& b, int grid, cudaStream_t st) {
+    if (grid < 1) return cudaErrorInvalidValue;
+    batch_init_kernel<<<grid, kBlock, 0, st>>>(b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_step(const BatchDev& b, int stages, int minb, int grid, cudaStream_t st) {

@@ -320,10 +320,11 @@ def _mixed_batch(n, seed, n_range, d_range):
     return out
 
 
-@pytest.mark.parametrize("iters", [5, 30])
+@pytest.mark.parametrize("iters", [0, 1, 5, 30])
 def test_batched_solve_matches_oracle(P, iters):
-    """Uneven swarms with every fitness function in one batch; 30 iterations run the
-    launch-shape tuner on the real work first. Each swarm must equal its oracle run."""
+    """Uneven swarms with every fitness function in one batch; 0 iterations is
+    Step 1 alone, 30 iterations run the launch-shape tuner on the real work
+    first. Each swarm must equal its oracle run."""
     probs = _mixed_batch(24, 7, (64, 2500), (3, 40))
     probs[3]["D"] = 2              # too few dimension pairs: solved through its own handle
     probs[5]["D"] = 3              # the smallest batched dimension count

@@ -120,7 +120,9 @@ typedef enum {
     CUPSO_OPT_PARTICLES_PER_THREAD = 8, /* pipelined SYNC kernel: 4, 2, 1, or 0 = automatic (fewer
                                            for small swarms, so that their units fill the GPU) */
     CUPSO_OPT_TIME_FITNESS = 7,   /* 1: time the fitness phase of least-squares iterations with
-                                     CUDA events (no graph capture); 0: off. Read in cupso_info */
+                                     CUDA events (no graph capture); 0: off. Read in cupso_info.
+                                     BF16/FP8: the tensor-core product and the partial sums (the
+                                     move kernel before it writes the operand) */
     CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
                                        lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
 } cupso_option;

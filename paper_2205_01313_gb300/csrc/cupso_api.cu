@@ -216,20 +216,22 @@ constexpr int kModeLsq = 100;   // internal: one least-squares iteration
 cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
     cupso_swarm::Lsq& L = *h->lsq;
     const int grid = h->num_sms * 8;   // grid-stride over (particle group, dimension) items
-    cudaError_t e = lsq_launch_move(h->dev, grid, st);
-    if (e != cudaSuccess) return e;
     if (L.precision == CUPSO_LSQ_FP32) {
-        e = lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
+        cudaError_t e = lsq_launch_move(h->dev, grid, st);
+        if (e == cudaSuccess) e = lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
         if (e != cudaSuccess) return e;
         return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
+    // the move writes the tensor-core operand too; the fitness is then the product alone
+    cudaError_t e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms * 6, st);
+    if (e != cudaSuccess) return e;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (L.time_fitness) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
     }
-    if (lsq_eval_tc(&L.tc, h->dev.x, 1, (size_t)h->Np, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
+    if (lsq_eval_tc_operand(&L.tc, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
     if (L.time_fitness) {
         cudaEventRecord(e1, st);
         L.ev.push_back(e0);

@@ -53,6 +53,7 @@ struct LsqTcPlan {
     alignas(64) unsigned char tmA[128];   // CUtensorMap of A [Mp][Kp]
     bool fp8;
     int Np, Mp, Kp;                       // Np % 128 == 0, Mp % 256 == 0, Kp * elem % 128 == 0
+    int num_sms;                          // grid of the persistent product kernel
 };
 bool lsq_tc_available();
 cudaError_t lsq_prepare();
@@ -60,10 +61,11 @@ cudaError_t lsq_prepare();
 cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
                         void* dst, cudaStream_t st);
 bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp);
-// part[s][i] (s < splits actually used) = partial sum of squared residuals.
-cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, int splits, float* part,
+// part[mt][i] (mt < lsq_tc_partials) = sum of squared residuals of particle i
+// over residual rows 256 mt .. 256 mt + 255.
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st);
-int lsq_tc_splits_used(const LsqTcPlan& p, int splits);
+int lsq_tc_partials(const LsqTcPlan& p);
 // Tensor-core fitness state for fixed (A, b): operand copies, scales, plan.
 struct LsqTcState {
     void* arena = nullptr;
@@ -74,9 +76,8 @@ struct LsqTcState {
     void* Xq = nullptr;              // [Np][Kp] operand copy of the positions
     float* bpad = nullptr;           // [Mp]
     float* inv = nullptr;            // [Mp] 1 / (sx * row scale of A) (FP8)
-    float* part = nullptr;           // [splits][Np] partial sums
+    float* part = nullptr;           // [Mp / 256][Np] partial sums
     unsigned int* status = nullptr;
-    int splits = 2;
     LsqTcPlan plan;
 };
 int lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, int D, int Np, bool fp8, float sx,
@@ -84,6 +85,8 @@ int lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, int D, i
 void lsq_free_tc(LsqTcState* st);
 // f[i] for positions X(i, k) = src[i * si + k * sk], i < N (asynchronous).
 int lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, float* f, cudaStream_t stream);
+// f[i], i < N, for the operand already in st->Xq (asynchronous).
+int lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream);
 
 // f[i] = plain FP32 fitness of X(i, d) = x[d * ldx + i], i < N.
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
@@ -91,6 +94,10 @@ cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* 
 
 // Least-squares swarm iteration (kernels_lsq_swarm.cu); all read t from t_dev.
 cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
+// The same moves, writing the new positions also as the tensor-core operand
+// Xq ([Np][Kp], BF16, or FP8 e4m3 of x * sx), zero for i >= N and k >= D.
+// Requires Np and Kp multiples of 64 and Kp >= D.
+cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int grid, cudaStream_t st);
 cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
                                     cudaStream_t st);
 int lsq_cand_blocks(const SwarmDev& s);

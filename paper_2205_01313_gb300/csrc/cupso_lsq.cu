@@ -70,10 +70,10 @@ __global__ void transpose_kernel(const float* __restrict__ in, int N, int D, flo
     }
 }
 
-__global__ void sum_parts_kernel(const float* __restrict__ part, int splits, int Np, int N, float* __restrict__ f) {
+__global__ void sum_parts_kernel(const float* __restrict__ part, int nparts, int Np, int N, float* __restrict__ f) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         float s = 0.0f;
-        for (int k = 0; k < splits; ++k) s = __fadd_rn(s, part[(size_t)k * Np + i]);
+        for (int k = 0; k < nparts; ++k) s = __fadd_rn(s, part[(size_t)k * Np + i]);
         f[i] = s;
     }
 }
@@ -93,9 +93,9 @@ int cupso::lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, i
     st->sx = fp8 ? sx : 1.0f;
     const size_t esz = fp8 ? 1 : 2;
     const size_t bytes_A = (size_t)st->Mp * st->Kp * esz, bytes_X = (size_t)Np * st->Kp * esz;
-    const size_t splits = 4;
+    const size_t nparts = (size_t)st->Mp / 256;   // one partial sum per residual-row tile
     const size_t bytes = up(bytes_A, 256) + up(bytes_X, 256) + up(sizeof(float) * st->Mp, 256) * 2 +
-                         up(sizeof(float) * splits * Np, 256) + up(sizeof(float) * (size_t)M * D, 256) +
+                         up(sizeof(float) * nparts * Np, 256) + up(sizeof(float) * (size_t)M * D, 256) +
                          up(sizeof(float) * M, 256) + 256;
     cudaError_t e = cudaMalloc(&st->arena, bytes);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (lsq)"), e == cudaErrorMemoryAllocation ? CUPSO_ERR_OOM : CUPSO_ERR_CUDA;
@@ -104,7 +104,7 @@ int cupso::lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, i
     st->Xq = p; p += up(bytes_X, 256);
     st->bpad = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
     st->inv = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
-    st->part = reinterpret_cast<float*>(p); p += up(sizeof(float) * splits * Np, 256);
+    st->part = reinterpret_cast<float*>(p); p += up(sizeof(float) * nparts * Np, 256);
     float* Ascaled = reinterpret_cast<float*>(p); p += up(sizeof(float) * (size_t)M * D, 256);
     float* amax = reinterpret_cast<float*>(p); p += up(sizeof(float) * M, 256);
     st->status = reinterpret_cast<unsigned int*>(p);
@@ -138,10 +138,14 @@ void cupso::lsq_free_tc(LsqTcState* st) {
 // f[i] for the positions X(i, k) = src[i * si + k * sk], i < N.
 int cupso::lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, float* f, cudaStream_t stream) {
     cudaError_t e = lsq_convert(src, si, sk, N, st->D, st->Np, st->Kp, st->fp8, st->sx, st->Xq, stream);
-    if (e == cudaSuccess)
-        e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->splits, st->part, st->status,
-                          2000000000ll, stream);
-    const int used = lsq_tc_splits_used(st->plan, st->splits);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsq operand conversion"), CUPSO_ERR_CUDA;
+    return lsq_eval_tc_operand(st, N, f, stream);
+}
+
+int cupso::lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream) {
+    cudaError_t e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->part, st->status,
+                                  2000000000ll, stream);
+    const int used = lsq_tc_partials(st->plan);
     if (e == cudaSuccess) {
         sum_parts_kernel<<<std::max(1, std::min(1024, (N + 255) / 256)), 256, 0, stream>>>(st->part, used, st->Np, N, f);
         e = cudaGetLastError();

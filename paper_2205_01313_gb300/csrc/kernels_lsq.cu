@@ -138,15 +138,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 
 }  // namespace
 
-// Per-particle partial fitness over this CTA's residual rows:
-//   part[split][i] = sum over m in the split of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
+// Per-particle partial fitness of each tile of 128 particles x 256 residual rows:
+//   part[mt][i] = sum over m in tile mt of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
 // X: [Np][Kp] (K-major), A: [Mp][Kp], b: [Mp] (zero-padded rows contribute 0).
-// grid = (Np / 128, splits); each split covers `mt_per_split` tiles of 256 rows.
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... of the (Np / 128) x
+// (Mp / 256) tiles (residual-row tile fastest), so a grid of one CTA per SM
+// covers every tile in waves of equal work.
 template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     lsq_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
-                  const float* __restrict__ b, const float* __restrict__ inv_scale, int Mp, int KT, int mt_per_split,
-                  int Np, float* __restrict__ part, unsigned int* status, long long limit_ns) {
+                  const float* __restrict__ b, const float* __restrict__ inv_scale, int Mp, int KT, int Np,
+                  float* __restrict__ part, unsigned int* status, long long limit_ns) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
     const uint32_t raw = smem_u32(smem_raw);
@@ -164,10 +166,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ volatile int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pblock = blockIdx.x;
-    const int mt0 = blockIdx.y * mt_per_split;
-    const int mt1 = min(mt0 + mt_per_split, Mp / BN);
-    const int nt = mt1 - mt0;
+    const int mtiles = Mp / BN;
+    const int ntiles = (Np / BM) * mtiles;
+    const int nt = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    // the jj-th tile of this CTA: residual-row tile and particle block
+    auto tile_mt = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) % mtiles; };
+    auto tile_pb = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) / mtiles; };
 
     if (threadIdx.x == 0) {
         s_fail = 0;
@@ -211,8 +215,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int jj = step / KT, kk = step % KT;
                 mbar_expect_tx(full_bar(s), (uint32_t)STAGE_BYTES);
                 const uint32_t xs = base + (uint32_t)(s * STAGE_BYTES);
-                tma_load_2d(xs, &tmX, kk * KB / (FP8 ? 1 : 2), pblock * BM, full_bar(s));
-                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / (FP8 ? 1 : 2), (mt0 + jj) * BN, full_bar(s));
+                tma_load_2d(xs, &tmX, kk * KB / (FP8 ? 1 : 2), tile_pb(jj) * BM, full_bar(s));
+                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / (FP8 ? 1 : 2), tile_mt(jj) * BN, full_bar(s));
                 ++issued;
             }
             // let every issued copy land before shared memory can go away
@@ -264,18 +268,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         // epilogue: thread = one particle row of the tile
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
         const int row = q * 32 + lane;
-        const int i = pblock * BM + row;
-        float sum = 0.0f;
         bool ok = true;
         for (int jj = 0; jj < nt; ++jj) {
             const int a = jj & 1, u = jj >> 1;
+            const int mt = tile_mt(jj);
+            const int i = tile_pb(jj) * BM + row;
             // warp-uniform outcome: tcgen05.ld below needs the whole warp
             if (!__all_sync(0xFFFFFFFFu, mbar_wait(tfull_bar(a), (uint32_t)(u & 1), limit_ns))) {
                 ok = false;
+                part[(size_t)mt * Np + i] = __int_as_float(0x7fc00000);
                 break;
             }
             tc_fence_after();
-            const int m0 = (mt0 + jj) * BN;
+            const int m0 = mt * BN;
+            float sum = 0.0f;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
             for (int c = 0; c < BN; c += 16) {
                 float v[16];
@@ -291,12 +297,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(a));
+            part[(size_t)mt * Np + i] = sum;
         }
         if (!ok) {
             if (lane == 0) atomicOr(status, kStatusTimeout);
             s_fail = 1;
         }
-        if (i < Np) part[(size_t)blockIdx.y * Np + i] = ok ? sum : __int_as_float(0x7fc00000);
     }
     tc_fence_before();
     __syncthreads();
@@ -481,33 +487,33 @@ bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int
     p->Np = Np;
     p->Mp = Mp;
     p->Kp = Kp;
+    int dev = 0;
+    p->num_sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->num_sms < 1)
+        return false;
     if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmX), Xq, fp8, Np, Kp, BM)) return false;
     if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmA), Aq, fp8, Mp, Kp, BN)) return false;
     return true;
 }
 
-cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, int splits, float* part,
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st) {
-    const int mtiles = p.Mp / BN;
-    const int per = (mtiles + splits - 1) / splits;
+    const int ntiles = (p.Np / BM) * (p.Mp / BN);
+    const int grid = std::max(1, std::min(ntiles, p.num_sms));
     const int KT = p.Kp * (p.fp8 ? 1 : 2) / KB;
-    dim3 grid(p.Np / BM, (mtiles + per - 1) / per);
     const CUtensorMap& tx = *reinterpret_cast<const CUtensorMap*>(p.tmX);
     const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(p.tmA);
     if (p.fp8)
-        lsq_tc_kernel<true><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, per, p.Np, part,
-                                                                  status, limit_ns);
+        lsq_tc_kernel<true><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+                                                                  limit_ns);
     else
-        lsq_tc_kernel<false><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, per, p.Np, part,
-                                                                   status, limit_ns);
+        lsq_tc_kernel<false><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+                                                                   limit_ns);
     return cudaGetLastError();
 }
 
-int lsq_tc_splits_used(const LsqTcPlan& p, int splits) {
-    const int mtiles = p.Mp / BN;
-    const int per = (mtiles + splits - 1) / splits;
-    return (mtiles + per - 1) / per;
-}
+int lsq_tc_partials(const LsqTcPlan& p) { return p.Mp / BN; }
 
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
                             cudaStream_t st) {

@@ -13,6 +13,8 @@
 //
 // Every kernel reads the iteration counter from device memory, so a chain of
 // iterations can be captured in a CUDA graph.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include "cupso_device.cuh"
@@ -74,6 +76,93 @@ __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant_
             st4(s.x + off, X);
             st4(s.v + off, V);
         }
+    }
+}
+
+// Step 2 fused with the tensor-core operand of the fitness product: the same
+// moves as lsq_move_kernel, and the new positions also land in Xq[i][k]
+// (row-major, row length Kp) rounded to BF16, or multiplied by sx and rounded
+// to FP8 e4m3 with saturation -- the bytes the separate conversion would
+// write, zero for i >= N and k >= D. A CTA takes tiles of 64 particles x 64
+// dimensions; the transposition goes through shared memory, so the swarm rows
+// and the operand rows are both written in whole segments.
+template <bool FP8>
+__global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constant__ SwarmDev s, void* __restrict__ Xq,
+                                                            int Kp, float sx) {
+    __shared__ uint32_t S[32][65];   // [dimension pair][particle]: the pair's two operand values
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const uint32_t t = t_prev + 1u;
+    const float* G = s.G + (size_t)(t_prev & 1u) * s.D;
+    const size_t Np = (size_t)s.Np;
+    const int ptiles = s.Np / 64, ntiles = ptiles * (Kp / 64);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t p0 = (uint32_t)(tile % ptiles) * 64u;
+        const int dt = tile / ptiles;
+        for (int q = threadIdx.x; q < 16 * 32; q += kBlock) {
+            const int grp = q & 15, gl = q >> 4;
+            const int g = dt * 32 + gl;
+            const uint32_t i0 = p0 + 4u * (uint32_t)grp;
+            float xn[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+            if (2 * g < s.D) {
+                uint4 r[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    r[j] = philox4x32_10(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.key0, s.key1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int d = 2 * g + h;
+                    if (d >= s.D) break;
+                    const size_t off = (size_t)d * Np + i0;
+                    float4 X = ld4(s.x + off), V = ld4(s.v + off);
+                    const float4 P = ld4(s.pb + off);
+                    const float gd = __ldg(G + d);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        float xj = lane(X, j), vj = lane(V, j);
+                        move_one(xj, vj, lane(P, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
+                        set_lane(X, j, xj);
+                        set_lane(V, j, vj);
+                        xn[h][j] = xj;
+                    }
+                    st4(s.x + off, X);
+                    st4(s.v + off, V);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const bool real = i0 + j < (uint32_t)s.N;
+                const float a = real ? xn[0][j] : 0.0f, b = real ? xn[1][j] : 0.0f;
+                uint32_t wq;
+                if constexpr (FP8) {
+                    const __nv_fp8x2_e4m3 q2(make_float2(__fmul_rn(a, sx), __fmul_rn(b, sx)));
+                    wq = (uint32_t)q2.__x;
+                } else {
+                    const __nv_bfloat162 q2 = __floats2bfloat162_rn(a, b);
+                    wq = *reinterpret_cast<const uint32_t*>(&q2);
+                }
+                S[gl][4 * grp + j] = wq;
+            }
+        }
+        __syncthreads();
+        char* row0 = static_cast<char*>(Xq) + (size_t)p0 * Kp * (FP8 ? 1 : 2);
+        if constexpr (FP8) {
+            // 64 rows x 4 pieces of 16 dimensions (16 B)
+            const int c = threadIdx.x & 3, pl = threadIdx.x >> 2;
+            uint4 u;
+            u.x = (S[8 * c + 0][pl] & 0xFFFFu) | (S[8 * c + 1][pl] << 16);
+            u.y = (S[8 * c + 2][pl] & 0xFFFFu) | (S[8 * c + 3][pl] << 16);
+            u.z = (S[8 * c + 4][pl] & 0xFFFFu) | (S[8 * c + 5][pl] << 16);
+            u.w = (S[8 * c + 6][pl] & 0xFFFFu) | (S[8 * c + 7][pl] << 16);
+            *reinterpret_cast<uint4*>(row0 + (size_t)pl * Kp + dt * 64 + 16 * c) = u;
+        } else {
+            // 64 rows x 8 pieces of 8 dimensions (16 B)
+            for (int q = threadIdx.x; q < 64 * 8; q += kBlock) {
+                const int c = q & 7, pl = q >> 3;
+                const uint4 u = make_uint4(S[4 * c][pl], S[4 * c + 1][pl], S[4 * c + 2][pl], S[4 * c + 3][pl]);
+                *reinterpret_cast<uint4*>(row0 + ((size_t)pl * Kp + dt * 64 + 8 * c) * 2) = u;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -469,6 +558,15 @@ __global__ void lsq_keep_t_kernel(const __grid_constant__ SwarmDev s, uint32_t t
 
 cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st) {
     lsq_move_kernel<<<grid, kBlock, sizeof(float) * (size_t)s.D, st>>>(s);
+    return cudaGetLastError();
+}
+
+cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int grid, cudaStream_t st) {
+    if (s.Np % 64 != 0 || Kp % 64 != 0 || Kp < s.D || grid < 1) return cudaErrorInvalidValue;
+    const int ntiles = (s.Np / 64) * (Kp / 64);
+    grid = std::min(grid, ntiles);
+    if (fp8) lsq_move_q_kernel<true><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
+    else lsq_move_q_kernel<false><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
     return cudaGetLastError();
 }
 

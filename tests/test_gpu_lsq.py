@@ -145,3 +145,26 @@ def test_lsq_approx_swarm_gbest_is_fp64_verified(P, precision):
             assert np.all(st["pbest_fit"] <= prev["pbest_fit"])
             assert np.all(np.abs(st["v"]) <= np.float32(0.4))
             prev64, prev = g64, st
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_lsq_swarm_operand_matches_standalone_eval(P, precision):
+    """The swarm's move kernel writes the tensor-core operand itself; the fitness
+    that follows must be what cupso_lsq_eval computes from the same positions:
+    every particle whose pbest improved in a step holds exactly that value.
+    D = 200 leaves a ragged last dimension tile, N = 1500 a ragged particle block."""
+    N, D, M = 1500, 200, 300
+    A, b, _ = _problem(M, D, 1, seed=5)
+    with _lsq_swarm(P, A, b, N, 7, precision) as s:
+        s.step(2)
+        before = s.state()
+        s.step(1)
+        st = s.state()
+    improved = st["pbest_fit"] < before["pbest_fit"]
+    assert improved.sum() > 10
+    X = st["pos"]
+    if precision == "fp8":
+        # cupso_lsq_eval scales X by 448 / max|X|; a row at the bound gives the swarm's scale, 448 / 2
+        X = np.vstack([X, np.full((1, D), 2.0, np.float32)])
+    f = _eval(P, A, b, X, P.CUPSO_LSQ_BF16 if precision == "bf16" else P.CUPSO_LSQ_FP8)[:N]
+    np.testing.assert_array_equal(st["pbest_fit"][improved].view(np.uint32), f[improved].view(np.uint32))

@@ -121,8 +121,9 @@ typedef enum {
                                            for small swarms, so that their units fill the GPU) */
     CUPSO_OPT_TIME_FITNESS = 7,   /* 1: time the fitness phase of least-squares iterations with
                                      CUDA events (no graph capture); 0: off. Read in cupso_info.
-                                     BF16/FP8: the tensor-core product and the partial sums (the
-                                     move kernel before it writes the operand) */
+                                     BF16/FP8: the tensor-core product alone (the move kernel
+                                     before it writes the operand; the selection after it adds the
+                                     product's partial sums) */
     CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
                                        lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
 } cupso_option;

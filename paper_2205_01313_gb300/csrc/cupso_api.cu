@@ -82,13 +82,13 @@ struct cupso_swarm {
         const float* b = nullptr;   // [M], borrowed
         int M = 0, precision = 0;
         LsqTcState tc;              // BF16 / FP8 operands and plan
-        void* buf = nullptr;        // f [Np] | cand [blocks*16 + 16] | partial [16 * chunks] | g64
+        void* buf = nullptr;        // f [Np] | cand [blocks*16 + 16 + ticket] | partial [16 * chunks] | g64
         float* f = nullptr;
         unsigned long long* cand = nullptr;
         double* partial = nullptr;
         double* g64 = nullptr;
         unsigned int* flags = nullptr;   // [Np / 4]: improved this iteration (one byte per particle)
-        int chunks = 32;
+        int chunks = 32;                 // pieces of the FP64 rescoring per candidate (set with A)
         LsqGram gram;                    // FP64 A^T A etc. for the rescoring when D <= M
         void* gram_buf = nullptr;
         bool time_fitness = false;       // CUPSO_OPT_TIME_FITNESS
@@ -231,14 +231,16 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
     }
-    if (lsq_eval_tc_operand(&L.tc, h->N, L.f, st) != CUPSO_OK) return cudaErrorLaunchFailure;
+    // the product leaves partial sums; the selection kernel adds them
+    if (lsq_eval_tc_partials(&L.tc, st) != CUPSO_OK) return cudaErrorLaunchFailure;
     if (L.time_fitness) {
         cudaEventRecord(e1, st);
         L.ev.push_back(e0);
         L.ev.push_back(e1);
     }
-    return lsq_launch_gbest_approx(h->dev, L.f, 0, L.A, L.b, L.M, L.cand, L.partial, L.chunks, L.g64, L.flags, grid,
-                                   L.gram, st);
+    return lsq_launch_gbest_approx(h->dev, nullptr, L.tc.part, lsq_tc_partials(L.tc.plan), 0, true, L.A, L.b, L.M,
+                                   L.cand, L.partial, L.chunks, L.g64, reinterpret_cast<unsigned int*>(h->dev.pflag),
+                                   grid, L.gram, st);
 }
 
 cudaError_t launch_one64(cupso_swarm* h, int mode, cudaStream_t st) {
@@ -713,6 +715,8 @@ int cupso_step(cupso_handle h, int iters) {
             cudaError_t e = launch_lsq_iteration(h, h->stream);
             if (e != cudaSuccess) return cuda_fail(e, "least-squares iteration");
         }
+        // the tensor-core iteration leaves improved pbest rows to the next move
+        if (h->lsq->precision != CUPSO_LSQ_FP32) h->lazy_pending = true;
         h->t_host += (uint32_t)iters;
         return CUPSO_OK;
     }
@@ -869,20 +873,25 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     L->b = b_dev;
     L->M = M;
     L->precision = precision;
-    const int nblk = tiles_of(h->Np);
-    const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256) +
+    const int nblk = lsq_cand_blocks(h->Np);
+    // FP64 rescoring in pieces of 8 row pairs of A^T A, one per warp of a block
+    L->chunks = std::max(32, ((h->D + 1) / 2 + 7) / 8);
+    // candidates: 16 per block, the merged 16, and the merging ticket
+    const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 17), 256) +
                          align_up(sizeof(double) * 16 * L->chunks, 256) + align_up((size_t)h->Np, 256) + 256;
     cudaError_t e = cudaMalloc(&L->buf, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (lsq)");
     char* p = static_cast<char*>(L->buf);
     L->f = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * h->Np, 256);
-    L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nblk * 16 + 16), 256);
+    L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nblk * 16 + 17), 256);
     L->partial = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * 16 * L->chunks, 256);
     L->flags = reinterpret_cast<unsigned int*>(p); p += align_up((size_t)h->Np, 256);
     L->g64 = reinterpret_cast<double*>(p);
     const double inf = INFINITY;
     CUPSO_CUDA(cudaMemcpyAsync(L->g64, &inf, sizeof(double), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync");
     CUPSO_CUDA(cudaMemsetAsync(L->f, 0, sizeof(float) * h->Np, h->stream), "cudaMemsetAsync");
+    CUPSO_CUDA(cudaMemsetAsync(L->cand + (size_t)nblk * 16 + 16, 0, sizeof(unsigned long long), h->stream),
+               "cudaMemsetAsync");
     if (precision != CUPSO_LSQ_FP32) {
         // FP8 scale of the positions from the search box
         const float xmax = std::max(std::fabs(h->dev.lo), std::fabs(h->dev.hi));
@@ -915,8 +924,10 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         CUPSO_CUDA(lsq_launch_set_pf(h->dev, L->f, h->stream), "lsq pbest");
         // the accept kernel advances t: start one below and let it land on t_host
         CUPSO_CUDA(lsq_launch_set_t(h->dev, h->t_host - 1u, h->stream), "lsq t");
-        CUPSO_CUDA(lsq_launch_gbest_approx(h->dev, L->f, 1, A_dev, b_dev, M, L->cand, L->partial, L->chunks, L->g64,
-                                           L->flags, h->num_sms * 8, L->gram, h->stream),
+        CUPSO_CUDA(lsq_launch_gbest_approx(h->dev, L->f, nullptr, 0, 1, true, A_dev, b_dev, M, L->cand, L->partial,
+                                           L->chunks,
+                                           L->g64, reinterpret_cast<unsigned int*>(h->dev.pflag), h->num_sms * 8,
+                                           L->gram, h->stream),
                    "lsq gbest");
     }
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");

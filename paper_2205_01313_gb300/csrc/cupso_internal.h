@@ -87,6 +87,9 @@ void lsq_free_tc(LsqTcState* st);
 int lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, float* f, cudaStream_t stream);
 // f[i], i < N, for the operand already in st->Xq (asynchronous).
 int lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream);
+// The same product, leaving f[i] as lsq_tc_partials(st->plan) partial sums
+// st->part[k][i] (f[i] = their sum in k order).
+int lsq_eval_tc_partials(LsqTcState* st, cudaStream_t stream);
 
 // f[i] = plain FP32 fitness of X(i, d) = x[d * ldx + i], i < N.
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
@@ -100,7 +103,8 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
 cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int grid, cudaStream_t st);
 cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
                                     cudaStream_t st);
-int lsq_cand_blocks(const SwarmDev& s);
+// Blocks of the candidate selection (one particle per thread).
+int lsq_cand_blocks(int Np);
 // FP64 Gram data of the rescoring (Gm = A^T A, cvec = A^T b, bb = b^T b); Gm null: direct form.
 struct LsqGram {
     double* Gm = nullptr;
@@ -108,9 +112,15 @@ struct LsqGram {
     double bb = 0.0;
 };
 cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, cudaStream_t st);
-cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all, const float* A, const float* b,
-                                    int M, unsigned long long* cand, double* partial, int chunks, double* g64,
-                                    unsigned int* flags, int grid, const LsqGram& gram, cudaStream_t st);
+// Steps 4-5 with an approximate fitness. lazy: flags is s.pflag and the
+// improved particles' pbest_pos rows are left to the next move (and to the
+// materialize kernel); otherwise they are copied here.
+// fit: the approximate fitness, or null with part/nparts: its partial sums
+// part[k][i] (Np apart), added in k order.
+cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const float* part, int nparts, int all,
+                                    bool lazy, const float* A, const float* b, int M, unsigned long long* cand,
+                                    double* partial, int chunks, double* g64, unsigned int* flags, int grid,
+                                    const LsqGram& gram, cudaStream_t st);
 cudaError_t lsq_launch_set_pf(const SwarmDev& s, const float* fit, cudaStream_t st);
 // FP64 fitness of the pbest_pos of the particle in `key`, into *g64; waits.
 cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, int M, unsigned long long key,

@@ -142,6 +142,13 @@ int cupso::lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, i
     return lsq_eval_tc_operand(st, N, f, stream);
 }
 
+int cupso::lsq_eval_tc_partials(LsqTcState* st, cudaStream_t stream) {
+    cudaError_t e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->part, st->status,
+                                  2000000000ll, stream);
+    if (e != cudaSuccess) return set_cuda_error(e, "lsq tensor-core launch"), CUPSO_ERR_CUDA;
+    return CUPSO_OK;
+}
+
 int cupso::lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream) {
     cudaError_t e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->part, st->status,
                                   2000000000ll, stream);

@@ -29,13 +29,6 @@ namespace {
 
 constexpr int kCand = 16;   // candidates rescored in FP64 per iteration
 
-__device__ __forceinline__ unsigned long long my_min4(const unsigned long long k[4]) {
-    unsigned long long m = k[0];
-#pragma unroll
-    for (int j = 1; j < 4; ++j) m = k[j] < m ? k[j] : m;
-    return m;
-}
-
 }  // namespace
 
 // Steps 2 of every particle at iteration t = *t_dev + 1 (the fitness is a
@@ -85,7 +78,9 @@ __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant_
 // to FP8 e4m3 with saturation -- the bytes the separate conversion would
 // write, zero for i >= N and k >= D. A CTA takes tiles of 64 particles x 64
 // dimensions; the transposition goes through shared memory, so the swarm rows
-// and the operand rows are both written in whole segments.
+// and the operand rows are both written in whole segments. Lazy pbest: a
+// particle flagged in s.pflag improved in the previous iteration, so its
+// pbest_pos is the position loaded here; that row is written back on the way.
 template <bool FP8>
 __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constant__ SwarmDev s, void* __restrict__ Xq,
                                                             int Kp, float sx) {
@@ -98,7 +93,34 @@ __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constan
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t p0 = (uint32_t)(tile % ptiles) * 64u;
         const int dt = tile / ptiles;
-        for (int q = threadIdx.x; q < 16 * 32; q += kBlock) {
+        // 512 (4-particle group, dimension pair) items, kItems per thread; every
+        // row of all of them is loaded before any is used, so that a thread
+        // keeps 6 kItems loads in flight
+        constexpr int kItems = 16 * 32 / kBlock;
+        float4 X[kItems][2], V[kItems][2], P[kItems][2];
+        uint32_t fl[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int q = (int)threadIdx.x + it * kBlock;
+            const int g = dt * 32 + (q >> 4);
+            const uint32_t i0 = p0 + 4u * (uint32_t)(q & 15);
+            fl[it] = 0u;
+            if (2 * g < s.D) fl[it] = __ldcg(reinterpret_cast<const unsigned int*>(s.pflag) + (i0 >> 2));
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int d = 2 * g + h;
+                X[it][h] = V[it][h] = P[it][h] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (d < s.D) {
+                    const size_t off = (size_t)d * Np + i0;
+                    X[it][h] = ld4(s.x + off);
+                    V[it][h] = ld4(s.v + off);
+                    P[it][h] = ld4(s.pb + off);
+                }
+            }
+        }
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int q = (int)threadIdx.x + it * kBlock;
             const int grp = q & 15, gl = q >> 4;
             const int g = dt * 32 + gl;
             const uint32_t i0 = p0 + 4u * (uint32_t)grp;
@@ -113,19 +135,24 @@ __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constan
                     const int d = 2 * g + h;
                     if (d >= s.D) break;
                     const size_t off = (size_t)d * Np + i0;
-                    float4 X = ld4(s.x + off), V = ld4(s.v + off);
-                    const float4 P = ld4(s.pb + off);
+                    float4 Xh = X[it][h], Vh = V[it][h], Ph = P[it][h];
+                    if (fl[it]) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if ((fl[it] >> (8 * j)) & 1u) set_lane(Ph, j, lane(Xh, j));
+                        st4(s.pb + off, Ph);
+                    }
                     const float gd = __ldg(G + d);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        float xj = lane(X, j), vj = lane(V, j);
-                        move_one(xj, vj, lane(P, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
-                        set_lane(X, j, xj);
-                        set_lane(V, j, vj);
+                        float xj = lane(Xh, j), vj = lane(Vh, j);
+                        move_one(xj, vj, lane(Ph, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
+                        set_lane(Xh, j, xj);
+                        set_lane(Vh, j, vj);
                         xn[h][j] = xj;
                     }
-                    st4(s.x + off, X);
-                    st4(s.v + off, V);
+                    st4(s.x + off, Xh);
+                    st4(s.v + off, Vh);
                 }
             }
 #pragma unroll
@@ -254,69 +281,103 @@ __global__ void lsq_gather_kernel(const __grid_constant__ SwarmDev s) {
     }
 }
 
-// Step 4 with an approximate fitness, and each block's 16 lowest keys among the
-// particles that improved (all particles when `all` is set: the first gbest).
-// One 1024-particle tile per block; cand[block][16] (kKeyNone where fewer).
-__global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
-                                                                 const float* __restrict__ fit, int all,
-                                                                 unsigned long long* __restrict__ cand,
-                                                                 unsigned int* __restrict__ flags) {
-    __shared__ unsigned long long red[kBlock / 32];
-    const uint32_t i0 = (uint32_t)blockIdx.x * kTile + threadIdx.x * kPerThread;
-    unsigned long long k4[4] = {kKeyNone, kKeyNone, kKeyNone, kKeyNone};
-    bool nan = false;
-    if (i0 < (uint32_t)s.Np) {
-        float f[4], pf[4];
-        const float4 F = ld4(fit + i0);
-        f[0] = F.x; f[1] = F.y; f[2] = F.z; f[3] = F.w;
-        if (all) flags[i0 / 4] = 0u;
-        const unsigned mask = all ? 0u : lsq_pf4(s, i0, f, flags);
-        (void)pf;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const bool real = (i0 + j) < (uint32_t)s.N;
-            if (real && (all || (mask & (1u << j)))) k4[j] = pack_key(f[j], i0 + j);
-        }
-        nan = any_nan4(s, i0, f);
-    }
-    if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
-    // 16 rounds: the block minimum, removed by its owner
-    for (int r = 0; r < kCand; ++r) {
-        const unsigned long long m = block_min(my_min4(k4), red);
-        if (threadIdx.x == 0) cand[(size_t)blockIdx.x * kCand + r] = m;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (k4[j] == m) k4[j] = kKeyNone;
-    }
-}
-
-// The 16 lowest keys over all blocks' candidate lists, ascending, into top[16].
-// Keys are unique (the index is in the low bits), so round r takes the
-// smallest key above round r-1's.
-__global__ void __launch_bounds__(1024) lsq_merge_cand_kernel(const unsigned long long* __restrict__ cand, int n,
-                                                              unsigned long long* __restrict__ top) {
-    __shared__ unsigned long long red[32];
+// The 16 smallest keys a warp holds, ascending, into out[0..15] (lane 0
+// writes): round r takes the smallest key above round r-1's (keys are unique:
+// the particle index is in the low bits; kKeyNone fills the rounds past the
+// last key). item(q) is the lane's q-th key, q < n (N > 0: n = N, unrolled).
+template <int N, typename Item>
+__device__ __forceinline__ void warp_top(Item item, int n, unsigned long long* out) {
     unsigned long long last = 0;
     for (int r = 0; r < kCand; ++r) {
         unsigned long long lm = kKeyNone;
-        for (int e = threadIdx.x; e < n; e += blockDim.x) {
-            const unsigned long long k = cand[e];
-            if ((r == 0 || k > last) && k < lm) lm = k;
+        if constexpr (N > 0) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) {
+                const unsigned long long k = item(q);
+                if ((r == 0 || k > last) && k < lm) lm = k;
+            }
+        } else {
+            for (int q = 0; q < n; ++q) {
+                const unsigned long long k = item(q);
+                if ((r == 0 || k > last) && k < lm) lm = k;
+            }
         }
-        const unsigned long long m = block_min(lm, red);
-        if (threadIdx.x == 0) top[r] = m;
+        const unsigned long long m = warp_min_u64(lm);
+        if ((threadIdx.x & 31) == 0) out[r] = m;
         last = m;
-        if (m == kKeyNone) {
-            for (int q = r + 1 + (int)threadIdx.x; q < kCand; q += blockDim.x) top[q] = kKeyNone;
-            break;
-        }
     }
 }
 
+// Step 4 with an approximate fitness, and the 16 lowest keys among the
+// particles that improved (all particles when `all` is set: the first gbest).
+// One particle per thread: each warp finds its 16 lowest, warp 0 the block's
+// 16 of those (cand[block][16]); the last block to finish merges all blocks'
+// lists into top[16], ascending (kKeyNone where fewer). The fitness comes from
+// `fit`, or, with `part`, as the sum of the product's nparts partial sums in
+// their order.
+__global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
+                                                                 const float* __restrict__ fit,
+                                                                 const float* __restrict__ part, int nparts,
+                                                                 int all,
+                                                                 unsigned long long* __restrict__ cand,
+                                                                 unsigned int* __restrict__ flags,
+                                                                 unsigned long long* __restrict__ top,
+                                                                 unsigned int* __restrict__ ticket) {
+    __shared__ unsigned long long wtop[kBlock / 32][kCand];
+    __shared__ int s_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t i = (uint32_t)blockIdx.x * kBlock + threadIdx.x;
+    unsigned long long key = kKeyNone;
+    bool nan = false;
+    if (i < (uint32_t)s.Np) {
+        float f = 0.0f;
+        if (part) {
+            for (int k = 0; k < nparts; ++k) f = __fadd_rn(f, __ldcg(part + (size_t)k * s.Np + i));
+        } else {
+            f = fit[i];
+        }
+        const bool real = i < (uint32_t)s.N;
+        // strict improvement; the byte flag tells the next move (or the
+        // pbest copy) that pbest_pos must become pos
+        unsigned char fl = 0;
+        if (!all && real && f < s.pf[i]) {
+            s.pf[i] = f;
+            fl = 1;
+        }
+        reinterpret_cast<unsigned char*>(flags)[i] = fl;
+        if (real && (all || fl)) key = pack_key(f, i);
+        nan = real && (f != f);
+    }
+    if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
+    constexpr int kPerLane = kBlock / 32 * kCand / 32;   // the block's warp lists, over warp 0's lanes
+    warp_top<1>([&](int) { return key; }, 1, wtop[warp]);
+    __syncthreads();
+    const unsigned long long* flat = &wtop[0][0];
+    if (warp == 0)
+        warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, cand + (size_t)blockIdx.x * kCand);
+    // the last block merges
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int n = (int)gridDim.x * kCand;
+    const int tid = (int)threadIdx.x;
+    const int per = tid < n ? (n - tid + kBlock - 1) / kBlock : 0;   // this thread's entries: tid + kBlock q
+    warp_top<0>([&](int q) { return __ldcg(cand + tid + (size_t)kBlock * q); }, per, wtop[warp]);
+    __syncthreads();
+    if (warp == 0) warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, top);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
 // FP64 rescoring: partial[c][chunk] = sum over rows m of the chunk of
-// (sum_d A[m][d] pbest_pos[d][i_c] - b[m])^2 in double, i_c = index of top[c].
-// One warp per row at a time, lanes over d; fixed reduction order throughout.
+// (sum_d A[m][d] src[d][i_c] - b[m])^2 in double, i_c = index of top[c], src
+// the candidates' pbest_pos (or their positions, which equal it when they
+// improved in this iteration). One warp per row at a time, lanes over d;
+// fixed reduction order throughout.
 __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant__ SwarmDev s,
+                                                          const float* __restrict__ src,
                                                           const float* __restrict__ A, const float* __restrict__ b,
                                                           int M, const unsigned long long* __restrict__ top,
                                                           int rows_per_chunk, double* __restrict__ partial) {
@@ -330,7 +391,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
         return;
     }
     const uint32_t i = (uint32_t)(key & 0xFFFFFFFFull);
-    for (int d = threadIdx.x; d < s.D; d += blockDim.x) xc[d] = (double)s.pb[(size_t)d * s.Np + i];
+    for (int d = threadIdx.x; d < s.D; d += blockDim.x) xc[d] = (double)src[(size_t)d * s.Np + i];
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = chunk * rows_per_chunk, m1 = min(M, m0 + rows_per_chunk);
@@ -371,6 +432,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
 // partial[cand][chunk] = its rows' terms (+ bb in chunk 0), pairs in order per
 // warp, warps in a fixed order.
 __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_constant__ SwarmDev s,
+                                                               const float* __restrict__ src,
                                                                const double* __restrict__ Gm,
                                                                const double* __restrict__ cvec, double bb,
                                                                const unsigned long long* __restrict__ top,
@@ -387,7 +449,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
         live[q] = key != kKeyNone;
         const uint32_t i = live[q] ? (uint32_t)(key & 0xFFFFFFFFull) : 0u;
         for (int d = threadIdx.x; d < D; d += blockDim.x)
-            xg[q * D + d] = live[q] ? (double)s.pb[(size_t)d * s.Np + i] : 0.0;
+            xg[q * D + d] = live[q] ? (double)src[(size_t)d * s.Np + i] : 0.0;
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -485,6 +547,7 @@ __global__ void __launch_bounds__(256) lsq_gram_kernel(const float* __restrict__
 // Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
 // Warp c sums candidate c's chunks (in chunk order); thread 0 compares.
 __global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__ SwarmDev s,
+                                                         const float* __restrict__ src,
                                                          const unsigned long long* __restrict__ top,
                                                          const double* __restrict__ partial, int chunks,
                                                          double* __restrict__ g64) {
@@ -520,7 +583,7 @@ __global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__
     __syncthreads();
     const int best = s_best;
     for (int d = threadIdx.x; d < s.D; d += blockDim.x)
-        s.G[(size_t)nxt * s.D + d] = best >= 0 ? s.pb[(size_t)d * s.Np + best] : s.G[(size_t)cur * s.D + d];
+        s.G[(size_t)nxt * s.D + d] = best >= 0 ? src[(size_t)d * s.Np + best] : s.G[(size_t)cur * s.D + d];
     if (threadIdx.x == 0) {
         if (best >= 0) {
             *g64 = s_f;
@@ -583,7 +646,7 @@ cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigne
     return cudaGetLastError();
 }
 
-int lsq_cand_blocks(const SwarmDev& s) { return tiles_of(s.Np); }
+int lsq_cand_blocks(int Np) { return (Np + kBlock - 1) / kBlock; }
 
 cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec,
                             cudaStream_t st) {
@@ -593,34 +656,36 @@ cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double
 
 // cand: [blocks * 16] + [16] scratch; partial: [16 * chunks]; flags: [Np / 4].
 // With Gm set (D <= M) the rescoring uses the FP64 Gram form.
-cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, int all, const float* A, const float* b,
-                                    int M, unsigned long long* cand, double* partial, int chunks, double* g64,
-                                    unsigned int* flags, int grid, const LsqGram& gram, cudaStream_t st) {
-    const int nblk = tiles_of(s.Np);
+cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const float* part, int nparts, int all,
+                                    bool lazy, const float* A, const float* b, int M, unsigned long long* cand,
+                                    double* partial, int chunks, double* g64, unsigned int* flags, int grid,
+                                    const LsqGram& gram, cudaStream_t st) {
+    const int nblk = lsq_cand_blocks(s.Np);
     unsigned long long* top = cand + (size_t)nblk * kCand;
-    lsq_select_cand_kernel<<<nblk, kBlock, 0, st>>>(s, fit, all, cand, flags);
+    unsigned int* ticket = reinterpret_cast<unsigned int*>(top + kCand);
+    lsq_select_cand_kernel<<<nblk, kBlock, 0, st>>>(s, fit, part, nparts, all, cand, flags, top, ticket);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (!all) {
+    if (!all && !lazy) {
         lsq_copy_pbest_kernel<<<grid, kBlock, 0, st>>>(s, flags);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    lsq_merge_cand_kernel<<<1, 1024, 0, st>>>(cand, nblk * kCand, top);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    // the candidates improved in this iteration (or, with `all`, are every
+    // pbest): their pbest_pos is the position, pending write-back when lazy
+    const float* src = (lazy && !all) ? s.x : s.pb;
     if (gram.Gm) {
         const int pairs = ((s.D + 1) / 2 + chunks - 1) / chunks;
         lsq_rescore_gram_kernel<<<dim3(kCand / 4, chunks), 256, sizeof(double) * 4 * (size_t)s.D, st>>>(
-            s, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial);
+            s, src, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial);
     } else {
         const int rows = (M + chunks - 1) / chunks;
-        lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, A, b, M, top, rows,
-                                                                                          partial);
+        lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, src, A, b, M, top,
+                                                                                          rows, partial);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    lsq_accept_kernel<<<1, 512, 0, st>>>(s, top, partial, chunks, g64);
+    lsq_accept_kernel<<<1, 512, 0, st>>>(s, src, top, partial, chunks, g64);
     return cudaGetLastError();
 }
 
@@ -632,8 +697,8 @@ cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, i
     cudaError_t e = cudaMemcpyAsync(scratch, top, sizeof(top), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     const int rows = (M + chunks - 1) / chunks;
-    lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, A, b, M, scratch, rows,
-                                                                                      partial);
+    lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, s.pb, A, b, M, scratch,
+                                                                                      rows, partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     lsq_sum_one_kernel<<<1, 32, 0, st>>>(partial, chunks, g64);

@@ -168,3 +168,23 @@ def test_lsq_swarm_operand_matches_standalone_eval(P, precision):
         X = np.vstack([X, np.full((1, D), 2.0, np.float32)])
     f = _eval(P, A, b, X, P.CUPSO_LSQ_BF16 if precision == "bf16" else P.CUPSO_LSQ_FP8)[:N]
     np.testing.assert_array_equal(st["pbest_fit"][improved].view(np.uint32), f[improved].view(np.uint32))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_lsq_swarm_lazy_pbest_consistent(P, precision):
+    """The tensor-core iteration leaves improved particles' pbest rows to be
+    written back by the next move (or before the state is read). With state
+    reads in the middle of the run, every particle's pbest_fit must still be
+    the approximate fitness of its pbest_pos, bit for bit."""
+    N, D, M = 700, 72, 200
+    A, b, _ = _problem(M, D, 1, seed=9)
+    with _lsq_swarm(P, A, b, N, 3, precision) as s:
+        s.step(3)
+        s.state()            # writes the pending rows back in the middle of the run
+        s.step(20)           # a captured graph of 16, then single launches
+        st = s.state()
+    X = st["pbest_pos"]
+    if precision == "fp8":
+        X = np.vstack([X, np.full((1, D), 2.0, np.float32)])   # the swarm's FP8 scale, 448 / 2
+    f = _eval(P, A, b, X, P.CUPSO_LSQ_BF16 if precision == "bf16" else P.CUPSO_LSQ_FP8)[:N]
+    np.testing.assert_array_equal(st["pbest_fit"].view(np.uint32), f.view(np.uint32))

@@ -223,7 +223,7 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
         return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
     // the move writes the tensor-core operand too; the fitness is then the product alone
-    cudaError_t e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms * 6, st);
+    cudaError_t e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms, st);
     if (e != cudaSuccess) return e;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (L.time_fitness) {

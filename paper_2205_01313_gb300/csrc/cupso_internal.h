@@ -100,7 +100,7 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
 // The same moves, writing the new positions also as the tensor-core operand
 // Xq ([Np][Kp], BF16, or FP8 e4m3 of x * sx), zero for i >= N and k >= D.
 // Requires Np and Kp multiples of 64 and Kp >= D.
-cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int grid, cudaStream_t st);
+cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int num_sms, cudaStream_t st);
 cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
                                     cudaStream_t st);
 // Blocks of the candidate selection (one particle per thread).

@@ -624,10 +624,14 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int grid, cudaStream_t st) {
-    if (s.Np % 64 != 0 || Kp % 64 != 0 || Kp < s.D || grid < 1) return cudaErrorInvalidValue;
+cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int num_sms, cudaStream_t st) {
+    if (s.Np % 64 != 0 || Kp % 64 != 0 || Kp < s.D || num_sms < 1) return cudaErrorInvalidValue;
     const int ntiles = (s.Np / 64) * (Kp / 64);
-    grid = std::min(grid, ntiles);
+    // one wave of resident CTAs walks the tiles
+    int per_sm = 0;
+    const void* k = fp8 ? (const void*)lsq_move_q_kernel<true> : (const void*)lsq_move_q_kernel<false>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int grid = std::min(num_sms * per_sm, ntiles);
     if (fp8) lsq_move_q_kernel<true><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
     else lsq_move_q_kernel<false><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
     return cudaGetLastError();

@@ -374,6 +374,21 @@ def test_batched_solve_general_path_matches_oracle(P, kernel, monkeypatch):
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
 
 
+def test_batched_solve_wide_swarm_matches_oracle(P, monkeypatch):
+    """A swarm wider than any tile (D = 4500 > 4096 items) leaves only the
+    streaming kernel to the tuner; next to small swarms it must still give
+    every swarm's oracle result."""
+    monkeypatch.delenv("CUPSO_BATCH_KERNEL", raising=False)
+    probs = _mixed_batch(4, 21, (64, 300), (3, 20))
+    probs.append(dict(D=4500, N=130, bounds=BOUNDS[3], w=W, c1=C12, c2=C12, fitness_id=3, seed=77, swarm_id=9))
+    rc, res = P.cupso_solve_batch(probs, 20)
+    assert rc == P.CUPSO_OK
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"]).init().step_sync(20)
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
 def test_batched_kernels_interchange_with_lazy_pbest(P, monkeypatch):
     """The tuner may switch kernels between iterations of one solve; the
     streaming kernel leaves pbest rows pending (lazy write-back) and the tiled

@@ -218,7 +218,7 @@ CUPSO_API int cupso_set_state(cupso_handle h, const float* pos, const float* v, 
 CUPSO_API int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M, int precision);
 
 /* FP64 fitness ||A g - b||^2 of the current gbest_pos g of a least-squares
- * swarm (the residual the precision modes are judged by). Waits. */
+ * swarm (the residual by which the precision modes are compared). Waits. */
 CUPSO_API int cupso_get_gbest_f64(cupso_handle h, double* fit_out);
 
 /* Double-precision swarm: the paper's own precision (Sec. 5.1 runs FP64).

@@ -1,6 +1,6 @@
 """Asynchronous path (Sec. 3.2 / Alg. 3 without a grid barrier).
 
-Its trajectory depends on timing, so it is judged by invariants, by the one
+Its trajectory depends on timing, so it is checked by invariants, by the one
 case where it must equal the synchronous path (a single CTA), and by reaching
 the known optimum to 1e-4 on workloads where PSO does. Its bounded waits are
 tested by holding the lock from the start: every wait must expire, set the

@@ -8,14 +8,16 @@
 // with that particle's position (Sec. 4.3: index first, position after) --
 // into a slot of every CTA of the cluster through distributed shared memory,
 // then one cluster barrier replaces the paper's kernel boundary (Sec. 2.2).
-// Every CTA then reduces the same slots in the same order, so all hold the
-// same gbest. The arithmetic is that of the streaming kernels: bit-identical
-// synchronous PSO.
+// Every thread then reduces the same slots in the same order, so all hold the
+// same gbest. pbest rows are copied lazily (in the next move), so an
+// iteration takes three CTA barriers and the cluster barrier. The arithmetic
+// is that of the streaming kernels: bit-identical synchronous PSO.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "stream_common.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -29,7 +31,7 @@ constexpr int kMaxCluster = 16;
 struct OnchipLayout {
     int P;            // particles per CTA (Np / cluster)
     int C;            // CTAs in the cluster
-    size_t o_x, o_v, o_pb, o_aux, o_pf, o_fit, o_imp, o_G, o_slots, bytes;
+    size_t o_x, o_v, o_pb, o_aux, o_pf, o_imp, o_G, o_slots, bytes;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) / 16 * 16; }
@@ -45,7 +47,6 @@ __host__ __device__ inline OnchipLayout onchip_layout(int Np, int D, int C) {
     L.o_pb = o; o = al16(o + plane);
     L.o_aux = o; o = al16(o + plane);                 // cos2pi(x') where the fitness needs it
     L.o_pf = o; o = al16(o + sizeof(float) * L.P);
-    L.o_fit = o; o = al16(o + sizeof(float) * L.P);
     L.o_imp = o; o = al16(o + sizeof(int) * L.P);
     L.o_G = o; o = al16(o + sizeof(float) * D);
     // slots[2][C]: 8-byte key then D floats, padded to 16 bytes
@@ -58,7 +59,7 @@ __host__ __device__ inline OnchipLayout onchip_layout(int Np, int D, int C) {
 
 __device__ __forceinline__ size_t slot_bytes(int D) { return al16(8 + sizeof(float) * (size_t)D); }
 
-template <int FIT>
+template <int FIT, bool FAST>
 __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_constant__ SwarmDev s, int iters) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cluster = cg::this_cluster();
@@ -72,20 +73,21 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
     float* pb = reinterpret_cast<float*>(smem + L.o_pb);
     float* caux = reinterpret_cast<float*>(smem + L.o_aux);
     float* pf = reinterpret_cast<float*>(smem + L.o_pf);
-    float* fit = reinterpret_cast<float*>(smem + L.o_fit);
     int* imp = reinterpret_cast<int*>(smem + L.o_imp);
     float* G = reinterpret_cast<float*>(smem + L.o_G);
     unsigned char* slots = smem + L.o_slots;
     const size_t sb = slot_bytes(D);
     __shared__ unsigned long long red[kOnchipThreads / 32];
-    __shared__ unsigned long long s_K;
 
     const uint32_t base = (uint32_t)rank * (uint32_t)P;   // first particle of this CTA
     const size_t Np = (size_t)s.Np;
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur0 = (int)(t_prev & 1u);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // Load the CTA's particles, gbest and its key.
+    // Load the CTA's particles, gbest and its key. imp[p] marks a particle
+    // whose pbest_pos row is still to be copied from its position (lazy
+    // pbest: the copy happens in the next move, or at the end).
     for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
         const int d = e / P, p = e - d * P;
         const size_t g = (size_t)d * Np + base + p;
@@ -93,53 +95,54 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
         v[e] = s.v[g];
         pb[e] = s.pb[g];
     }
-    for (int p = threadIdx.x; p < P; p += blockDim.x) pf[p] = s.pf[base + p];
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        pf[p] = s.pf[base + p];
+        imp[p] = 0;
+    }
     for (int d = threadIdx.x; d < D; d += blockDim.x) G[d] = s.G[(size_t)cur0 * D + d];
-    if (threadIdx.x == 0) s_K = s.gkey[cur0];
+    // every thread keeps the gbest key; all of them compute the same one each iteration
+    unsigned long long K = __ldcg(s.gkey + cur0);
     __syncthreads();
 
     const int npairs = (D + 1) / 2;
     bool nan = false;
     for (int k = 0; k < iters; ++k) {
         const uint32_t t = t_prev + 1u + (uint32_t)k;
-        const unsigned long long K = s_K;
-        // Steps 2 (Eq. 1, Eq. 2): one Philox call per (particle, dimension pair).
+        // Step 2 (Eq. 1, Eq. 2): one Philox call per (particle, dimension pair).
+#pragma unroll 2
         for (int e = threadIdx.x; e < P * npairs; e += blockDim.x) {
             const int g2 = e / P, p = e - g2 * P;
             const uint4 r = philox4x32_10(make_uint4((uint32_t)g2, base + (uint32_t)p, t, s.swarm), s.key0, s.key1);
+            const bool lazy = imp[p] != 0;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int d = 2 * g2 + h;
                 if (d >= D) break;
                 const int idx = d * P + p;
-                const float r1 = u01(h == 0 ? r.x : r.z);
-                const float r2 = u01(h == 0 ? r.y : r.w);
                 float xx = x[idx], vv = v[idx];
-                const float cognitive = __fsub_rn(pb[idx], xx);
-                const float social = __fsub_rn(G[d], xx);
-                float vel = __fmul_rn(s.w, vv);
-                vel = __fmaf_rn(__fmul_rn(s.c1, r1), cognitive, vel);
-                vel = __fmaf_rn(__fmul_rn(s.c2, r2), social, vel);
-                vv = clampf(vel, -s.vmax, s.vmax);
-                xx = clampf(__fadd_rn(xx, vv), s.lo, s.hi);
+                float pp = pb[idx];
+                if (lazy) {
+                    pp = xx;
+                    pb[idx] = xx;
+                }
+                if constexpr (FAST)
+                    move_one_fast(xx, vv, pp, G[d], hi24(word(r, 2 * h)), hi24(word(r, 2 * h + 1)), s);
+                else
+                    move_one(xx, vv, pp, G[d], u01(word(r, 2 * h)), u01(word(r, 2 * h + 1)), s);
                 x[idx] = xx;
                 v[idx] = vv;
                 if constexpr (FitAcc<FIT>::kNeedsCos) caux[idx] = cos2pi(xx);
             }
         }
         __syncthreads();
-        // Step 3: fitness, sequential over d per particle.
+        // Steps 3-4: fitness, sequential over d per particle; strict
+        // improvement; the CTA's Step-5 candidate.
+        unsigned long long cand = kKeyNone;
         for (int p = threadIdx.x; p < P; p += blockDim.x) {
             FitAcc<FIT> acc;
             for (int d = 0; d < D; ++d) acc.add_c(d, x[d * P + p], FitAcc<FIT>::kNeedsCos ? caux[d * P + p] : 0.0f);
-            fit[p] = acc.finish(D);
-        }
-        __syncthreads();
-        // Step 4 (strict improvement) and the CTA's Step-5 candidate.
-        unsigned long long cand = kKeyNone;
-        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const float f = acc.finish(D);
             const uint32_t i = base + (uint32_t)p;
-            const float f = fit[p];
             int up = 0;
             if (i < (uint32_t)s.N) {
                 nan |= (f != f);
@@ -153,36 +156,30 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
             imp[p] = up;
         }
         cand = warp_min_u64(cand);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cand;
+        if (lane == 0) red[warp] = cand;
         __syncthreads();
-        for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
-            const int p = e % P;
-            if (imp[p]) pb[e] = x[e];
-        }
-        if (threadIdx.x < 32) {
-            unsigned long long c2 = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : kKeyNone;
-            c2 = warp_min_u64(c2);
-            if (threadIdx.x == 0) red[0] = c2;
-        }
-        __syncthreads();
-        cand = red[0];
-        // Push the candidate into slot [k & 1][rank] of every CTA of the cluster.
+        // Warp 0 pushes the CTA's candidate into slot [k & 1][rank] of every
+        // CTA of the cluster: key from lane r to CTA r, then the position.
         const int par = k & 1;
         const size_t my_slot = ((size_t)par * C + rank) * sb;
-        if (threadIdx.x < C) {
-            unsigned char* remote = cluster.map_shared_rank(slots, threadIdx.x);
-            *reinterpret_cast<unsigned long long*>(remote + my_slot) = cand;
-        }
-        if (cand != kKeyNone) {
-            const int pc = (int)((uint32_t)(cand & 0xFFFFFFFFull) - base);
-            for (int e = threadIdx.x; e < C * D; e += blockDim.x) {
-                const int r = e / D, d = e - r * D;
-                unsigned char* remote = cluster.map_shared_rank(slots, r);
-                reinterpret_cast<float*>(remote + my_slot + 8)[d] = x[d * P + pc];
+        if (warp == 0) {
+            unsigned long long c2 = lane < (int)(blockDim.x >> 5) ? red[lane] : kKeyNone;
+            c2 = warp_min_u64(c2);
+            if (lane < C) {
+                unsigned char* remote = cluster.map_shared_rank(slots, lane);
+                *reinterpret_cast<unsigned long long*>(remote + my_slot) = c2;
+            }
+            if (c2 != kKeyNone) {
+                const int pc = (int)((uint32_t)(c2 & 0xFFFFFFFFull) - base);
+                for (int e = lane; e < C * D; e += 32) {
+                    const int r = e / D, d = e - r * D;
+                    unsigned char* remote = cluster.map_shared_rank(slots, r);
+                    reinterpret_cast<float*>(remote + my_slot + 8)[d] = x[d * P + pc];
+                }
             }
         }
         cluster.sync();
-        // Step 5: every CTA reduces the same slots in rank order.
+        // Step 5: every thread reduces the same slots in rank order.
         unsigned long long best = K;
         int win = -1;
         for (int r = 0; r < C; ++r) {
@@ -196,18 +193,18 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
             const float* row = reinterpret_cast<const float*>(slots + ((size_t)par * C + win) * sb + 8);
             for (int d = threadIdx.x; d < D; d += blockDim.x) G[d] = row[d];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_K = best;
+        K = best;
         __syncthreads();
     }
 
-    // Write the state back so that every other mode and the host see it.
+    // Write the state back so that every other mode and the host see it
+    // (pending pbest rows included).
     for (int e = threadIdx.x; e < P * D; e += blockDim.x) {
         const int d = e / P, p = e - d * P;
         const size_t g = (size_t)d * Np + base + p;
         s.x[g] = x[e];
         s.v[g] = v[e];
-        s.pb[g] = pb[e];
+        s.pb[g] = imp[p] ? x[e] : pb[e];
     }
     for (int p = threadIdx.x; p < P; p += blockDim.x) s.pf[base + p] = pf[p];
     if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
@@ -216,8 +213,8 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
         const int cur = (int)(t_end & 1u);
         for (int d = threadIdx.x; d < D; d += blockDim.x) s.G[(size_t)cur * D + d] = G[d];
         if (threadIdx.x == 0) {
-            s.gkey[0] = s_K;
-            s.gkey[1] = s_K;
+            s.gkey[0] = K;
+            s.gkey[1] = K;
             *s.t_dev = t_end;
         }
     }
@@ -234,7 +231,7 @@ int max_optin_smem() {
 
 // The cluster can be scheduled: the device reports room for at least one.
 bool cluster_schedulable(int C, size_t smem) {
-    auto kernel = onchip_kernel<kSphere>;
+    auto kernel = onchip_kernel<kSphere, false>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return false;
     if (C > 8 && cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
@@ -282,12 +279,12 @@ bool onchip_fits(int N, int D, int* cluster_out, int* per_cta_out) {
 }
 
 namespace {
-template <int FIT>
+template <int FIT, bool FAST>
 cudaError_t launch_onchip_t(const SwarmDev& s, int iters, cudaStream_t st) {
     int C = 0, P = 0;
     if (!onchip_fits(s.N, s.D, &C, &P)) return cudaErrorInvalidConfiguration;
     const OnchipLayout L = onchip_layout(s.Np, s.D, C);
-    auto kernel = onchip_kernel<FIT>;
+    auto kernel = onchip_kernel<FIT, FAST>;
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     if (e != cudaSuccess) return e;
     if (C > 8) {
@@ -310,15 +307,24 @@ cudaError_t launch_onchip_t(const SwarmDev& s, int iters, cudaStream_t st) {
 }
 }  // namespace
 
-cudaError_t launch_onchip(const SwarmDev& s, int fid, int iters, cudaStream_t st) {
+namespace {
+template <bool FAST>
+cudaError_t launch_onchip_f(const SwarmDev& s, int fid, int iters, cudaStream_t st) {
     switch (fid) {
-        case kSphere: return launch_onchip_t<kSphere>(s, iters, st);
-        case kRastrigin: return launch_onchip_t<kRastrigin>(s, iters, st);
-        case kAckley: return launch_onchip_t<kAckley>(s, iters, st);
-        case kRosenbrock: return launch_onchip_t<kRosenbrock>(s, iters, st);
-        case kCubicMax: return launch_onchip_t<kCubicMax>(s, iters, st);
+        case kSphere: return launch_onchip_t<kSphere, FAST>(s, iters, st);
+        case kRastrigin: return launch_onchip_t<kRastrigin, FAST>(s, iters, st);
+        case kAckley: return launch_onchip_t<kAckley, FAST>(s, iters, st);
+        case kRosenbrock: return launch_onchip_t<kRosenbrock, FAST>(s, iters, st);
+        case kCubicMax: return launch_onchip_t<kCubicMax, FAST>(s, iters, st);
         default: return cudaErrorInvalidValue;
     }
+}
+}  // namespace
+
+cudaError_t launch_onchip(const SwarmDev& s, int fid, int iters, cudaStream_t st) {
+    // the fast path (fused c r, min/max clamps) wherever it gives the same bits
+    if (s.fast_cr && s.fast_clamp) return launch_onchip_f<true>(s, fid, iters, st);
+    return launch_onchip_f<false>(s, fid, iters, st);
 }
 
 }  // namespace cupso

@@ -105,13 +105,17 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
     __syncthreads();
 
     const int npairs = (D + 1) / 2;
+    // (pair, particle) items e = g2 * P + p, walked with a stride of the block
+    // without a division per item
+    const int g2_first = (int)threadIdx.x / P, p_first = (int)threadIdx.x - g2_first * P;
+    const int g2_step = (int)blockDim.x / P, p_step = (int)blockDim.x - g2_step * P;
     bool nan = false;
     for (int k = 0; k < iters; ++k) {
         const uint32_t t = t_prev + 1u + (uint32_t)k;
         // Step 2 (Eq. 1, Eq. 2): one Philox call per (particle, dimension pair).
+        int g2 = g2_first, p = p_first;
 #pragma unroll 2
-        for (int e = threadIdx.x; e < P * npairs; e += blockDim.x) {
-            const int g2 = e / P, p = e - g2 * P;
+        for (; g2 < npairs;) {
             const uint4 r = philox4x32_10(make_uint4((uint32_t)g2, base + (uint32_t)p, t, s.swarm), s.key0, s.key1);
             const bool lazy = imp[p] != 0;
 #pragma unroll
@@ -132,6 +136,12 @@ __global__ void __launch_bounds__(kOnchipThreads) onchip_kernel(const __grid_con
                 x[idx] = xx;
                 v[idx] = vv;
                 if constexpr (FitAcc<FIT>::kNeedsCos) caux[idx] = cos2pi(xx);
+            }
+            p += p_step;
+            g2 += g2_step;
+            if (p >= P) {
+                p -= P;
+                ++g2;
             }
         }
         __syncthreads();

@@ -244,6 +244,33 @@ def test_persistent_bit_exact_fp64(P, N, D):
     assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
 
 
+@pytest.mark.parametrize("N", [1, 127, 1000, 8192])
+def test_persistent_restart_from_earlier_iteration(P, N):
+    """The persistent kernel across launches: a run that goes back to an
+    earlier iteration count (set_state) and one that switches to another mode
+    and back must still follow the oracle (one dimension, the paper's 1D
+    shapes)."""
+    fid = 4
+    kw = _paper_kw()
+    with gpu64(P, fid, N, 1, 31, "persistent", **kw) as s:
+        s.step(6)
+        st = s.state()
+        s.set_state(st["pos"], st["v"], st["pbest_pos"], st["pbest_fit"], 4)   # iterations 5, 6 again
+        s.step(3)
+        s.set_mode("sync")
+        s.step(2)
+        s.set_mode("persistent")
+        s.step(4)
+        st2 = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = ora64(fid, N, 1, 31, **kw).init().step_sync(6)
+    ref.set_state(ref.pos.copy(), ref.v.copy(), ref.pbest_pos.copy(), ref.pbest_fit.copy(), 4)
+    ref.step_sync(9)
+    assert rc == P.CUPSO_OK and st2["t"] == 13
+    assert_state64(st2, ref)
+    assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
+
+
 def test_fp64_handle_rejections(P):
     with gpu64(P, 0, 300, 2, 1) as s:
         assert s.info()["mode"] == P.CUPSO_MODE_ONCHIP            # AUTO: the swarm fits one CTA

@@ -567,13 +567,6 @@ int ensure_pinned(cupso_swarm* h, size_t bytes) {
     return CUPSO_OK;
 }
 
-int read_status(cupso_swarm* h, unsigned* st) {
-    CUPSO_CUDA(cudaMemcpyAsync(st, h->dev.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream),
-               "cudaMemcpyAsync");
-    CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
-    return CUPSO_OK;
-}
-
 int status_code(unsigned st) {
     if (st & kStatusBadArg) return CUPSO_ERR_CUDA;   // a device-side bound check dropped work
     if (st & kStatusTimeout) return CUPSO_ERR_DEVICE_TIMEOUT;

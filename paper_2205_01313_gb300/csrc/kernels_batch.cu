@@ -189,17 +189,23 @@ __device__ __forceinline__ void run_unit_t(const BatchDev& b, unsigned* work, fl
     }
     if (fl_new) st4(w.pf + i0, PF);
     if (fl_new != fl) *reinterpret_cast<unsigned int*>(w.pflag + i0) = fl_new;
+    const bool lane_cand = best < K;
     best = warp_min_u64(best);
     const bool any_nan = __any_sync(0xFFFFFFFFu, nan);
     // Publish, then count the unit; the warp that completes the swarm gathers
-    // its gbest. Every lane's stores are made visible before lane 0 counts.
-    __threadfence();
+    // its gbest. The gather reads only the winner's row and improvement flag,
+    // and the winner was a candidate below K in its unit, so only a lane that
+    // holds such a candidate makes its stores visible before lane 0 counts
+    // (a fence per unit in every lane stalled each warp on its own stores).
+    if (lane_cand) __threadfence();
     __syncwarp();
     int last = 0;
     if (lane_id == 0) {
-        if (best < K) atomicMin(w.gkey + nxt, best);
+        if (best < K) {
+            atomicMin(w.gkey + nxt, best);
+            __threadfence();
+        }
         if (any_nan) atomicOr(w.status, kStatusNaN);
-        __threadfence();
         last = atomicAdd(w.done, 1u) == w.nunits - 1u;
         if (last) __threadfence();
     }

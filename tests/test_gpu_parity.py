@@ -389,6 +389,24 @@ def test_batched_solve_wide_swarm_matches_oracle(P, monkeypatch):
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
 
 
+def test_batched_solve_nan_swarm_status(P):
+    """A swarm whose fitness overflows to NaN (the cubic at +-1e30) gets the NaN
+    status in its own result, the batch returns it as the first failure, the
+    other swarms stay CUPSO_OK, and every swarm still equals its oracle run
+    (NaN ranks last)."""
+    probs = _mixed_batch(4, 23, (100, 600), (3, 12))
+    probs.append(dict(D=2, N=300, bounds=(-1e30, 1e30, 1.0), w=W, c1=C12, c2=C12, fitness_id=4, seed=5,
+                      swarm_id=40))
+    rc, res = P.cupso_solve_batch(probs, 6)
+    assert rc == P.CUPSO_ERR_NAN
+    for k, p in enumerate(probs):
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"],
+                           bounds=p["bounds"]).init().step_sync(6)
+        assert res[k]["status"] == (P.CUPSO_ERR_NAN if k == len(probs) - 1 else P.CUPSO_OK), k
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
 def test_batched_kernels_interchange_with_lazy_pbest(P, monkeypatch):
     """The tuner may switch kernels between iterations of one solve; the
     streaming kernel leaves pbest rows pending (lazy write-back) and the tiled

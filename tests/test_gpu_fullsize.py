@@ -64,3 +64,28 @@ def test_rastrigin_65536x128_sampled(P):
     with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed, mode="sync") as s:
         s.step(2)
         _check_step(P, s, fid, N, D, seed, samples)
+
+
+def test_batch512_full_solve_sampled(P):
+    """The benchmark's 512-swarm batch, 500 iterations, in the launch configuration
+    it times (tuned kernel, graph-captured iterations): the swarms small enough
+    for the oracle to replay whole (about 3 million particle-dimension updates
+    each) must equal their oracle runs bit for bit, and every swarm's result
+    must be a valid gbest (finite, within its bounds)."""
+    from paper_2205_01313_gb300 import workloads as Wl
+    probs = Wl.batch_problems(512)
+    iters = 500
+    rc, res = P.cupso_solve_batch(probs, iters)
+    assert rc == P.CUPSO_OK
+    for p, r in zip(probs, res):
+        lo, hi, _ = p["bounds"]
+        assert r["status"] == P.CUPSO_OK and np.isfinite(r["fit"])
+        assert 0 <= r["idx"] < p["N"]
+        assert np.all((r["pos"] >= np.float32(lo)) & (r["pos"] <= np.float32(hi)))
+    small = sorted(range(len(probs)), key=lambda k: probs[k]["N"] * probs[k]["D"])[:6]
+    for k in small:
+        p = probs[k]
+        ref = oracle_swarm(p["fitness_id"], p["N"], p["D"], p["seed"], swarm=p["swarm_id"],
+                           bounds=p["bounds"]).init().step_sync(iters)
+        assert res[k]["idx"] == ref.gbest_idx, k
+        assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k

@@ -89,3 +89,47 @@ def test_batch512_full_solve_sampled(P):
                            bounds=p["bounds"]).init().step_sync(iters)
         assert res[k]["idx"] == ref.gbest_idx, k
         assert same_bits(res[k]["fit"], ref.gbest_fit) and same_bits(res[k]["pos"], ref.gbest_pos), k
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_lsq_8192x1024_full_size(P, precision):
+    """The benchmark's least-squares swarm (N = 8192, D = 1024, M = 4096) in the
+    launch configuration it times (graph-captured iterations): gbest's FP64
+    fitness never increases and equals ||A g - b||^2 recomputed on the host in
+    FP64; sampled particles' pbest_fit equal the tensor-core fitness of their
+    pbest_pos (cupso_lsq_eval); every position stays within the bounds."""
+    import torch
+    from paper_2205_01313_gb300 import workloads as Wl
+    cfg = Wl.lsq_config()
+    N, D, M = cfg["N"], cfg["D"], cfg["M"]
+    A, b, _ = Wl.lsq_problem(M, D, seed=cfg["seed"])
+    dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    A64, b64 = A.astype(np.float64), b.astype(np.float64)
+    lo, hi, vmax = cfg["bounds"]
+    with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"]) as s:
+        s.set_lsq(dA.data_ptr(), db.data_ptr(), M, precision)
+        prev = s.gbest_f64()
+        for _ in range(2):
+            s.step(16)
+            g64 = s.gbest_f64()
+            rc, fit, idx, pos = s.gbest()
+            assert rc == P.CUPSO_OK and g64 <= prev
+            r = A64 @ pos.astype(np.float64) - b64
+            exact = float(r @ r)
+            assert abs(g64 - exact) <= 1e-9 * exact
+            prev = g64
+        st = s.state()
+    assert np.all((st["pos"] >= np.float32(lo)) & (st["pos"] <= np.float32(hi)))
+    assert np.all(np.abs(st["v"]) <= np.float32(vmax))
+    rng = np.random.default_rng(3)
+    sample = rng.choice(N, 64, replace=False)
+    X = st["pbest_pos"][sample]
+    if precision == "fp8":
+        X = np.vstack([X, np.full((1, D), max(abs(lo), abs(hi)), np.float32)])   # the swarm's FP8 scale
+    dX = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    f = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, dX.data_ptr(), X.shape[0], P.LSQ_PRECISIONS[precision],
+                     f.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = f.cpu().numpy()[:len(sample)]
+    np.testing.assert_array_equal(st["pbest_fit"][sample].view(np.uint32), got.view(np.uint32))

@@ -133,3 +133,20 @@ def test_lsq_8192x1024_full_size(P, precision):
     torch.cuda.synchronize()
     got = f.cpu().numpy()[:len(sample)]
     np.testing.assert_array_equal(st["pbest_fit"][sample].view(np.uint32), got.view(np.uint32))
+
+
+@pytest.mark.parametrize("mode", ["onchip", "sync", "tree"])
+def test_sphere_1024x32_full_run(P, mode):
+    """The sphere workload whole: 1024 particles x 32 dimensions, 1000 iterations
+    in one cupso_step call (on-chip: a single launch of the cluster kernel); the
+    final state equals the oracle's full run bit for bit."""
+    from tests.gpu_common import assert_state_equal
+    fid, N, D, T, seed = 0, 1024, 32, 1000, 1
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed, mode=mode) as s:
+        s.step(T)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, seed).init().step_sync(T)
+    assert rc == P.CUPSO_OK and st["t"] == T
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)

@@ -150,3 +150,30 @@ def test_sphere_1024x32_full_run(P, mode):
     assert rc == P.CUPSO_OK and st["t"] == T
     assert_state_equal(st, ref)
     assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+def test_rastrigin_65536x128_async_invariants(P):
+    """ASYNC at the benchmark's Rastrigin size (persistent CTAs, no grid barrier):
+    after each run, gbest is the lowest-index argmin of pbest_fit and equals its
+    pbest_pos, sampled pbest_fit equal the oracle's fitness of their pbest_pos,
+    pbest_fit never increases, and every position and velocity is in bounds."""
+    from oracle import oracle as O
+    fid, N, D, seed = 1, 65536, 128, 1
+    lo, hi, vmax = BOUNDS[fid]
+    rng = np.random.default_rng(4)
+    sample = rng.choice(N, 100, replace=False)
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed, mode="async") as s:
+        prev = s.state()
+        for _ in range(2):
+            s.step(100)
+            st = s.state()
+            rc, fit, idx, pos = s.gbest()
+            assert rc == P.CUPSO_OK
+            assert np.all(st["pbest_fit"] <= prev["pbest_fit"])
+            g = int(np.lexsort((np.arange(N), st["pbest_fit"]))[0])
+            assert idx == g and same_bits(fit, st["pbest_fit"][g]) and same_bits(pos, st["pbest_pos"][g])
+            for i in sample:
+                assert same_bits(np.float32(O.fitness(fid, st["pbest_pos"][i])), st["pbest_fit"][i]), i
+            assert np.all((st["pos"] >= np.float32(lo)) & (st["pos"] <= np.float32(hi)))
+            assert np.all(np.abs(st["v"]) <= np.float32(vmax))
+            prev = st

@@ -177,3 +177,32 @@ def test_rastrigin_65536x128_async_invariants(P):
             assert np.all((st["pos"] >= np.float32(lo)) & (st["pos"] <= np.float32(hi)))
             assert np.all(np.abs(st["v"]) <= np.float32(vmax))
             prev = st
+
+
+def test_paper_cubic_131072x120_fp64_sampled(P):
+    """The paper's largest 120D shape in its own precision (Eq. 3 maximised,
+    w = 1, c1 = c2 = 2, FP64; the tiled FP64 SYNC step): one step checked on
+    sampled particles against the FP64 oracle's single-particle step from the
+    state before it, gbest by brute force over all pbest."""
+    from oracle import oracle as O
+    fid, N, D, seed = 4, 131072, 120, 1
+    lo, hi, vmax = -100.0, 100.0, 20.0
+    with P.Swarm(D, N, (lo, hi, vmax), 1.0, 2.0, 2.0, fid, seed, mode="sync", dtype="f64") as s:
+        s.step(3)
+        before = s.state()
+        _, _, _, gpos = s.gbest()
+        s.step(1)
+        after = s.state()
+        rc, fit, idx, pos = s.gbest()
+    assert rc == P.CUPSO_OK and after["t"] == before["t"] + 1
+    ref = O.Swarm64(N, D, lo, hi, vmax, 1.0, 2.0, 2.0, fid, seed)
+    rng = np.random.default_rng(5)
+    for i in np.concatenate([[0, N - 1], rng.integers(0, N, 60)]):
+        x, v, pb, pf, _ = ref.move_one(after["t"], int(i), before["pos"][i], before["v"][i], before["pbest_pos"][i],
+                                       before["pbest_fit"][i], gpos)
+        for got, want in ((after["pos"][i], x), (after["v"][i], v), (after["pbest_pos"][i], pb)):
+            assert np.array_equal(np.asarray(got, np.float64).view(np.uint64), np.asarray(want, np.float64).view(np.uint64)), i
+        assert np.float64(after["pbest_fit"][i]).view(np.uint64) == np.float64(pf).view(np.uint64), i
+    assert np.all((after["pos"] >= lo) & (after["pos"] <= hi)) and np.all(np.abs(after["v"]) <= vmax)
+    g = int(np.lexsort((np.arange(N), after["pbest_fit"]))[0])
+    assert idx == g and fit == after["pbest_fit"][g] and np.array_equal(pos, after["pbest_pos"][g])

@@ -425,6 +425,17 @@ def run_batch(a):
         "alone_vs_batched_mismatches": mism,
         "clocks": clk,
     }
+    # The step kernel against HBM: compulsory bytes of one iteration of all
+    # swarms (20 B per padded particle-dimension + 8 B per padded particle:
+    # pbest_fit read and written) over the solve's time per iteration (set-up,
+    # Step 1 and the host results included, so a lower bound).
+    padded = [((p["N"] + 127) // 128 * 128, p["D"]) for p in probs]
+    alg = sum(20 * n * d + 8 * n for n, d in padded)
+    peak, src = hbm_peak()
+    achieved = alg / (batched_s / iters) / 1e9
+    out["roofline"] = {"bound": "hbm", "kernel": "batch_step_kernel", "achieved": achieved, "peak": peak,
+                       "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                       "algorithmic_bytes_per_iteration": alg, "peak_source": src}
     print(json.dumps(out), flush=True)
 
 

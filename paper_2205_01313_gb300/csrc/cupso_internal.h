@@ -61,8 +61,8 @@ cudaError_t lsq_prepare();
 cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
                         void* dst, cudaStream_t st);
 bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp);
-// part[mt][i] (mt < lsq_tc_partials) = sum of squared residuals of particle i
-// over residual rows 256 mt .. 256 mt + 255.
+// part[k][i] (k < lsq_tc_partials) = sum of squared residuals of particle i
+// over residual rows 128 k .. 128 k + 127.
 cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st);
 int lsq_tc_partials(const LsqTcPlan& p);
@@ -76,7 +76,7 @@ struct LsqTcState {
     void* Xq = nullptr;              // [Np][Kp] operand copy of the positions
     float* bpad = nullptr;           // [Mp]
     float* inv = nullptr;            // [Mp] 1 / (sx * row scale of A) (FP8)
-    float* part = nullptr;           // [Mp / 256][Np] partial sums
+    float* part = nullptr;           // [Mp / 128][Np] partial sums
     unsigned int* status = nullptr;
     LsqTcPlan plan;
 };

@@ -93,7 +93,7 @@ int cupso::lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, i
     st->sx = fp8 ? sx : 1.0f;
     const size_t esz = fp8 ? 1 : 2;
     const size_t bytes_A = (size_t)st->Mp * st->Kp * esz, bytes_X = (size_t)Np * st->Kp * esz;
-    const size_t nparts = (size_t)st->Mp / 256;   // one partial sum per residual-row tile
+    const size_t nparts = (size_t)st->Mp / 128;   // one partial sum per 128 residual rows
     const size_t bytes = up(bytes_A, 256) + up(bytes_X, 256) + up(sizeof(float) * st->Mp, 256) * 2 +
                          up(sizeof(float) * nparts * Np, 256) + up(sizeof(float) * (size_t)M * D, 256) +
                          up(sizeof(float) * M, 256) + 256;

@@ -14,12 +14,17 @@
 //  * lsq_tc_kernel<true>: the same with FP8 e4m3 operands: A scaled per row,
 //    X by one factor from the search bounds; the epilogue undoes the scales.
 //
-// The tensor-core kernel is warp-specialised: warp 0 issues the TMA loads
-// into a 4-stage shared-memory ring, warp 1 owns the tensor memory and issues
-// the MMAs (128 particles x 256 residual rows per accumulator, two
-// accumulators alternating), warps 2-5 drain the accumulators. Every
-// mbarrier wait is bounded in time; on expiry the kernel records a timeout,
-// lets the copies in flight land, frees its tensor memory and returns.
+// The tensor-core kernel runs on pairs of SMs (clusters of two CTAs, MMAs of
+// cta_group::2): a pair computes a tile of 256 particles x 256 residual rows,
+// each CTA staging its own 128 particle rows and half of the 256 residual
+// rows, so an SM takes in 32 KB of operands per 128-byte K step instead of
+// the 48 KB a one-SM 128 x 256 tile needs, and the ring holds 6 stages.
+// Warp-specialised: warp 0 of each CTA issues its TMA loads, warp 1 of the
+// even CTA issues the MMAs (two accumulators alternating), warps 2-9 of both
+// CTAs drain their half of the accumulator, two warps per TMEM lane quarter,
+// each over 128 residual rows, in loads of 32 columns. Every mbarrier wait is
+// bounded in time; on expiry the kernel records a timeout, frees its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -35,13 +40,15 @@ namespace cupso {
 
 namespace {
 
-constexpr int BM = 128;          // particles per tile (MMA M)
-constexpr int BN = 256;          // residual rows per tile (MMA N)
+constexpr int BM = 128;          // particles per CTA (a pair's MMA M = 256)
+constexpr int BN = 256;          // residual rows per tile (MMA N), 128 staged per CTA
+constexpr int BNH = BN / 2;
 constexpr int KB = 128;          // K bytes per stage: one 128-byte swizzle row
-constexpr int STAGES = 4;
-constexpr int kTcThreads = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int STAGES = 6;
+constexpr int kTcThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiWarps = 8;
 constexpr int X_BYTES = BM * KB; // 16 KB
-constexpr int A_BYTES = BN * KB; // 32 KB
+constexpr int A_BYTES = BNH * KB; // 16 KB
 constexpr int STAGE_BYTES = X_BYTES + A_BYTES;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -51,9 +58,6 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -77,11 +81,26 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t bar) {
+// Address of the same shared-memory offset in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Tile copy into this CTA's shared memory, completing on an mbarrier that may
+// sit in either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t cluster_bar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(bar)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+        "%3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(cluster_bar)
         : "memory");
 }
 
@@ -98,10 +117,11 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, A and B K-major, M = 128, N = 256.
-// ab_fmt: BF16 = 1 for kind::f16, E4M3 = 0 for kind::f8f6f4.
+// Instruction descriptor: FP32 accumulator, A and B K-major, M = 256 (the
+// pair), N = 256. ab_fmt: BF16 = 1 for kind::f16, E4M3 = 0 for kind::f8f6f4.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_fmt) {
-    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)((2 * BM) >> 4) << 24);
 }
 
 template <bool FP8>
@@ -109,69 +129,89 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, ui
     if constexpr (FP8) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
     }
 }
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+// Arrives on the barrier at this shared-memory offset in each CTA of `mask`
+// once the MMAs issued so far are complete.
+__device__ __forceinline__ void umma_commit(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
+        : "memory");
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// 32 consecutive FP32 columns of this thread's TMEM lane; the wait is in the
+// same statement, so no register is read before the load has landed.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 }  // namespace
 
-// Per-particle partial fitness of each tile of 128 particles x 256 residual rows:
-//   part[mt][i] = sum over m in tile mt of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
+// Per-particle partial fitness over each block of 128 residual rows:
+//   part[h][i] = sum over m in 128 h .. 128 h + 127 of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
 // X: [Np][Kp] (K-major), A: [Mp][Kp], b: [Mp] (zero-padded rows contribute 0).
-// Persistent: CTA c takes tiles c, c + gridDim.x, ... of the (Np / 128) x
-// (Mp / 256) tiles (residual-row tile fastest), so a grid of one CTA per SM
-// covers every tile in waves of equal work.
+// Launched in clusters of two CTAs. Pair c (of gridDim.x / 2) takes tiles
+// c, c + gridDim.x / 2, ... of the ceil(Np / 256) x (Mp / 256) tiles
+// (residual-row tile fastest). CTA r of the pair stages particle rows
+// 256 pb + 128 r .. + 127 and residual rows 256 mt + 128 r .. + 127; the MMA
+// (issued by CTA 0) leaves particle row 128 r + lane of the tile, against all
+// 256 residual rows, in lane `lane` of CTA r's tensor memory.
 template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     lsq_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
                   const float* __restrict__ b, const float* __restrict__ inv_scale, int Mp, int KT, int Np,
                   float* __restrict__ part, unsigned int* status, long long limit_ns) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned base for the swizzled tiles
+    // 1024-byte aligned base for the swizzled tiles (the same offset in both CTAs)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
     unsigned char* base_ptr = smem_raw + (base - raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(base_ptr + STAGES * STAGE_BYTES);
-    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]; then the TMEM address slot
+    // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2], drain; then the TMEM address slot.
+    // full, tempty and drain are used in CTA 0 only; empty and tfull in both.
     const uint32_t bar0 = base + STAGES * STAGE_BYTES;
     auto full_bar = [&](int s) { return bar0 + 8u * (uint32_t)s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (uint32_t)(STAGES + s); };
     auto tfull_bar = [&](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + a); };
     auto tempty_bar = [&](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + 2 + a); };
-    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * STAGES + 5);
     const uint32_t drain_bar = bar0 + 8u * (uint32_t)(2 * STAGES + 4);
+    volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(bars + 2 * STAGES + 5);
     __shared__ volatile int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t rank, pair, npairs;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(pair));
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(npairs));
     const int mtiles = Mp / BN;
-    const int ntiles = (Np / BM) * mtiles;
-    const int nt = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
-    // the jj-th tile of this CTA: residual-row tile and particle block
-    auto tile_mt = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) % mtiles; };
-    auto tile_pb = [&](int jj) { return ((int)blockIdx.x + jj * (int)gridDim.x) / mtiles; };
+    const int ntiles = ((Np + 2 * BM - 1) / (2 * BM)) * mtiles;
+    const int nt = (int)pair < ntiles ? (ntiles - (int)pair + (int)npairs - 1) / (int)npairs : 0;
+    // the jj-th tile of this pair: residual-row tile and 256-particle block
+    auto tile_mt = [&](int jj) { return ((int)pair + jj * (int)npairs) % mtiles; };
+    auto tile_pb = [&](int jj) { return ((int)pair + jj * (int)npairs) / mtiles; };
 
     if (threadIdx.x == 0) {
         s_fail = 0;
@@ -181,29 +221,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(tfull_bar(a), 1);
-            mbar_init(tempty_bar(a), 4);
+            mbar_init(tempty_bar(a), 2 * kEpiWarps);   // the epilogue warps of both CTAs
         }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) {
-        // 512 columns: two 128 x 256 FP32 accumulators
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+        // 512 columns in each CTA of the pair: two 128-lane x 256 FP32 accumulators
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32((const void*)tmem_slot)),
                      "r"(512)
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();   // barriers of both CTAs initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int total = nt * KT;   // (tile, k-stage) steps
     int issued = 0;              // TMA stages issued (producer)
+    const uint16_t both = 0x3;
 
     if (warp == 0) {
         if (lane == 0) {
+            const int esz = FP8 ? 1 : 2;
             for (int step = 0; step < total; ++step) {
                 const int s = step % STAGES, f = step / STAGES;
                 if (f > 0 && !mbar_wait(empty_bar(s), (uint32_t)((f - 1) & 1), limit_ns)) {
@@ -213,20 +255,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 if (s_fail) break;
                 const int jj = step / KT, kk = step % KT;
-                mbar_expect_tx(full_bar(s), (uint32_t)STAGE_BYTES);
+                // CTA 0's barrier counts the bytes of both CTAs' copies
+                if (rank == 0) mbar_expect_tx(full_bar(s), (uint32_t)(2 * STAGE_BYTES));
+                const uint32_t fb = cluster_addr(full_bar(s), 0);
                 const uint32_t xs = base + (uint32_t)(s * STAGE_BYTES);
-                tma_load_2d(xs, &tmX, kk * KB / (FP8 ? 1 : 2), tile_pb(jj) * BM, full_bar(s));
-                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / (FP8 ? 1 : 2), tile_mt(jj) * BN, full_bar(s));
+                tma_load_2d(xs, &tmX, kk * KB / esz, tile_pb(jj) * (2 * BM) + (int)rank * BM, fb);
+                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / esz, tile_mt(jj) * BN + (int)rank * BNH, fb);
                 ++issued;
             }
-            // let every issued copy land before shared memory can go away
-            for (int step = 0; step < issued; ++step) {
-                if (step + STAGES < issued) continue;   // older stages were consumed already
-                mbar_wait(full_bar(step % STAGES), (uint32_t)((step / STAGES) & 1), limit_ns);
-            }
+            // CTA 0's barriers count both CTAs' copies: let the last ones land
+            // (already consumed, so immediate, unless the pipeline stopped early)
+            if (rank == 0)
+                for (int step = issued - STAGES > 0 ? issued - STAGES : 0; step < issued; ++step)
+                    mbar_wait(full_bar(step % STAGES), (uint32_t)((step / STAGES) & 1), limit_ns);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && rank == 0) {
             constexpr uint32_t idesc = make_idesc(FP8 ? 0u : 1u);
             constexpr uint32_t kstep_bytes = 32;   // 16 bf16 or 32 fp8 per MMA
             int step = 0;
@@ -254,61 +298,78 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint64_t bd = desc_sw128(xs + X_BYTES + k4 * kstep_bytes);
                         umma<FP8>(d_tmem, ad, bd, idesc, (kk > 0 || k4 > 0) ? 1u : 0u);
                     }
-                    umma_commit(empty_bar(s));   // the stage is free once these MMAs are done
+                    umma_commit(empty_bar(s), both);   // stage s is free in both CTAs once these are done
                 }
                 if (s_fail) break;
-                umma_commit(tfull_bar(a));       // accumulator a holds tile jj
+                umma_commit(tfull_bar(a), both);       // accumulator a holds tile jj in both CTAs
             }
             // every MMA issued has finished before tensor memory is released
-            umma_commit(drain_bar);
+            umma_commit(drain_bar, 0x1);
             if (!mbar_wait(drain_bar, 0u, limit_ns)) atomicOr(status, kStatusTimeout);
         }
         __syncwarp();
     } else {
-        // epilogue: thread = one particle row of the tile
+        // epilogue: thread = one particle row of this CTA's half of the tile,
+        // against residual rows 128 h .. 128 h + 127 of the tile
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;
         const int row = q * 32 + lane;
         bool ok = true;
         for (int jj = 0; jj < nt; ++jj) {
             const int a = jj & 1, u = jj >> 1;
             const int mt = tile_mt(jj);
-            const int i = tile_pb(jj) * BM + row;
+            const int i = tile_pb(jj) * (2 * BM) + (int)rank * BM + row;
+            const size_t slot = (size_t)(2 * mt + h) * Np + i;
             // warp-uniform outcome: tcgen05.ld below needs the whole warp
             if (!__all_sync(0xFFFFFFFFu, mbar_wait(tfull_bar(a), (uint32_t)(u & 1), limit_ns))) {
                 ok = false;
-                part[(size_t)mt * Np + i] = __int_as_float(0x7fc00000);
+                if (i < Np) part[slot] = __int_as_float(0x7fc00000);
                 break;
             }
             tc_fence_after();
-            const int m0 = mt * BN;
+            const int m0 = mt * BN + h * 128;
             float sum = 0.0f;
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN);
-            for (int c = 0; c < BN; c += 16) {
-                float v[16];
-                tmem_ld16(taddr + (uint32_t)c, v);
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + h * 128);
+#pragma unroll 1
+            for (int c = 0; c < 128; c += 32) {
+                // b (and the FP8 scales) of these 32 rows, requested before the TMEM load
+                float bb[32], sc[32];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int m = m0 + c + e;
-                    const float val = FP8 ? __fmul_rn(v[e], __ldg(inv_scale + m)) : v[e];
-                    const float r = __fsub_rn(val, __ldg(b + m));
+                for (int e = 0; e < 32; e += 4) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(b + m0 + c + e));
+                    bb[e] = t.x; bb[e + 1] = t.y; bb[e + 2] = t.z; bb[e + 3] = t.w;
+                    if constexpr (FP8) {
+                        const float4 z = __ldg(reinterpret_cast<const float4*>(inv_scale + m0 + c + e));
+                        sc[e] = z.x; sc[e + 1] = z.y; sc[e + 2] = z.z; sc[e + 3] = z.w;
+                    }
+                }
+                float v[32];
+                tmem_ld32(taddr + (uint32_t)c, v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const float val = FP8 ? __fmul_rn(v[e], sc[e]) : v[e];
+                    const float r = __fsub_rn(val, bb[e]);
                     sum = __fmaf_rn(r, r, sum);
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty_bar(a));
-            part[(size_t)mt * Np + i] = sum;
+            if (lane == 0) mbar_arrive_cluster(cluster_addr(tempty_bar(a), 0));
+            if (i < Np) part[slot] = sum;
         }
         if (!ok) {
             if (lane == 0) atomicOr(status, kStatusTimeout);
             s_fail = 1;
         }
     }
+    // CTA 0's MMAs read both CTAs' shared memory and the epilogues arrive on
+    // CTA 0's barriers: neither CTA leaves or frees tensor memory before both
+    // are done
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
@@ -493,27 +554,58 @@ bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int
         cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || p->num_sms < 1)
         return false;
     if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmX), Xq, fp8, Np, Kp, BM)) return false;
-    if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmA), Aq, fp8, Mp, Kp, BN)) return false;
+    if (!make_map(reinterpret_cast<CUtensorMap*>(p->tmA), Aq, fp8, Mp, Kp, BNH)) return false;
+    // The persistent grid: as many CTA pairs as can be resident at once (a GPC
+    // with an odd number of free SMs leaves one out), never more than SMs / 2.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (p->num_sms / 2));
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = tc_smem();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, fp8 ? (const void*)lsq_tc_kernel<true> : (const void*)lsq_tc_kernel<false>,
+                                       &cfg) != cudaSuccess ||
+        clusters < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    p->num_sms = 2 * std::min(clusters, p->num_sms / 2);
     return true;
 }
 
 cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st) {
-    const int ntiles = (p.Np / BM) * (p.Mp / BN);
-    const int grid = std::max(1, std::min(ntiles, p.num_sms));
+    const int ntiles = ((p.Np + 2 * BM - 1) / (2 * BM)) * (p.Mp / BN);
+    const int pairs = std::max(1, std::min(ntiles, p.num_sms / 2));   // num_sms: the resident pairs x 2
     const int KT = p.Kp * (p.fp8 ? 1 : 2) / KB;
     const CUtensorMap& tx = *reinterpret_cast<const CUtensorMap*>(p.tmX);
     const CUtensorMap& ta = *reinterpret_cast<const CUtensorMap*>(p.tmA);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = tc_smem();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     if (p.fp8)
-        lsq_tc_kernel<true><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
-                                                                  limit_ns);
-    else
-        lsq_tc_kernel<false><<<grid, kTcThreads, tc_smem(), st>>>(tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
-                                                                   limit_ns);
-    return cudaGetLastError();
+        return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<true>, tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+                                  limit_ns);
+    return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<false>, tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+                              limit_ns);
 }
 
-int lsq_tc_partials(const LsqTcPlan& p) { return p.Mp / BN; }
+int lsq_tc_partials(const LsqTcPlan& p) { return p.Mp / 128; }
 
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
                             cudaStream_t st) {

@@ -47,7 +47,7 @@ def test_lsq_fp32_bit_exact(P, M, D, N):
     np.testing.assert_array_equal(f.view(np.uint32), ref.view(np.uint32))
 
 
-@pytest.mark.parametrize("M,D,N", [(256, 64, 128), (700, 200, 1000), (4096, 1024, 512)])
+@pytest.mark.parametrize("M,D,N", [(256, 64, 128), (700, 200, 1000), (4096, 1024, 512), (1300, 96, 1100)])
 def test_lsq_bf16_tensor_cores(P, M, D, N):
     """f~ from BF16 operands equals the FP64 fitness of the BF16-rounded operands up
     to FP32 accumulation error, and the FP64 fitness of the exact operands within
@@ -66,7 +66,7 @@ def test_lsq_bf16_tensor_cores(P, M, D, N):
     assert np.median(np.abs(f - f64) / f64) < 5e-3
 
 
-@pytest.mark.parametrize("M,D,N", [(256, 128, 128), (700, 300, 1000)])
+@pytest.mark.parametrize("M,D,N", [(256, 128, 128), (700, 300, 1000), (1300, 96, 1100)])
 def test_lsq_fp8_tensor_cores(P, M, D, N):
     A, b, X = _problem(M, D, N, seed=M + 1)
     f = _eval(P, A, b, X, P.CUPSO_LSQ_FP8).astype(np.float64)

@@ -96,11 +96,13 @@ __device__ __forceinline__ void cluster_sync() {
 
 // Tile copy into this CTA's shared memory, completing on an mbarrier that may
 // sit in either CTA of the pair (cluster address).
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t cluster_bar) {
+// `policy` is an L2 cache policy (createpolicy).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, uint32_t cluster_bar,
+                                            uint64_t policy) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
-        "%3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(cluster_bar)
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+        "[%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(cluster_bar), "l"(policy)
         : "memory");
 }
 
@@ -246,6 +248,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             const int esz = FP8 ? 1 : 2;
+            // A is the same in every launch and each tile of X is read by all
+            // residual-row tiles: keep both in L2 ahead of the swarm state
+            // that the move kernel streams between launches
+            uint64_t keep;
+            asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
             for (int step = 0; step < total; ++step) {
                 const int s = step % STAGES, f = step / STAGES;
                 if (f > 0 && !mbar_wait(empty_bar(s), (uint32_t)((f - 1) & 1), limit_ns)) {
@@ -259,8 +266,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (rank == 0) mbar_expect_tx(full_bar(s), (uint32_t)(2 * STAGE_BYTES));
                 const uint32_t fb = cluster_addr(full_bar(s), 0);
                 const uint32_t xs = base + (uint32_t)(s * STAGE_BYTES);
-                tma_load_2d(xs, &tmX, kk * KB / esz, tile_pb(jj) * (2 * BM) + (int)rank * BM, fb);
-                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / esz, tile_mt(jj) * BN + (int)rank * BNH, fb);
+                tma_load_2d(xs, &tmX, kk * KB / esz, tile_pb(jj) * (2 * BM) + (int)rank * BM, fb, keep);
+                tma_load_2d(xs + X_BYTES, &tmA, kk * KB / esz, tile_mt(jj) * BN + (int)rank * BNH, fb, keep);
                 ++issued;
             }
             // CTA 0's barriers count both CTAs' copies: let the last ones land

@@ -964,6 +964,194 @@ __global__ void __launch_bounds__(kPersistThreads) persist64_kernel(const __grid
     }
 }
 
+// ---------------------------------------------------------------------------
+// Resident variant of the persistent FP64 swarm, for swarms of at most one
+// particle per thread: x, v and pbest_pos stay in shared memory ([D][TB]) and
+// pbest_fit in a register for all iterations of the launch, so an iteration
+// touches global memory only for the Step-5 exchange. A block's candidate goes
+// to its slot together with its position (index first, position after, as in
+// Sec. 4.3); after the barrier every block reduces the same slots in the same
+// order, and for D <= kResPos the position travels with the key in that one
+// pass over the slots.
+// ---------------------------------------------------------------------------
+constexpr int kResPos = 4;
+constexpr int kResMaxIters = 1 << 24;   // per launch: (k + 1) * blocks stays below 2^32
+
+__device__ __forceinline__ unsigned int add_release_gpu(unsigned int* p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier number k of a launch that started with the counter at
+// zero: thread 0 of every block adds one arrival, and barrier k is complete
+// once all blocks have arrived k + 1 times. One atomic per block, no reset and
+// no generation word to read first. The arrival releases the block's writes
+// (ordered before it by the block barrier) and the wait acquires the others'.
+// A wait past the limit sets the timeout status and returns false.
+__device__ bool grid_barrier_k(const PaperBufs& b, unsigned int nblocks, int k, long long limit_ns,
+                               unsigned int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int target = (unsigned int)(k + 1) * nblocks;
+        if (add_release_gpu(b.bar_count, 1u) + 1u < target) {
+            const long long deadline = global_ns() + limit_ns;
+            while (ld_acquire_gpu(b.bar_count) < target) {
+                if (global_ns() > deadline) {
+                    ok = 0;
+                    atomicOr(status, kStatusTimeout);
+                    break;
+                }
+            }
+        } else {
+            (void)ld_acquire_gpu(b.bar_count);   // the last arrival acquires too
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__host__ __device__ inline size_t res_slot_bytes(int D) { return (sizeof(PKey) + sizeof(double) * (size_t)D + 15) / 16 * 16; }
+
+template <int FIT>
+__global__ void __launch_bounds__(512) persist64r_kernel(const __grid_constant__ SwarmDev64 s,
+                                                          const __grid_constant__ PaperBufs b, int iters) {
+    extern __shared__ double sm64[];
+    __shared__ PKey red[32];
+    const int TB = (int)blockDim.x, D = s.D, tid = threadIdx.x;
+    double* X = sm64;                       // [D][TB]
+    double* V = X + (size_t)D * TB;
+    double* PB = V + (size_t)D * TB;
+    double* Gsh = PB + (size_t)D * TB;      // [D] the current gbest
+    const unsigned int nblk = gridDim.x;
+    const uint32_t i = blockIdx.x * (uint32_t)TB + (uint32_t)tid;
+    const bool own = i < (uint32_t)s.N;
+    const size_t Np = (size_t)s.Np;
+    const size_t rec = res_slot_bytes(D);
+    unsigned char* slots = reinterpret_cast<unsigned char*>(b.list);
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const int cur0 = (int)(t_prev & 1u);
+    PKey K = Fp64::load_gkey(s, cur0);
+    for (int d = tid; d < D; d += TB) Gsh[d] = s.G[(size_t)cur0 * D + d];
+    double pf = 0.0;
+    if (own) {
+        pf = s.pf[i];
+        for (int d = 0; d < D; ++d) {
+            const size_t g = (size_t)d * Np + i;
+            X[d * TB + tid] = s.x[g];
+            V[d * TB + tid] = s.v[g];
+            PB[d * TB + tid] = s.pb[g];
+        }
+    }
+    __syncthreads();
+    bool nan = false;
+    int done = 0;
+    for (int k = 0; k < iters; ++k) {
+        const uint32_t t = t_prev + 1u + (uint32_t)k;
+        PKey cand = key_none();
+        if (own) {   // Steps 2-4 of this thread's particle
+            FitAcc64<FIT> acc;
+            for (int d = 0; d < D; ++d) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)d, i, t, s.swarm), s.key0, s.key1);
+                const int j = d * TB + tid;
+                double x = X[j], v = V[j];
+                move_one64(x, v, PB[j], Gsh[d], r, s);
+                X[j] = x;
+                V[j] = v;
+                acc.add(d, x);
+            }
+            const double f = acc.finish();
+            nan |= (f != f);
+            if (f < pf) {
+                pf = f;
+                for (int d = 0; d < D; ++d) PB[d * TB + tid] = X[d * TB + tid];
+                const PKey c = Fp64::key(f, i);
+                if (key_less(c, K)) cand = c;
+            }
+        }
+        const PKey best = block_min_key(cand, red);
+        unsigned char* mine = slots + ((size_t)(k & 1) * nblk + blockIdx.x) * rec;
+        if (best.i == kNoIdx) {
+            if (tid == 0) *reinterpret_cast<PKey*>(mine) = key_none();
+        } else if (best.i == i) {   // the candidate's own thread fills the slot
+            double* pos = reinterpret_cast<double*>(mine + sizeof(PKey));
+            for (int d = 0; d < D; ++d) pos[d] = PB[d * TB + tid];
+            *reinterpret_cast<PKey*>(mine) = best;
+        }
+        if (!grid_barrier_k(b, nblk, k, s.wait_limit_ns, s.status)) break;
+        // Step 5: the same reduction over the slots in every block
+        PKey m = K;
+        int mj = -1;
+        double mpos[kResPos];
+        for (unsigned int j = tid; j < nblk; j += TB) {
+            const unsigned char* sl = slots + ((size_t)(k & 1) * nblk + j) * rec;
+            const PKey* pk = reinterpret_cast<const PKey*>(sl);
+            PKey c;
+            c.k = __ldcg(&pk->k);
+            c.i = __ldcg(&pk->i);
+            c.pad = 0u;
+            double q[kResPos];
+            if (D <= kResPos) {
+#pragma unroll
+                for (int d = 0; d < kResPos; ++d)
+                    q[d] = d < D ? __ldcg(reinterpret_cast<const double*>(sl + sizeof(PKey)) + d) : 0.0;
+            }
+            if (key_less(c, m)) {
+                m = c;
+                mj = (int)j;
+#pragma unroll
+                for (int d = 0; d < kResPos; ++d) mpos[d] = D <= kResPos ? q[d] : 0.0;
+            }
+        }
+        const PKey nbest = block_min_key(m, red);
+        if (key_less(nbest, K)) {
+            // the thread that read the winning slot brings its position
+            if (mj >= 0 && m.i == nbest.i && m.k == nbest.k) {
+                if (D <= kResPos) {
+#pragma unroll
+                    for (int d = 0; d < kResPos; ++d)
+                        if (d < D) Gsh[d] = mpos[d];
+                } else {
+                    const double* pos =
+                        reinterpret_cast<const double*>(slots + ((size_t)(k & 1) * nblk + mj) * rec + sizeof(PKey));
+                    for (int d = 0; d < D; ++d) Gsh[d] = __ldcg(pos + d);
+                }
+            }
+            K = nbest;
+        }
+        __syncthreads();
+        done = k + 1;
+    }
+    if (own) {
+        s.pf[i] = pf;
+        for (int d = 0; d < D; ++d) {
+            const size_t g = (size_t)d * Np + i;
+            s.x[g] = X[d * TB + tid];
+            s.v[g] = V[d * TB + tid];
+            s.pb[g] = PB[d * TB + tid];
+        }
+    }
+    if (__syncthreads_or(nan) && tid == 0) atomicOr(s.status, kStatusNaN);
+    if (blockIdx.x == 0) {
+        const uint32_t t_end = t_prev + (uint32_t)done;
+        const int out = (int)(t_end & 1u);
+        for (int d = tid; d < D; d += TB) s.G[(size_t)out * D + d] = Gsh[d];
+        if (tid == 0) {
+            Fp64::store_gkey(s, 0, K);
+            Fp64::store_gkey(s, 1, K);
+            *s.t_dev = t_end;
+        }
+    }
+}
+
 #define CUPSO_DISPATCH_FIT32(fid, CALL)            \
     switch (fid) {                                 \
         case kSphere: { constexpr int F = kSphere; CALL; break; }         \
@@ -1095,9 +1283,60 @@ int persist64_grid(int fid, int N, int D, int num_sms) {
     return (int)(want < cap ? want : cap);
 }
 
+namespace {
+
+const void* persist64r_fn(int fid) {
+    switch (fid) {
+        case kSphere: return (const void*)persist64r_kernel<kSphere>;
+        case kRosenbrock: return (const void*)persist64r_kernel<kRosenbrock>;
+        case kCubicMax: return (const void*)persist64r_kernel<kCubicMax>;
+        default: return nullptr;
+    }
+}
+
+// Threads per block of the resident variant (one particle each, at most one
+// block per SM, block size from 128 doubling to 512), or 0 where it does not
+// apply: too many particles, state over 48 KB per block, slots beyond the
+// candidate list, or blocks that cannot all be resident.
+int persist64r_block(int fid, int N, int D, int num_sms, unsigned int list_cap) {
+    int tb = 128;
+    while ((N + tb - 1) / tb > num_sms && tb < 512) tb *= 2;
+    const int nblk = (N + tb - 1) / tb;
+    if (nblk > num_sms) return 0;
+    const size_t smem = sizeof(double) * (3 * (size_t)D * tb + (size_t)D);
+    if (smem > 48 * 1024) return 0;
+    if (2 * (size_t)nblk * res_slot_bytes(D) > sizeof(PKey) * (size_t)list_cap) return 0;
+    const void* fn = persist64r_fn(fid);
+    int per_sm = 0;
+    if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tb, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (long long)per_sm * num_sms >= nblk ? tb : 0;
+}
+
+}  // namespace
+
 cudaError_t launch_persist64(const SwarmDev64& s, const PaperBufs& b, int fid, int iters, int num_sms,
                              cudaStream_t st) {
     if (s.D > 4096) return cudaErrorInvalidValue;
+    if (const int tb = persist64r_block(fid, s.N, s.D, num_sms, b.list_cap)) {
+        const int nblk = (s.N + tb - 1) / tb;
+        const size_t smem = sizeof(double) * (3 * (size_t)s.D * tb + (size_t)s.D);
+        for (int left = iters; left > 0;) {
+            // the barrier counter starts every launch at zero
+            cudaError_t me = cudaMemsetAsync(b.bar_count, 0, sizeof(unsigned int), st);
+            if (me != cudaSuccess) return me;
+            int iters_arg = left < kResMaxIters ? left : kResMaxIters;
+            left -= iters_arg;
+            SwarmDev64 s_arg = s;
+            PaperBufs b_arg = b;
+            void* args[] = {&s_arg, &b_arg, &iters_arg};
+            cudaError_t e = cudaLaunchCooperativeKernel(persist64r_fn(fid), dim3(nblk), dim3(tb), args, smem, st);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int grid = persist64_grid(fid, s.N, s.D, num_sms);
     if (2u * (unsigned)grid > b.list_cap) return cudaErrorInvalidConfiguration;
     // a barrier abandoned by a timed-out launch must not leave arrivals behind

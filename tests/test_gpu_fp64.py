@@ -244,6 +244,26 @@ def test_persistent_bit_exact_fp64(P, N, D):
     assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
 
 
+@pytest.mark.parametrize("fid", [0, 3, 4])
+@pytest.mark.parametrize("N,D", [(500, 7), (6000, 2), (60000, 1)])
+def test_persistent_resident_bit_exact_fp64(P, fid, N, D):
+    """Swarms of at most one particle per thread keep their state in shared
+    memory for the whole launch; candidates travel with their positions (read
+    with the key for D <= 4, after the reduction above that). N = 6000 has more
+    blocks (94) than threads per block (64), so a reducing thread reads several
+    slots; N = 60000 takes blocks of 512 threads."""
+    T = 12
+    with gpu64(P, fid, N, D, 29, "persistent") as s:
+        s.step(5)
+        s.step(T - 5)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = ora64(fid, N, D, 29).init().step_sync(T)
+    assert rc == P.CUPSO_OK
+    assert_state64(st, ref)
+    assert idx == ref.gbest_idx and same64(fit, ref.gbest_fit) and same64(pos, ref.gbest_pos)
+
+
 @pytest.mark.parametrize("N", [1, 127, 1000, 8192])
 def test_persistent_restart_from_earlier_iteration(P, N):
     """The persistent kernel across launches: a run that goes back to an

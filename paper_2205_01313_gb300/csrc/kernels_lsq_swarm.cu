@@ -429,8 +429,10 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
 // Rows are taken in pairs (q, D-1-q), whose upper parts hold D-1 entries
 // together, so every warp gets the same work. Block (group, chunk) handles 4
 // candidates (group 4g..4g+3) and the pairs of its chunk:
-// partial[cand][chunk] = its rows' terms (+ bb in chunk 0), pairs in order per
-// warp, warps in a fixed order.
+// partial[cand][chunk] = its rows' terms (+ bb in chunk 0): per warp, each lane
+// sums x_r times its columns of row r over the warp's rows, lanes take the
+// diagonal and linear terms row by row, and one butterfly over the warp adds
+// them; warps in a fixed order.
 __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_constant__ SwarmDev s,
                                                                const float* __restrict__ src,
                                                                const double* __restrict__ Gm,
@@ -455,12 +457,16 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int npairs = (D + 1) / 2;
     const int p0 = chunk * pairs_per_chunk, p1 = min(npairs, p0 + pairs_per_chunk);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};   // lane 0: this warp's rows, in order
+    // off[q]: this lane's share of sum_r x_r sum_{c>r} Gm_rc x_c over the warp's
+    // rows (its columns of each row); reduced over the warp once, at the end
+    double off[4] = {0.0, 0.0, 0.0, 0.0};
+    int nrows = 0;   // rows of this warp, in order
     for (int pr = p0 + warp; pr < p1; pr += 8) {
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
             const int r = side == 0 ? pr : D - 1 - pr;
             if (side == 1 && r == pr) break;   // the middle row of an odd D
+            ++nrows;
             const double* row = Gm + (size_t)r * D;
             double y[4] = {0.0, 0.0, 0.0, 0.0};
             int c = r + 1 + lane;
@@ -481,16 +487,27 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
 #pragma unroll
                 for (int q = 0; q < 4; ++q) y[q] = fma(g, xg[q * D + c], y[q]);
             }
-            const double grr = row[r];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                double v = y[q];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-                const double xr = xg[q * D + r];
-                const double inner = fma(grr, xr, fma(2.0, v, -2.0 * cvec[r]));
-                acc[q] = fma(xr, inner, acc[q]);
-            }
+            for (int q = 0; q < 4; ++q) off[q] = fma(xg[q * D + r], y[q], off[q]);
         }
+    }
+    // diagonal and linear terms x_r (Gm_rr x_r - 2 c_r) of the warp's rows:
+    // item t * 4 + q (row t of the warp, candidate q) on lane item % 32, so a
+    // lane's items all belong to candidate lane % 4
+    double dg = 0.0;
+    for (int item = lane; item < nrows * 4; item += 32) {
+        const int t = item >> 2, q = item & 3;
+        const int pr = p0 + warp + 8 * (t >> 1);
+        const int r = (t & 1) == 0 ? pr : D - 1 - pr;
+        const double xr = xg[q * D + r];
+        dg = fma(xr, fma(Gm[(size_t)r * D + r], xr, -2.0 * cvec[r]), dg);
+    }
+    double acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = fma(2.0, off[q], (lane & 3) == q ? dg : 0.0);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+        acc[q] = v;
     }
     if (lane == 0)
 #pragma unroll

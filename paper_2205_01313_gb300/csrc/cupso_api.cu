@@ -867,8 +867,14 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     L->M = M;
     L->precision = precision;
     const int nblk = lsq_cand_blocks(h->Np);
-    // FP64 rescoring in pieces of 8 row pairs of A^T A, one per warp of a block
-    L->chunks = std::max(32, ((h->D + 1) / 2 + 7) / 8);
+    // FP64 rescoring in pieces of at most 8 row pairs of A^T A (one per warp of
+    // a block), as many pieces as give every SM two of the 4 x pieces blocks
+    {
+        const int npairs = (h->D + 1) / 2;
+        const int target = std::max(1, h->num_sms / 2);
+        const int per = std::min(8, std::max(1, (npairs + target - 1) / target));
+        L->chunks = std::max(32, (npairs + per - 1) / per);
+    }
     // candidates: 16 per block, the merged 16, and the merging ticket
     const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 17), 256) +
                          align_up(sizeof(double) * 16 * L->chunks, 256) + align_up((size_t)h->Np, 256) + 256;

@@ -308,11 +308,15 @@ CUPSO_API int cupso_solve_batch(int n_swarms, const cupso_problem* problems, int
  * Working storage: a fixed device array of about 41 KB inside the library
  * (static, one per GPU that loads the library, held until the process exits)
  * holds the per-block keys, the double-buffered gbest position, the iteration
- * counter and the status word. Limits: N <= CUPSO_NOALLOC_MAX_N and D <=
- * CUPSO_NOALLOC_MAX_D; larger sizes return CUPSO_ERR_INVALID_ARG with a
- * message in cupso_last_error(). The first call on each device looks up that
- * array's device address (with the device current); make that first call
- * before any stream capture. Every call on a device shares the one array and
+ * counter and the status word. Limits: N <= CUPSO_NOALLOC_MAX_N, D <=
+ * CUPSO_NOALLOC_MAX_D and also ld <= CUPSO_NOALLOC_MAX_N (every column of the
+ * stride is moved and reduced, one scratch key per 1024 columns); larger sizes
+ * return CUPSO_ERR_INVALID_ARG with a message in cupso_last_error(), before
+ * anything is queued. The first call on each device looks up that array's
+ * device address (with the device current); make that first call before any
+ * stream capture. The address is remembered together with the context it was
+ * taken in; after cudaDeviceReset the next call looks it up again, and that
+ * call, too, must come before any stream capture. Every call on a device shares the one array and
  * clears the counters it needs at its start: calls that overlap on the GPU
  * (several streams, several host threads) race and give wrong results, so
  * serialise them.

@@ -77,10 +77,32 @@ __global__ void noalloc_epilogue(const NoAllocScratch* sc, float* gbest_pos, flo
 }
 
 // Device address of the scratch on the current device, looked up once per
-// device with that device current.
+// device with that device current. The address belongs to the module loaded
+// into the device's current context: after cudaDeviceReset (or a primary
+// context released and created again) the module is loaded anew and the
+// symbol may move, so the cache also remembers the context it was taken in
+// and looks the address up again when the current context differs.
 constexpr int kMaxDevices = 64;
 NoAllocScratch* g_scratch_ptr[kMaxDevices] = {};
+void* g_scratch_ctx[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link to
+// libcuda): the identity of the context whose module holds the scratch.
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current_fn() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    return fn;
+}
 
 int scratch_on_current_device(NoAllocScratch** out, char* err, size_t errlen) {
     int dev = 0;
@@ -93,15 +115,23 @@ int scratch_on_current_device(NoAllocScratch** out, char* err, size_t errlen) {
         std::snprintf(err, errlen, "device ordinal %d out of range", dev);
         return CUPSO_ERR_UNSUPPORTED;
     }
+    CtxGetCurrentFn get_ctx = ctx_get_current_fn();
+    void* ctx = nullptr;
+    if (get_ctx) get_ctx(&ctx);
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || !ctx || g_scratch_ctx[dev] != ctx) {
+        // The lookup also makes the device's primary context current when no
+        // context is yet, so the context is read again after it.
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             std::snprintf(err, errlen, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
             return CUPSO_ERR_CUDA;
         }
+        ctx = nullptr;
+        if (get_ctx) get_ctx(&ctx);
         g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_ptr[dev];
     return CUPSO_OK;
@@ -124,6 +154,14 @@ int noalloc_step(int D, int N, const cupso_bounds* bounds, float w, float c1, fl
     }
     if (ld < N || ld % kPad != 0) {
         std::snprintf(err, errlen, "ld must be a multiple of %d and >= N", kPad);
+        return CUPSO_ERR_INVALID_ARG;
+    }
+    // Every column up to ld is moved and reduced: the first kernel runs one
+    // block per kTile columns of the stride and each block writes one key into
+    // the scratch, which holds kNoAllocMaxTiles of them. So the stride, not
+    // only N, is bounded by the scratch.
+    if (ld > CUPSO_NOALLOC_MAX_N) {
+        std::snprintf(err, errlen, "no-allocation step supports ld <= %d (got ld=%d)", CUPSO_NOALLOC_MAX_N, ld);
         return CUPSO_ERR_INVALID_ARG;
     }
     if (!pos || !v || !pbest_pos || !pbest_fit || !gbest_pos || !aligned16(pos) || !aligned16(v) ||

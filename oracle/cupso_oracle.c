@@ -262,7 +262,10 @@ double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x)
 
 float ora_fitness_p(const ora_params* p, const float* x)
 {
-    if (p->fitness == ORA_LSQ) return ora_lsq_f32(p->lsq_A, p->lsq_b, p->lsq_M, p->D, x);
+    if (p->fitness == ORA_LSQ) {
+        if (p->lsq_fp64) return (float)ora_lsq_f64(p->lsq_A, p->lsq_b, p->lsq_M, p->D, x);
+        return ora_lsq_f32(p->lsq_A, p->lsq_b, p->lsq_M, p->D, x);
+    }
     return ora_fitness(p->fitness, x, p->D);
 }
 

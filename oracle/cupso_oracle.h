@@ -47,6 +47,10 @@ typedef struct {
     const float* lsq_A;
     const float* lsq_b;
     int lsq_M;
+    /* nonzero: the least-squares fitness is computed in binary64 in the order
+     * of ora_lsq_f64 and rounded once to binary32 (the reference "FP64
+     * fitness" swarm); zero: ora_lsq_f32 */
+    int lsq_fp64;
 } ora_params;
 
 typedef struct {
@@ -84,7 +88,11 @@ float ora_fitness(int fitness, const float* x, int D);
 /* Least-squares fitness in FP32 with a fixed order: per m, r = -b_m, then
  * r = fma(A_md, x_d, r) for d = 0..D-1; acc = fma(r, r, acc) for m = 0..M-1. */
 float ora_lsq_f32(const float* A, const float* b, int M, int D, const float* x);
-/* The same sum in double precision (the FP64 reference of the rescoring). */
+/* The same sum in double precision (the FP64 reference of the rescoring and
+ * of the FP64-fitness swarm): per m, r = -b_m, then r = r + A_md * x_d for
+ * d = 0..D-1 (each product of two binary32 values is exact in binary64, so
+ * one rounding per term); acc = acc + r * r for m = 0..M-1 (the square
+ * rounded, then the sum). */
 double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x);
 /* Fitness with the swarm's parameters (LSQ needs p->lsq_*). */
 float ora_fitness_p(const ora_params* p, const float* x);

@@ -22,7 +22,7 @@ class _Params(C.Structure):
                 ("min_pos", C.c_float), ("max_pos", C.c_float), ("max_v", C.c_float),
                 ("w", C.c_float), ("c1", C.c_float), ("c2", C.c_float),
                 ("fitness", C.c_int), ("seed", C.c_uint64), ("swarm", C.c_uint32),
-                ("lsq_A", C.c_void_p), ("lsq_b", C.c_void_p), ("lsq_M", C.c_int)]
+                ("lsq_A", C.c_void_p), ("lsq_b", C.c_void_p), ("lsq_M", C.c_int), ("lsq_fp64", C.c_int)]
 
 
 class _State(C.Structure):
@@ -161,11 +161,14 @@ def fit_key(f):
 class Swarm:
     """One swarm as the oracle holds it. Fields mirror Table 1 of the paper."""
 
-    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0, lsq=None):
-        """lsq = (A [M][D] float32, b [M] float32) for the least-squares fitness."""
+    def __init__(self, N, D, min_pos, max_pos, max_v, w, c1, c2, fitness, seed, swarm=0, lsq=None, lsq_fp64=False):
+        """lsq = (A [M][D] float32, b [M] float32) for the least-squares fitness;
+        lsq_fp64: that fitness in binary64 (ora_lsq_f64's order), rounded to
+        float32, instead of the binary32 order of ora_lsq_f32."""
         self.p = _Params(int(N), int(D), float(np.float32(min_pos)), float(np.float32(max_pos)),
                          float(np.float32(max_v)), float(np.float32(w)), float(np.float32(c1)),
-                         float(np.float32(c2)), int(fitness), int(seed), int(swarm), None, None, 0)
+                         float(np.float32(c2)), int(fitness), int(seed), int(swarm), None, None, 0,
+                         1 if lsq_fp64 else 0)
         if lsq is not None:
             self._A = np.ascontiguousarray(lsq[0], np.float32)
             self._b = np.ascontiguousarray(lsq[1], np.float32)

@@ -426,3 +426,47 @@ def test_lsq_swarm_steps_follow_the_swarm_rules():
     for i in range(40):
         assert s.pbest_fit[i] == O.lsq_f32(A, b, s.pbest_pos[i])
     assert s.gbest_idx == int(np.lexsort((np.arange(40), s.pbest_fit))[0])
+
+
+def test_lsq_f64_is_the_exact_residual_sum():
+    """ora_lsq_f64 against the exact rational value of sum_m (sum_d A_md x_d - b_m)^2
+    (every float32 input is an exact rational): within the binary64 rounding of
+    its M (D + 2) operations. A dropped term, a sign error on b or a transposed
+    A would be off by far more."""
+    from fractions import Fraction as Fr
+    rng = np.random.default_rng(21)
+    for M, D in [(7, 3), (5, 11), (13, 1)]:
+        A = rng.standard_normal((M, D)).astype(np.float32)
+        b = rng.standard_normal(M).astype(np.float32)
+        x = rng.uniform(-2, 2, D).astype(np.float32)
+        exact = Fr(0)
+        for m in range(M):
+            r = -Fr(float(b[m])) + sum(Fr(float(A[m, d])) * Fr(float(x[d])) for d in range(D))
+            exact += r * r
+        got = O.lsq_f64(A, b, x)
+        assert abs(Fr(got) - exact) <= Fr(M * (D + 3)) * Fr(2) ** -52 * (exact + 1), (M, D)
+
+
+def test_lsq_fp64_fitness_swarm():
+    """The FP64-fitness swarm (the reference run of the precision study): every
+    pbest_fit is the FP64 fitness of its pbest_pos rounded once to float32, the
+    gbest is the lowest-index argmin, pbest_fit never increases, and on a small
+    convex problem the swarm reaches the closed-form least-squares minimum to
+    1e-6 relative."""
+    A, b, _ = _lsq_problem(64, 6, seed=5)
+    s = O.Swarm(40, 6, -2, 2, 0.4, 0.729, 1.49445, 1.49445, O.LSQ, 2, lsq=(A, b), lsq_fp64=True).init()
+    for i in range(40):
+        assert s.pbest_fit[i] == np.float32(O.lsq_f64(A, b, s.pbest_pos[i]))
+    prev = s.pbest_fit.copy()
+    for _ in range(20):
+        s.step_sync(1)
+        assert np.all(s.pbest_fit <= prev)
+        prev = s.pbest_fit.copy()
+    for i in range(40):
+        assert s.pbest_fit[i] == np.float32(O.lsq_f64(A, b, s.pbest_pos[i]))
+    assert s.gbest_idx == int(np.lexsort((np.arange(40), s.pbest_fit))[0])
+    s.step_sync(600)
+    x64, res, _, _ = np.linalg.lstsq(A.astype(np.float64), b.astype(np.float64), rcond=None)
+    fmin = float(res[0])
+    g = O.lsq_f64(A, b, s.gbest_pos)
+    assert fmin <= g * (1 + 1e-12) and g <= fmin * (1 + 1e-6), (g, fmin)

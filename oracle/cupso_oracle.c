@@ -260,6 +260,102 @@ double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x)
     return acc;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The tensor-core fitness of the least-squares swarm, on rounded operands    */
+/* ------------------------------------------------------------------------- */
+
+/* bfloat16 keeps the upper 16 bits of the binary32 encoding: 8 significant
+ * bits. Round to nearest, ties to even, by adding 0x7FFF plus the lowest kept
+ * bit and truncating; a carry into the exponent gives the next binade (or
+ * infinity). NaN is returned unchanged. */
+float ora_round_bf16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, sizeof u);
+    if ((u & 0x7F800000u) == 0x7F800000u && (u & 0x007FFFFFu)) return x;
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    float r;
+    memcpy(&r, &u, sizeof r);
+    return r;
+}
+
+/* FP8 e4m3 (the OCP "E4M3FN" format): 3 mantissa bits, exponent bias 7, no
+ * infinities, largest finite 448 = 1.75 * 2^8, normals from 2^-6, subnormals
+ * k * 2^-9. Round to nearest, ties to even, on the grid of the value's binade
+ * (spacing 2^(e - 3) for 2^e <= |x| < 2^(e + 1), 2^-9 below 2^-6), then
+ * saturate to +-448 (the conversion the tensor-core operands use). */
+float ora_round_e4m3(float x)
+{
+    if (isnan(x)) return x;
+    const double a = fabs((double)x);
+    double q = 0x1p-9;
+    if (a >= 0x1p-6) {
+        int e;
+        frexp(a, &e);              /* a = f 2^e, 0.5 <= f < 1: the binade is 2^(e-1) */
+        q = ldexp(1.0, e - 1 - 3);
+    }
+    double r = nearbyint(a / q) * q;   /* a / q is exact (q a power of two); default mode: ties to even */
+    if (r > 448.0) r = 448.0;
+    return (float)copysign(r, (double)x);
+}
+
+void ora_round_bf16_n(const float* in, float* out, size_t n)
+{
+    for (size_t k = 0; k < n; ++k) out[k] = ora_round_bf16(in[k]);
+}
+
+void ora_round_e4m3_n(const float* in, float* out, size_t n)
+{
+    for (size_t k = 0; k < n; ++k) out[k] = ora_round_e4m3(in[k]);
+}
+
+/* ||A x - b||^2 written as ||A (x - g) + (A g - b)||^2 around a reference
+ * point g, with the operands the tensor cores see: per row m the offset
+ * o_m = A_m g - b_m in binary64, rounded once to binary32; per dimension the
+ * displacement x_d - g_d in binary32, then rounded -- BF16: A_md and the
+ * displacement to bfloat16; FP8: A_md * sa_m and the displacement * sx to e4m3,
+ * with sa_m = 448 / max_d |A_md| (1 for a zero row) and the product scaled back
+ * by inv_m = 1 / (sx sa_m), all three in binary32. The products of the rounded
+ * operands, their sum over d, the offset and the sum of squares over m are
+ * then exact up to binary64 rounding: this is the value the FP32-accumulating
+ * tensor-core product approximates. fmt: 1 = BF16, 2 = FP8. */
+double ora_lsq_disp(const float* A, const float* b, int M, int D, const float* x, const float* g, int fmt,
+                    float sx)
+{
+    double acc = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const float* row = A + (size_t)m * D;
+        double o = -(double)b[m];
+        for (int d = 0; d < D; ++d) o += (double)row[d] * (double)g[d];
+        const float off = (float)o;
+        float sa = 1.0f, inv = 1.0f;
+        if (fmt == 2) {
+            float amax = 0.0f;
+            for (int d = 0; d < D; ++d) amax = fmaxf(amax, fabsf(row[d]));
+            sa = amax > 0.0f ? 448.0f / amax : 1.0f;
+            inv = 1.0f / (sx * sa);
+        }
+        double y = 0.0;
+        for (int d = 0; d < D; ++d) {
+            const float dd = x[d] - g[d];
+            float aq, dq;
+            if (fmt == 2) {
+                aq = ora_round_e4m3(row[d] * sa);
+                dq = ora_round_e4m3(dd * sx);
+            } else {
+                aq = ora_round_bf16(row[d]);
+                dq = ora_round_bf16(dd);
+            }
+            y += (double)aq * (double)dq;
+        }
+        if (fmt == 2) y *= (double)inv;
+        const double r = y + (double)off;
+        acc += r * r;
+    }
+    return acc;
+}
+
 float ora_fitness_p(const ora_params* p, const float* x)
 {
     if (p->fitness == ORA_LSQ) {

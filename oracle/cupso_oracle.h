@@ -18,6 +18,7 @@
 #ifndef CUPSO_ORACLE_H
 #define CUPSO_ORACLE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -94,6 +95,19 @@ float ora_lsq_f32(const float* A, const float* b, int M, int D, const float* x);
  * one rounding per term); acc = acc + r * r for m = 0..M-1 (the square
  * rounded, then the sum). */
 double ora_lsq_f64(const float* A, const float* b, int M, int D, const float* x);
+/* Rounding of binary32 values to the tensor-core operand formats: bfloat16
+ * (round to nearest even) and FP8 e4m3 (round to nearest even, saturated to
+ * +-448); the _n forms round an array. */
+float ora_round_bf16(float x);
+float ora_round_e4m3(float x);
+void ora_round_bf16_n(const float* in, float* out, size_t n);
+void ora_round_e4m3_n(const float* in, float* out, size_t n);
+/* The least-squares fitness as the tensor-core modes of the swarm compute it:
+ * ||A (x - g) + (A g - b)||^2 around the reference point g, from rounded
+ * operands (fmt 1 = BF16, 2 = FP8 with row scales of A and the scale sx of the
+ * displacement), evaluated in binary64. */
+double ora_lsq_disp(const float* A, const float* b, int M, int D, const float* x, const float* g, int fmt,
+                    float sx);
 /* Fitness with the swarm's parameters (LSQ needs p->lsq_*). */
 float ora_fitness_p(const ora_params* p, const float* x);
 

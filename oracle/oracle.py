@@ -76,6 +76,10 @@ def lib():
         L.ora_lsq_f32.restype = C.c_float
         L.ora_lsq_f64.argtypes = [f32p, f32p, C.c_int, C.c_int, f32p]
         L.ora_lsq_f64.restype = C.c_double
+        L.ora_round_bf16_n.argtypes = [f32p, f32p, C.c_size_t]
+        L.ora_round_e4m3_n.argtypes = [f32p, f32p, C.c_size_t]
+        L.ora_lsq_disp.argtypes = [f32p, f32p, C.c_int, C.c_int, f32p, f32p, C.c_int, C.c_float]
+        L.ora_lsq_disp.restype = C.c_double
         L.ora_argmin_pbest.argtypes = [C.POINTER(_Params), C.POINTER(_State)]
         L.ora_argmin_pbest.restype = C.c_int64
         f64p = C.POINTER(C.c_double)
@@ -152,6 +156,36 @@ def lsq_f64(A, b, x):
     b = np.ascontiguousarray(b, np.float32)
     x = np.ascontiguousarray(x, np.float32)
     return float(lib().ora_lsq_f64(_f32p(A), _f32p(b), A.shape[0], A.shape[1], _f32p(x)))
+
+
+def round_bf16(a):
+    """Elementwise round-to-nearest-even to bfloat16 (as float32 values)."""
+    a = np.ascontiguousarray(a, np.float32)
+    out = np.empty_like(a)
+    lib().ora_round_bf16_n(_f32p(a), _f32p(out), a.size)
+    return out
+
+
+def round_e4m3(a):
+    """Elementwise round-to-nearest-even to FP8 e4m3, saturated to +-448 (as float32 values)."""
+    a = np.ascontiguousarray(a, np.float32)
+    out = np.empty_like(a)
+    lib().ora_round_e4m3_n(_f32p(a), _f32p(out), a.size)
+    return out
+
+
+LSQ_FMT = {"bf16": 1, "fp8": 2}
+
+
+def lsq_disp(A, b, x, g, fmt, sx=1.0):
+    """||A (x - g) + (A g - b)||^2 on the operands the tensor-core modes round
+    (fmt "bf16" or "fp8"; sx: the FP8 scale of the displacement), in FP64."""
+    A = np.ascontiguousarray(A, np.float32)
+    b = np.ascontiguousarray(b, np.float32)
+    x = np.ascontiguousarray(x, np.float32)
+    g = np.ascontiguousarray(g, np.float32)
+    return float(lib().ora_lsq_disp(_f32p(A), _f32p(b), A.shape[0], A.shape[1], _f32p(x), _f32p(g),
+                                    LSQ_FMT[fmt], float(np.float32(sx))))
 
 
 def fit_key(f):

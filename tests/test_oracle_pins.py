@@ -470,3 +470,89 @@ def test_lsq_fp64_fitness_swarm():
     fmin = float(res[0])
     g = O.lsq_f64(A, b, s.gbest_pos)
     assert fmin <= g * (1 + 1e-12) and g <= fmin * (1 + 1e-6), (g, fmin)
+
+
+# --------------------------------------------------------------------------- #
+# Operand roundings and the displacement form of the tensor-core fitness      #
+# --------------------------------------------------------------------------- #
+
+def _special_floats():
+    rng = np.random.default_rng(31)
+    v = np.concatenate([rng.standard_normal(20000).astype(np.float32) * np.float32(10.0) ** rng.integers(-12, 12, 20000),
+                        np.array([0.0, -0.0, 1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, -1.5, 3e38, 1e-40,
+                                  2 ** -126, 2 ** -133], np.float32)]).astype(np.float32)
+    return v
+
+
+def test_round_bf16_closed_forms_and_torch():
+    """Ties go to the even neighbour (1 + 2^-8 -> 1; 1 + 3 2^-8 -> 1 + 2^-6), and every
+    value agrees bit for bit with torch's float32 -> bfloat16 conversion."""
+    torch = pytest.importorskip("torch")
+    r = O.round_bf16(np.array([1 + 2 ** -8, 1 + 3 * 2 ** -8, 1 + 2 ** -7, 255.5, 3.4e38], np.float32))
+    assert r[0] == 1.0 and r[1] == 1 + 2 ** -6 and r[2] == 1 + 2 ** -7 and r[3] == 256.0 and np.isinf(r[4])
+    v = _special_floats()
+    ref = torch.from_numpy(v).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(O.round_bf16(v).view(np.uint32), ref.view(np.uint32))
+
+
+def test_round_e4m3_closed_forms_and_torch():
+    """The format's grid: largest 448, smallest subnormal 2^-9, ties to even
+    (2^-10 -> 0, 3 2^-10 -> 2^-8, 1 + 2^-4 -> 1, 1 + 3 2^-4 -> 1.25), saturation
+    above 448; in range, bit for bit what torch's float8_e4m3fn conversion gives."""
+    torch = pytest.importorskip("torch")
+    cases = {448.0: 448.0, 500.0: 448.0, -1e6: -448.0, 2.0 ** -9: 2.0 ** -9, 2.0 ** -10: 0.0,
+             3 * 2.0 ** -10: 2.0 ** -8, 1 + 2.0 ** -4: 1.0, 1 + 3 * 2.0 ** -4: 1.25, 0.1: 0.1015625}
+    got = O.round_e4m3(np.array(list(cases), np.float32))
+    np.testing.assert_array_equal(got, np.array(list(cases.values()), np.float32))
+    v = _special_floats()
+    v = v[np.abs(v) <= 448.0]
+    ref = torch.from_numpy(v).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    np.testing.assert_array_equal(O.round_e4m3(v), ref)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_lsq_disp_is_the_fitness_up_to_operand_rounding(fmt):
+    """The displacement form is the same function: its distance from the FP64
+    fitness stays within the bound the operand rounding implies, and that bound
+    (hence the error) scales with |x - g|, which is the point of the form: 100x
+    closer to the reference point, about 100x smaller error. With g = x the
+    displacement is zero and only the offsets' float rounding is left."""
+    A, b, _ = _lsq_problem(200, 24, seed=8)
+    rng = np.random.default_rng(9)
+    g = rng.uniform(-2, 2, 24).astype(np.float32)
+    sx = np.float32(448.0 / 4.0)
+    unit = 2 ** -8 if fmt == "bf16" else 2 ** -3     # relative rounding of one operand (with margin)
+    errs = []
+    for eps in (1.0, 1e-2):
+        x = (g + eps * rng.uniform(-1, 1, 24)).astype(np.float32)
+        f = O.lsq_f64(A, b, x)
+        fd = O.lsq_disp(A, b, x, g, fmt, sx)
+        R = A.astype(np.float64) @ x.astype(np.float64) - b
+        dR = np.abs(A.astype(np.float64)) @ np.abs((x - g).astype(np.float64)) * 2 * unit \
+            + np.abs(R) * 2 ** -23 + 1e-12
+        bound = float(np.sum(2 * np.abs(R) * dR + dR * dR))
+        assert abs(fd - f) <= bound, (eps, fd, f, bound)
+        errs.append(abs(fd - f))
+    assert errs[1] < errs[0] / 20 + 1e-9
+    f0 = O.lsq_disp(A, b, g, g, fmt, sx)
+    R = A.astype(np.float64) @ g.astype(np.float64) - b
+    assert abs(f0 - O.lsq_f64(A, b, g)) <= float(np.sum(2 * np.abs(R) * np.abs(R) * 2 ** -24)) * 1.01 + 1e-15
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_lsq_disp_exact_on_representable_operands(fmt):
+    """Closed form: when A (each row holding 448, so the FP8 row scale is 1),
+    the displacements x - g and A g - b are exact in the format (sx = 1), the
+    displacement form rounds nothing, and must equal the exact rational value
+    of sum_m (A_m x - b_m)^2 -- a dropped term, a sign error on the offset or a
+    wrong scale would not."""
+    from fractions import Fraction as Fr
+    A = np.array([[448, 1, -2, 0.5], [3, 448, 0.25, -1], [-448, 2, 1, 1.5], [0.5, -3, 448, 2],
+                  [1, 1, 1, -448]], np.float32)
+    g = np.array([1, -2, 0.5, 0.25], np.float32)
+    x = (g + np.array([0.5, -1, 2, -0.125], np.float32)).astype(np.float32)
+    b = np.array([3, -7, 5, 11, -2], np.float32)
+    exact = sum((sum(Fr(float(A[m, d])) * Fr(float(x[d])) for d in range(4)) - Fr(float(b[m]))) ** 2
+                for m in range(5))
+    assert O.lsq_disp(A, b, x, g, fmt, 1.0) == float(exact)
+    assert O.lsq_f64(A, b, x) == float(exact)

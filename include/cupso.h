@@ -78,7 +78,9 @@ typedef enum {
 typedef enum {
     CUPSO_LSQ_FP32 = 0,   /* CUDA cores, fixed FP32 order (bit-exact with the oracle)          */
     CUPSO_LSQ_BF16 = 1,   /* tensor cores, BF16 operands, FP32 accumulation                    */
-    CUPSO_LSQ_FP8 = 2     /* tensor cores, FP8 e4m3 operands (A scaled per row), FP32 accumulation */
+    CUPSO_LSQ_FP8 = 2,    /* tensor cores, FP8 e4m3 operands (A scaled per row), FP32 accumulation */
+    CUPSO_LSQ_FP64 = 3    /* CUDA cores, FP64 in a fixed order, rounded once to FP32 (bit-exact with
+                             the oracle): the exact-fitness reference of the precision comparison */
 } cupso_lsq_precision;
 
 typedef enum {
@@ -206,10 +208,15 @@ CUPSO_API int cupso_set_state(cupso_handle h, const float* pos, const float* v, 
  * A device [M][D] row-major float32, b device [M] float32, both borrowed (they
  * must stay valid until the handle is destroyed or they are replaced).
  * precision (cupso_lsq_precision) selects how the swarm's fitness -- one
- * matrix product X A^T per iteration -- is computed: FP32 on the CUDA cores
- * in a fixed order (the synchronous trajectory is then exactly the oracle's),
- * or BF16 / FP8 e4m3 on the tensor cores with FP32 accumulation. In the BF16
- * and FP8 modes the pbest decisions use the approximate fitness, while a
+ * matrix product X A^T per iteration -- is computed: FP32 or FP64 on the CUDA
+ * cores in a fixed order (the synchronous trajectory is then exactly the
+ * oracle's), or BF16 / FP8 e4m3 on the tensor cores with FP32 accumulation.
+ * The tensor-core product takes each particle's displacement from the current
+ * gbest_pos g, x - g, as its operand, and adds the residual offsets A g - b
+ * (computed once per change of g with a compensated FP32 dot product) in its
+ * epilogue: the same function ||A x - b||^2, with the operand rounding scaled
+ * by |x - g|, which shrinks as the swarm converges, instead of by |x|. In the
+ * BF16 and FP8 modes the pbest decisions use the approximate fitness, while a
  * global best is accepted only after the (up to) 16 improved particles with
  * the lowest approximate fitness are rescored in FP64; gbest_fit is then that
  * FP64 value (rounded to float). This call evaluates the fitness of every
@@ -333,8 +340,10 @@ CUPSO_API int cupso_tree_step_noalloc(int D, int N, const cupso_bounds* bounds, 
  * A device [M][D] row-major, b device [M], X device [N][D] row-major, f_out
  * device [N], all float32 (caller-owned). precision selects the arithmetic:
  * FP32 follows a fixed order (per row m, r = -b_m then r = fma(A_md, x_d, r)
- * for d in order; f = sum over m in order of fma(r, r, .)); BF16 and FP8 form
- * X A^T on the tensor cores (the fitness of the dense-fitness extension of the
+ * for d in order; f = sum over m in order of fma(r, r, .)); FP64 the same
+ * order in binary64 (acc = acc + r * r, the square rounded first), rounded
+ * once to float at the end; BF16 and FP8 form X A^T on the tensor cores from
+ * the positions themselves (the fitness of the dense-fitness extension of the
  * method; the paper's own fitness is analytic, Sec. 5.1). Allocates temporary
  * device memory, queues on `cuda_stream` and waits. */
 CUPSO_API int cupso_lsq_eval(const float* A_dev, const float* b_dev, int M, int D, const float* X_dev, int N,

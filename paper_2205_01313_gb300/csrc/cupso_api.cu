@@ -213,12 +213,17 @@ void drop_graph(cupso_swarm* h) {
 
 constexpr int kModeLsq = 100;   // internal: one least-squares iteration
 
+// The tensor-core precisions: approximate fitness, FP64-verified gbest.
+bool lsq_approx(int precision) { return precision == CUPSO_LSQ_BF16 || precision == CUPSO_LSQ_FP8; }
+
 cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
     cupso_swarm::Lsq& L = *h->lsq;
     const int grid = h->num_sms * 8;   // grid-stride over (particle group, dimension) items
-    if (L.precision == CUPSO_LSQ_FP32) {
+    if (!lsq_approx(L.precision)) {
         cudaError_t e = lsq_launch_move(h->dev, grid, st);
-        if (e == cudaSuccess) e = lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
+        if (e == cudaSuccess)
+            e = L.precision == CUPSO_LSQ_FP64 ? lsq_fp64_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st)
+                                              : lsq_fp32_launch(h->dev.x, h->Np, h->N, h->D, L.A, L.b, L.M, L.f, st);
         if (e != cudaSuccess) return e;
         return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
@@ -240,7 +245,24 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
     }
     return lsq_launch_gbest_approx(h->dev, nullptr, L.tc.part, lsq_tc_partials(L.tc.plan), 0, true, L.A, L.b, L.M,
                                    L.cand, L.partial, L.chunks, L.g64, reinterpret_cast<unsigned int*>(h->dev.pflag),
-                                   grid, L.gram, st);
+                                   grid, L.gram, L.tc.roff, L.tc.roff_stale, h->num_sms, st);
+}
+
+// gbest of an approximate-fitness swarm from scratch, with `fit` (device, [Np])
+// as every particle's approximate fitness: the 16 lowest are rescored in FP64
+// and the best becomes gbest (and the reference point of the tensor-core
+// fitness, whose offsets are recomputed). t_dev ends at t.
+cudaError_t lsq_reset_gbest(cupso_swarm* h, const float* fit, uint32_t t, cudaStream_t st) {
+    cupso_swarm::Lsq& L = *h->lsq;
+    const double inf = INFINITY;
+    cudaError_t e = cudaMemcpyAsync(L.g64, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
+    // the accept kernel advances t: start one below and let it land on t
+    if (e == cudaSuccess) e = lsq_launch_set_t(h->dev, t - 1u, st);
+    if (e == cudaSuccess)
+        e = lsq_launch_gbest_approx(h->dev, fit, nullptr, 0, 1, true, L.A, L.b, L.M, L.cand, L.partial, L.chunks,
+                                    L.g64, reinterpret_cast<unsigned int*>(h->dev.pflag), h->num_sms * 8, L.gram,
+                                    L.tc.roff, L.tc.roff_stale, h->num_sms, st);
+    return e;
 }
 
 cudaError_t launch_one64(cupso_swarm* h, int mode, cudaStream_t st) {
@@ -709,7 +731,7 @@ int cupso_step(cupso_handle h, int iters) {
             if (e != cudaSuccess) return cuda_fail(e, "least-squares iteration");
         }
         // the tensor-core iteration leaves improved pbest rows to the next move
-        if (h->lsq->precision != CUPSO_LSQ_FP32) h->lazy_pending = true;
+        if (lsq_approx(h->lsq->precision)) h->lazy_pending = true;
         h->t_host += (uint32_t)iters;
         return CUPSO_OK;
     }
@@ -833,7 +855,12 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
     CUPSO_CUDA(cudaMemcpy(h->dev.pf, pf.data(), sizeof(float) * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
     CUPSO_CUDA(cudaMemset(h->dev.pflag, 0, Np), "cudaMemset");
     h->lazy_pending = false;
-    CUPSO_CUDA(launch_recompute(h->dev, t, h->stream), "recompute launch");
+    if (h->lsq && lsq_approx(h->lsq->precision)) {
+        // the given pbest_fit are approximate values: gbest only from FP64 rescoring
+        CUPSO_CUDA(lsq_reset_gbest(h, h->dev.pf, t, h->stream), "lsq gbest");
+    } else {
+        CUPSO_CUDA(launch_recompute(h->dev, t, h->stream), "recompute launch");
+    }
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     h->t_host = t;
     return CUPSO_OK;
@@ -844,8 +871,8 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
     if (h->fid != CUPSO_LSQ) return fail(CUPSO_ERR_INVALID_ARG, "swarm was not created with CUPSO_LSQ%s");
     if (!A_dev || !b_dev || M < 1) return fail(CUPSO_ERR_INVALID_ARG, "A, b must be device arrays and M >= 1%s");
-    if (precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP8) return fail(CUPSO_ERR_INVALID_ARG, "unknown precision%s");
-    if (precision != CUPSO_LSQ_FP32 && !lsq_tc_available())
+    if (precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP64) return fail(CUPSO_ERR_INVALID_ARG, "unknown precision%s");
+    if (lsq_approx(precision) && !lsq_tc_available())
         return fail(CUPSO_ERR_UNSUPPORTED, "tensor-core least squares needs cuTensorMapEncodeTiled%s");
     int rc = ensure_materialized(h);
     if (rc) return rc;
@@ -891,10 +918,11 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     CUPSO_CUDA(cudaMemsetAsync(L->f, 0, sizeof(float) * h->Np, h->stream), "cudaMemsetAsync");
     CUPSO_CUDA(cudaMemsetAsync(L->cand + (size_t)nblk * 16 + 16, 0, sizeof(unsigned long long), h->stream),
                "cudaMemsetAsync");
-    if (precision != CUPSO_LSQ_FP32) {
-        // FP8 scale of the positions from the search box
-        const float xmax = std::max(std::fabs(h->dev.lo), std::fabs(h->dev.hi));
-        const float sx = xmax > 0.0f ? 448.0f / xmax : 1.0f;
+    if (lsq_approx(precision)) {
+        // FP8 scale of the operand: displacements between two points of the box
+        // are at most max_pos - min_pos in magnitude
+        const float span = h->dev.hi - h->dev.lo;
+        const float sx = std::isfinite(span) && span > 0.0f ? 448.0f / span : 1.0f;
         rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
         if (rc) return rc;
         if (h->D <= M && (size_t)h->D * h->D <= ((size_t)1 << 26)) {
@@ -913,21 +941,19 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         }
     }
     // Step 1 completes here: pbest_fit = f(pbest_pos), gbest from it.
-    if (precision == CUPSO_LSQ_FP32) {
-        CUPSO_CUDA(lsq_fp32_launch(h->dev.pb, h->Np, h->N, h->D, A_dev, b_dev, M, L->f, h->stream), "lsq fitness");
+    if (precision == CUPSO_LSQ_FP32 || precision == CUPSO_LSQ_FP64) {
+        CUPSO_CUDA(precision == CUPSO_LSQ_FP32
+                       ? lsq_fp32_launch(h->dev.pb, h->Np, h->N, h->D, A_dev, b_dev, M, L->f, h->stream)
+                       : lsq_fp64_launch(h->dev.pb, h->Np, h->N, h->D, A_dev, b_dev, M, L->f, h->stream),
+                   "lsq fitness");
         CUPSO_CUDA(lsq_launch_set_pf(h->dev, L->f, h->stream), "lsq pbest");
         CUPSO_CUDA(launch_recompute(h->dev, h->t_host, h->stream), "recompute launch");
     } else {
+        // the positions' own fitness (reference point 0: offsets -b)
         rc = lsq_eval_tc(&L->tc, h->dev.pb, 1, (size_t)h->Np, h->N, L->f, h->stream);
         if (rc) return rc;
         CUPSO_CUDA(lsq_launch_set_pf(h->dev, L->f, h->stream), "lsq pbest");
-        // the accept kernel advances t: start one below and let it land on t_host
-        CUPSO_CUDA(lsq_launch_set_t(h->dev, h->t_host - 1u, h->stream), "lsq t");
-        CUPSO_CUDA(lsq_launch_gbest_approx(h->dev, L->f, nullptr, 0, 1, true, A_dev, b_dev, M, L->cand, L->partial,
-                                           L->chunks,
-                                           L->g64, reinterpret_cast<unsigned int*>(h->dev.pflag), h->num_sms * 8,
-                                           L->gram, h->stream),
-                   "lsq gbest");
+        CUPSO_CUDA(lsq_reset_gbest(h, L->f, h->t_host, h->stream), "lsq gbest");
     }
     CUPSO_CUDA(cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return CUPSO_OK;
@@ -937,7 +963,7 @@ int cupso_get_gbest_f64(cupso_handle h, double* fit_out) {
     if (!h || !fit_out) return fail(CUPSO_ERR_INVALID_ARG, "NULL argument%s");
     if (h->fid != CUPSO_LSQ || !h->lsq) return fail(CUPSO_ERR_INVALID_ARG, "not a least-squares swarm with A, b set%s");
     cupso_swarm::Lsq& L = *h->lsq;
-    if (L.precision == CUPSO_LSQ_FP32) {
+    if (!lsq_approx(L.precision)) {
         // rescore the gbest particle's pbest_pos (== gbest_pos) in FP64
         const int rc = ensure_materialized(h);
         if (rc) return rc;

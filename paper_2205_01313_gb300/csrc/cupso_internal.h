@@ -61,9 +61,10 @@ cudaError_t lsq_prepare();
 cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
                         void* dst, cudaStream_t st);
 bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp);
-// part[k][i] (k < lsq_tc_partials) = sum of squared residuals of particle i
-// over residual rows 128 k .. 128 k + 127.
-cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
+// part[k][i] (k < lsq_tc_partials) = sum of squared residuals y + off[m] of
+// particle i over residual rows 128 k .. 128 k + 127 (off = -b: the positions'
+// residuals; off = A c - b: residuals of displacements from c).
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* off, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st);
 int lsq_tc_partials(const LsqTcPlan& p);
 // Tensor-core fitness state for fixed (A, b): operand copies, scales, plan.
@@ -74,7 +75,9 @@ struct LsqTcState {
     float sx = 1.0f;                 // FP8 scale of the positions
     void* Aq = nullptr;              // [Mp][Kp] operand copy of A
     void* Xq = nullptr;              // [Np][Kp] operand copy of the positions
-    float* bpad = nullptr;           // [Mp]
+    float* negb = nullptr;           // [Mp] -b, zero past M: the offsets of the positions' residuals
+    float* roff = nullptr;           // [Mp] A c - b for the swarm's reference point c (gbest), zero past M
+    int* roff_stale = nullptr;       // nonzero: roff must be recomputed (the reference point moved)
     float* inv = nullptr;            // [Mp] 1 / (sx * row scale of A) (FP8)
     float* part = nullptr;           // [Mp / 128][Np] partial sums
     unsigned int* status = nullptr;
@@ -87,12 +90,16 @@ void lsq_free_tc(LsqTcState* st);
 int lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, int N, float* f, cudaStream_t stream);
 // f[i], i < N, for the operand already in st->Xq (asynchronous).
 int lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream);
-// The same product, leaving f[i] as lsq_tc_partials(st->plan) partial sums
+// The same product for the displacement operand of the swarm (offsets
+// st->roff), leaving f[i] as lsq_tc_partials(st->plan) partial sums
 // st->part[k][i] (f[i] = their sum in k order).
 int lsq_eval_tc_partials(LsqTcState* st, cudaStream_t stream);
 
 // f[i] = plain FP32 fitness of X(i, d) = x[d * ldx + i], i < N.
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
+                            cudaStream_t st);
+// f[i] = FP64 fitness of the same positions in the reference order, rounded to float.
+cudaError_t lsq_fp64_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
                             cudaStream_t st);
 
 // Least-squares swarm iteration (kernels_lsq_swarm.cu); all read t from t_dev.
@@ -117,10 +124,17 @@ cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double
 // materialize kernel); otherwise they are copied here.
 // fit: the approximate fitness, or null with part/nparts: its partial sums
 // part[k][i] (Np apart), added in k order.
+// When it accepts a new gbest it sets stale[0]; with `off` set it then
+// recomputes the residual offsets of the new reference point (off[m] = A g - b,
+// compensated) for the next iteration's product. stale: two ints (flag and the
+// offset kernel's block counter), zero-initialised.
 cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const float* part, int nparts, int all,
                                     bool lazy, const float* A, const float* b, int M, unsigned long long* cand,
                                     double* partial, int chunks, double* g64, unsigned int* flags, int grid,
-                                    const LsqGram& gram, cudaStream_t st);
+                                    const LsqGram& gram, float* off, int* stale, int num_sms, cudaStream_t st);
+// off[m] = A g - b for the current gbest_pos g (slot t & 1), if stale[0] is set.
+cudaError_t lsq_launch_offsets(const SwarmDev& s, const float* A, const float* b, int M, float* off, int* stale,
+                               int num_sms, cudaStream_t st);
 cudaError_t lsq_launch_set_pf(const SwarmDev& s, const float* fit, cudaStream_t st);
 // FP64 fitness of the pbest_pos of the particle in `key`, into *g64; waits.
 cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, int M, unsigned long long key,

@@ -36,8 +36,7 @@ __global__ void row_absmax_kernel(const float* __restrict__ A, int M, int D, flo
 // Scale each row of A in place into a scratch copy: As[m][d] = A[m][d] * sa_m,
 // with sa_m = 448 / amax_m (1 for an all-zero row); inv[m] = 1 / (sx * sa_m).
 __global__ void scale_rows_kernel(const float* __restrict__ A, int M, int D, const float* __restrict__ amax, float sx,
-                                  float* __restrict__ As, float* __restrict__ inv, const float* __restrict__ b,
-                                  float* __restrict__ bpad, int Mp) {
+                                  float* __restrict__ As, float* __restrict__ inv, int Mp) {
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)M * D; e += (size_t)gridDim.x * blockDim.x) {
         const int m = (int)(e / D);
         const float sa = amax[m] > 0.0f ? 448.0f / amax[m] : 1.0f;
@@ -47,11 +46,21 @@ __global__ void scale_rows_kernel(const float* __restrict__ A, int M, int D, con
         if (m < M) {
             const float sa = amax[m] > 0.0f ? 448.0f / amax[m] : 1.0f;
             inv[m] = 1.0f / (sx * sa);
-            bpad[m] = b[m];
         } else {
             inv[m] = 0.0f;
-            bpad[m] = 0.0f;
         }
+    }
+}
+
+// negb[m] = -b[m] for m < M, 0 up to Mp (negation is exact, so y + negb[m]
+// rounds exactly as y - b[m]); roff starts as the same offsets (reference
+// point 0) until the swarm sets its own.
+__global__ void neg_pad_kernel(const float* __restrict__ b, int M, int Mp, float* __restrict__ negb,
+                               float* __restrict__ roff) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < Mp; m += gridDim.x * blockDim.x) {
+        const float v = m < M ? -b[m] : 0.0f;
+        negb[m] = v;
+        roff[m] = v;
     }
 }
 
@@ -94,31 +103,31 @@ int cupso::lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, i
     const size_t esz = fp8 ? 1 : 2;
     const size_t bytes_A = (size_t)st->Mp * st->Kp * esz, bytes_X = (size_t)Np * st->Kp * esz;
     const size_t nparts = (size_t)st->Mp / 128;   // one partial sum per 128 residual rows
-    const size_t bytes = up(bytes_A, 256) + up(bytes_X, 256) + up(sizeof(float) * st->Mp, 256) * 2 +
+    const size_t bytes = up(bytes_A, 256) + up(bytes_X, 256) + up(sizeof(float) * st->Mp, 256) * 3 +
                          up(sizeof(float) * nparts * Np, 256) + up(sizeof(float) * (size_t)M * D, 256) +
-                         up(sizeof(float) * M, 256) + 256;
+                         up(sizeof(float) * M, 256) + 512;
     cudaError_t e = cudaMalloc(&st->arena, bytes);
     if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc (lsq)"), e == cudaErrorMemoryAllocation ? CUPSO_ERR_OOM : CUPSO_ERR_CUDA;
     char* p = static_cast<char*>(st->arena);
     st->Aq = p; p += up(bytes_A, 256);
     st->Xq = p; p += up(bytes_X, 256);
-    st->bpad = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
+    st->negb = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
+    st->roff = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
     st->inv = reinterpret_cast<float*>(p); p += up(sizeof(float) * st->Mp, 256);
     st->part = reinterpret_cast<float*>(p); p += up(sizeof(float) * nparts * Np, 256);
     float* Ascaled = reinterpret_cast<float*>(p); p += up(sizeof(float) * (size_t)M * D, 256);
     float* amax = reinterpret_cast<float*>(p); p += up(sizeof(float) * M, 256);
-    st->status = reinterpret_cast<unsigned int*>(p);
-    e = cudaMemsetAsync(st->status, 0, sizeof(unsigned int), stream);
+    st->status = reinterpret_cast<unsigned int*>(p); p += 256;
+    st->roff_stale = reinterpret_cast<int*>(p);
+    e = cudaMemsetAsync(st->status, 0, 512, stream);
     if (e == cudaSuccess) e = lsq_prepare();
     if (e != cudaSuccess) return set_cuda_error(e, "lsq setup"), CUPSO_ERR_CUDA;
+    neg_pad_kernel<<<(st->Mp + 255) / 256, 256, 0, stream>>>(b, M, st->Mp, st->negb, st->roff);
     const float* Asrc = A;
     if (fp8) {
         row_absmax_kernel<<<M, 256, 0, stream>>>(A, M, D, amax);
-        scale_rows_kernel<<<1024, 256, 0, stream>>>(A, M, D, amax, st->sx, Ascaled, st->inv, b, st->bpad, st->Mp);
+        scale_rows_kernel<<<1024, 256, 0, stream>>>(A, M, D, amax, st->sx, Ascaled, st->inv, st->Mp);
         Asrc = Ascaled;
-    } else {
-        cudaMemsetAsync(st->bpad, 0, sizeof(float) * st->Mp, stream);
-        cudaMemcpyAsync(st->bpad, b, sizeof(float) * M, cudaMemcpyDeviceToDevice, stream);
     }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = lsq_convert(Asrc, (size_t)D, 1, M, D, st->Mp, st->Kp, fp8, 1.0f, st->Aq, stream);
@@ -143,14 +152,14 @@ int cupso::lsq_eval_tc(LsqTcState* st, const float* src, size_t si, size_t sk, i
 }
 
 int cupso::lsq_eval_tc_partials(LsqTcState* st, cudaStream_t stream) {
-    cudaError_t e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->part, st->status,
+    cudaError_t e = lsq_tc_launch(st->plan, st->roff, st->fp8 ? st->inv : nullptr, st->part, st->status,
                                   2000000000ll, stream);
     if (e != cudaSuccess) return set_cuda_error(e, "lsq tensor-core launch"), CUPSO_ERR_CUDA;
     return CUPSO_OK;
 }
 
 int cupso::lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t stream) {
-    cudaError_t e = lsq_tc_launch(st->plan, st->bpad, st->fp8 ? st->inv : nullptr, st->part, st->status,
+    cudaError_t e = lsq_tc_launch(st->plan, st->negb, st->fp8 ? st->inv : nullptr, st->part, st->status,
                                   2000000000ll, stream);
     const int used = lsq_tc_partials(st->plan);
     if (e == cudaSuccess) {
@@ -164,22 +173,24 @@ int cupso::lsq_eval_tc_operand(LsqTcState* st, int N, float* f, cudaStream_t str
 extern "C" int cupso_lsq_eval(const float* A_dev, const float* b_dev, int M, int D, const float* X_dev, int N,
                               int precision, float* f_out_dev, void* cuda_stream) {
     if (!A_dev || !b_dev || !X_dev || !f_out_dev || M < 1 || D < 1 || N < 1 ||
-        precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP8) {
+        precision < CUPSO_LSQ_FP32 || precision > CUPSO_LSQ_FP64) {
         set_last_error("cupso_lsq_eval: invalid argument");
         return CUPSO_ERR_INVALID_ARG;
     }
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (precision == CUPSO_LSQ_FP32) {
-        // the FP32 kernel reads X(i, d) = x[d * ldx + i]: transpose into a temporary
+    if (precision == CUPSO_LSQ_FP32 || precision == CUPSO_LSQ_FP64) {
+        // the FP32 and FP64 kernels read X(i, d) = x[d * ldx + i]: transpose into a temporary
         float* xd = nullptr;
         cudaError_t e = cudaMalloc(&xd, sizeof(float) * (size_t)N * D);
         if (e != cudaSuccess) return set_cuda_error(e, "cudaMalloc"), CUPSO_ERR_OOM;
         transpose_kernel<<<dim3((D + 31) / 32, (N + 31) / 32), dim3(32, 8), 0, st>>>(X_dev, N, D, xd);
         e = cudaGetLastError();
-        if (e == cudaSuccess) e = lsq_fp32_launch(xd, N, N, D, A_dev, b_dev, M, f_out_dev, st);
+        if (e == cudaSuccess)
+            e = precision == CUPSO_LSQ_FP32 ? lsq_fp32_launch(xd, N, N, D, A_dev, b_dev, M, f_out_dev, st)
+                                            : lsq_fp64_launch(xd, N, N, D, A_dev, b_dev, M, f_out_dev, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         cudaFree(xd);
-        if (e != cudaSuccess) return set_cuda_error(e, "lsq fp32"), CUPSO_ERR_CUDA;
+        if (e != cudaSuccess) return set_cuda_error(e, "lsq fp32/fp64"), CUPSO_ERR_CUDA;
         return CUPSO_OK;
     }
     if (!lsq_tc_available()) {

@@ -173,8 +173,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }  // namespace
 
 // Per-particle partial fitness over each block of 128 residual rows:
-//   part[h][i] = sum over m in 128 h .. 128 h + 127 of (sum_d X[i,d] A[m,d] / scale_m - b[m])^2
-// X: [Np][Kp] (K-major), A: [Mp][Kp], b: [Mp] (zero-padded rows contribute 0).
+//   part[h][i] = sum over m in 128 h .. 128 h + 127 of (sum_d X[i,d] A[m,d] / scale_m + off[m])^2
+// X: [Np][Kp] (K-major), A: [Mp][Kp], off: [Mp] (zero-padded rows contribute 0).
+// With X the positions and off = -b this is ||A x - b||^2; with X the
+// displacements x - c from a reference point c and off = A c - b (computed
+// accurately elsewhere) it is the same function, ||A (x - c) + (A c - b)||^2,
+// with the operand rounding scaled by |x - c| instead of |x|.
 // Launched in clusters of two CTAs. Pair c (of gridDim.x / 2) takes tiles
 // c, c + gridDim.x / 2, ... of the ceil(Np / 256) x (Mp / 256) tiles
 // (residual-row tile fastest). CTA r of the pair stages particle rows
@@ -184,7 +188,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 template <bool FP8>
 __global__ void __launch_bounds__(kTcThreads, 1)
     lsq_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA,
-                  const float* __restrict__ b, const float* __restrict__ inv_scale, int Mp, int KT, int Np,
+                  const float* __restrict__ off, const float* __restrict__ inv_scale, int Mp, int KT, int Np,
                   float* __restrict__ part, unsigned int* status, long long limit_ns) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base for the swizzled tiles (the same offset in both CTAs)
@@ -339,11 +343,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * BN + h * 128);
 #pragma unroll 1
             for (int c = 0; c < 128; c += 32) {
-                // b (and the FP8 scales) of these 32 rows, requested before the TMEM load
+                // the offsets (and the FP8 scales) of these 32 rows, requested before the TMEM load
                 float bb[32], sc[32];
 #pragma unroll
                 for (int e = 0; e < 32; e += 4) {
-                    const float4 t = __ldg(reinterpret_cast<const float4*>(b + m0 + c + e));
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(off + m0 + c + e));
                     bb[e] = t.x; bb[e + 1] = t.y; bb[e + 2] = t.z; bb[e + 3] = t.w;
                     if constexpr (FP8) {
                         const float4 z = __ldg(reinterpret_cast<const float4*>(inv_scale + m0 + c + e));
@@ -355,7 +359,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const float val = FP8 ? __fmul_rn(v[e], sc[e]) : v[e];
-                    const float r = __fsub_rn(val, bb[e]);
+                    const float r = __fadd_rn(val, bb[e]);
                     sum = __fmaf_rn(r, r, sum);
                 }
             }
@@ -490,6 +494,74 @@ __global__ void __launch_bounds__(256) lsq_fp32_kernel(const float* __restrict__
     if (threadIdx.x < 64 && i0 + threadIdx.x < N) f[i0 + threadIdx.x] = acc_i;
 }
 
+// FP64 least-squares fitness in the reference order, rounded once to FP32:
+// per particle, acc = 0; for m ascending: r = -b_m, r = r + A_md x_d for d
+// ascending (each product of two floats is exact in binary64, so the fma below
+// rounds exactly as the separate product and sum would), acc = acc + r * r
+// (square rounded, then added); f = acc rounded to float. Block = 64 particles
+// x all M, in tiles of 32 residual rows; thread (ty, tx) holds the 4 x 2 block
+// of (particle, row) residuals, each a chain over d in order; 64 threads then
+// add the tile's squares to their particle's sum in row order.
+__global__ void __launch_bounds__(256) lsq_fp64_kernel(const float* __restrict__ x, int ldx, int N, int D,
+                                                       const float* __restrict__ A, const float* __restrict__ b, int M,
+                                                       float* __restrict__ f) {
+    __shared__ __align__(16) float Xs[32][64 + 4];   // [d][particle]
+    __shared__ __align__(16) float As[32][32 + 4];   // [d][row]
+    __shared__ double Rs[64][32 + 1];                 // [particle][row]
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i0 = blockIdx.x * 64;
+    double acc_i = 0.0;                // the running sum of particle i0 + threadIdx.x (threads < 64)
+    for (int m0 = 0; m0 < M; m0 += 32) {
+        double r[4][2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int m = m0 + tx * 2 + c;
+                r[a][c] = m < M ? -(double)b[m] : 0.0;
+            }
+        for (int d0 = 0; d0 < D; d0 += 32) {
+            for (int e = threadIdx.x; e < 32 * 64; e += 256) {
+                const int dd = e / 64, col = e % 64;
+                const int d = d0 + dd;
+                Xs[dd][col] = (d < D && i0 + col < N) ? x[(size_t)d * ldx + i0 + col] : 0.0f;
+            }
+            for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+                const int dd = e / 32, col = e % 32;
+                const int d = d0 + dd;
+                As[dd][col] = (d < D && m0 + col < M) ? A[(size_t)(m0 + col) * D + d] : 0.0f;
+            }
+            __syncthreads();
+            const int dn = min(32, D - d0);
+            for (int dd = 0; dd < dn; ++dd) {
+                const float4 x4 = *reinterpret_cast<const float4*>(&Xs[dd][ty * 4]);
+                const float2 a2 = *reinterpret_cast<const float2*>(&As[dd][tx * 2]);
+                const double xv[4] = {(double)x4.x, (double)x4.y, (double)x4.z, (double)x4.w};
+                const double av[2] = {(double)a2.x, (double)a2.y};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) r[a][c] = __fma_rn(av[c], xv[a], r[a][c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) Rs[ty * 4 + a][tx * 2 + c] = r[a][c];
+        __syncthreads();
+        if (threadIdx.x < 64) {
+            const int mn = min(32, M - m0);
+            for (int c = 0; c < mn; ++c) {
+                const double rc = Rs[threadIdx.x][c];
+                acc_i = __dadd_rn(acc_i, __dmul_rn(rc, rc));
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 64 && i0 + threadIdx.x < N) f[i0 + threadIdx.x] = __double2float_rn(acc_i);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -586,7 +658,7 @@ bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int
     return true;
 }
 
-cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_scale, float* part,
+cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* off, const float* inv_scale, float* part,
                           unsigned int* status, long long limit_ns, cudaStream_t st) {
     const int ntiles = ((p.Np + 2 * BM - 1) / (2 * BM)) * (p.Mp / BN);
     const int pairs = std::max(1, std::min(ntiles, p.num_sms / 2));   // num_sms: the resident pairs x 2
@@ -606,9 +678,9 @@ cudaError_t lsq_tc_launch(const LsqTcPlan& p, const float* b, const float* inv_s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (p.fp8)
-        return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<true>, tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+        return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<true>, tx, ta, off, inv_scale, p.Mp, KT, p.Np, part, status,
                                   limit_ns);
-    return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<false>, tx, ta, b, inv_scale, p.Mp, KT, p.Np, part, status,
+    return cudaLaunchKernelEx(&cfg, lsq_tc_kernel<false>, tx, ta, off, inv_scale, p.Mp, KT, p.Np, part, status,
                               limit_ns);
 }
 
@@ -617,6 +689,12 @@ int lsq_tc_partials(const LsqTcPlan& p) { return p.Mp / 128; }
 cudaError_t lsq_fp32_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
                             cudaStream_t st) {
     lsq_fp32_kernel<<<(N + 63) / 64, 256, 0, st>>>(x, ldx, N, D, A, b, M, f);
+    return cudaGetLastError();
+}
+
+cudaError_t lsq_fp64_launch(const float* x, int ldx, int N, int D, const float* A, const float* b, int M, float* f,
+                            cudaStream_t st) {
+    lsq_fp64_kernel<<<(N + 63) / 64, 256, 0, st>>>(x, ldx, N, D, A, b, M, f);
     return cudaGetLastError();
 }
 

@@ -73,14 +73,17 @@ __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant_
 }
 
 // Step 2 fused with the tensor-core operand of the fitness product: the same
-// moves as lsq_move_kernel, and the new positions also land in Xq[i][k]
-// (row-major, row length Kp) rounded to BF16, or multiplied by sx and rounded
-// to FP8 e4m3 with saturation -- the bytes the separate conversion would
-// write, zero for i >= N and k >= D. A CTA takes tiles of 64 particles x 64
-// dimensions; the transposition goes through shared memory, so the swarm rows
-// and the operand rows are both written in whole segments. Lazy pbest: a
-// particle flagged in s.pflag improved in the previous iteration, so its
-// pbest_pos is the position loaded here; that row is written back on the way.
+// moves as lsq_move_kernel, and each new position's displacement from the
+// iteration's gbest_pos g (the reference point of the fitness, see
+// lsq_offset_kernel) lands in Xq[i][k] (row-major, row length Kp): x'_k - g_k,
+// computed in FP32, rounded to BF16, or multiplied by sx and rounded to FP8
+// e4m3 with saturation (|x' - g| <= max_pos - min_pos, so sx = 448 / (max_pos -
+// min_pos) never saturates); zero for i >= N and k >= D. A CTA takes tiles of
+// 64 particles x 64 dimensions; the transposition goes through shared memory,
+// so the swarm rows and the operand rows are both written in whole segments.
+// Lazy pbest: a particle flagged in s.pflag improved in the previous
+// iteration, so its pbest_pos is the position loaded here; that row is written
+// back on the way.
 template <bool FP8>
 __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constant__ SwarmDev s, void* __restrict__ Xq,
                                                             int Kp, float sx) {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constan
                         move_one(xj, vj, lane(Ph, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
                         set_lane(Xh, j, xj);
                         set_lane(Vh, j, vj);
-                        xn[h][j] = xj;
+                        xn[h][j] = __fsub_rn(xj, gd);
                     }
                     st4(s.x + off, Xh);
                     st4(s.v + off, Vh);
@@ -561,13 +564,75 @@ __global__ void __launch_bounds__(256) lsq_gram_kernel(const float* __restrict__
     }
 }
 
+// Error-free transformations in FP32 (Knuth's TwoSum; the product's error by
+// one fma), for the compensated dot product of lsq_offset_kernel.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// The residual offsets of the reference point: off[m] = sum_d A[m][d] g[d] -
+// b[m] for the gbest_pos g that the next iteration moves towards (the tensor-
+// core fitness of a displacement y = x - g is then sum_m (A y + off)_m^2 =
+// ||A x - b||^2). Each dot product is the compensated Dot2 of Ogita, Rump and
+// Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005):
+// as accurate as if accumulated in twice the FP32 precision, then rounded,
+// which an FP32 sum of ~D terms of |A x| ~ 1 would not be next to residuals
+// near the noise level. One warp per row: each lane keeps (sum, error) over
+// its columns, the lanes are combined by the same transformation in a fixed
+// tree, and the result, with b subtracted, is rounded once to float. Runs only
+// when *stale is set (the accept kernel sets it when gbest moved) and clears it.
+__global__ void __launch_bounds__(256) lsq_offset_kernel(const __grid_constant__ SwarmDev s,
+                                                         const float* __restrict__ A, const float* __restrict__ b,
+                                                         int M, float* __restrict__ off, int* __restrict__ stale) {
+    if (__ldcg(stale) == 0) return;
+    const uint32_t t = __ldcg(s.t_dev);
+    const float* g = s.G + (size_t)(t & 1u) * s.D;
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    for (int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); m < M; m += warps) {
+        const float* row = A + (size_t)m * s.D;
+        float p = 0.0f, c = 0.0f;   // running sum and its accumulated error
+        for (int d = lane; d < s.D; d += 32) {
+            const float a = __ldg(row + d), x = __ldcg(g + d);
+            const float h = __fmul_rn(a, x);
+            const float r = __fmaf_rn(a, x, -h);   // exact: a x = h + r
+            float q;
+            two_sum(p, h, p, q);
+            c = __fadd_rn(c, __fadd_rn(q, r));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float p2 = __shfl_xor_sync(0xFFFFFFFFu, p, o), c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+            // the same operands on both lanes of a pair, in a fixed order, so every lane ends with the same bits
+            const float lo_p = lane & o ? p2 : p, hi_p = lane & o ? p : p2;
+            const float lo_c = lane & o ? c2 : c, hi_c = lane & o ? c : c2;
+            float q;
+            two_sum(lo_p, hi_p, p, q);
+            c = __fadd_rn(__fadd_rn(lo_c, hi_c), q);
+        }
+        if (lane == 0) off[m] = __double2float_rn(((double)p + (double)c) - (double)b[m]);
+    }
+    // every block has read *stale above; the last one to finish clears it
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(reinterpret_cast<unsigned int*>(stale) + 1, 1u) == gridDim.x - 1) {
+            stale[1] = 0;
+            stale[0] = 0;
+        }
+    }
+}
+
 // Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
 // Warp c sums candidate c's chunks (in chunk order); thread 0 compares.
+// When it accepts one, *stale is set: the reference point of the tensor-core
+// fitness moved, so its residual offsets must be recomputed.
 __global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__ SwarmDev s,
                                                          const float* __restrict__ src,
                                                          const unsigned long long* __restrict__ top,
                                                          const double* __restrict__ partial, int chunks,
-                                                         double* __restrict__ g64) {
+                                                         double* __restrict__ g64, int* __restrict__ stale) {
     __shared__ double fsum[kCand];
     __shared__ int s_best;
     __shared__ double s_f;
@@ -607,6 +672,7 @@ __global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__
             const unsigned long long k = pack_key((float)s_f, (uint32_t)best);
             s.gkey[0] = k;
             s.gkey[1] = k;
+            if (stale) *stale = 1;
         } else {
             s.gkey[nxt] = s.gkey[cur];
         }
@@ -677,10 +743,17 @@ cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double
 
 // cand: [blocks * 16] + [16] scratch; partial: [16 * chunks]; flags: [Np / 4].
 // With Gm set (D <= M) the rescoring uses the FP64 Gram form.
+cudaError_t lsq_launch_offsets(const SwarmDev& s, const float* A, const float* b, int M, float* off, int* stale,
+                               int num_sms, cudaStream_t st) {
+    const int grid = std::max(1, std::min(num_sms * 4, (M + 7) / 8));
+    lsq_offset_kernel<<<grid, 256, 0, st>>>(s, A, b, M, off, stale);
+    return cudaGetLastError();
+}
+
 cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const float* part, int nparts, int all,
                                     bool lazy, const float* A, const float* b, int M, unsigned long long* cand,
                                     double* partial, int chunks, double* g64, unsigned int* flags, int grid,
-                                    const LsqGram& gram, cudaStream_t st) {
+                                    const LsqGram& gram, float* off, int* stale, int num_sms, cudaStream_t st) {
     const int nblk = lsq_cand_blocks(s.Np);
     unsigned long long* top = cand + (size_t)nblk * kCand;
     unsigned int* ticket = reinterpret_cast<unsigned int*>(top + kCand);
@@ -706,8 +779,10 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const f
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    lsq_accept_kernel<<<1, 512, 0, st>>>(s, src, top, partial, chunks, g64);
-    return cudaGetLastError();
+    lsq_accept_kernel<<<1, 512, 0, st>>>(s, src, top, partial, chunks, g64, stale);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !off) return e;
+    return lsq_launch_offsets(s, A, b, M, off, stale, num_sms, st);
 }
 
 // FP64 fitness of pbest_pos of the particle in `key` into *g64 (one candidate).

@@ -48,8 +48,8 @@ ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_
                  "cupso_get_state_fp64", "cupso_set_state_fp64")
 
 CUPSO_LSQ = 5
-CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8 = 0, 1, 2
-LSQ_PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2}
+CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8, CUPSO_LSQ_FP64 = 0, 1, 2, 3
+LSQ_PRECISIONS = {"fp32": 0, "bf16": 1, "fp8": 2, "fp64": 3}
 
 CUPSO_NOALLOC_MAX_N = 4194304
 CUPSO_NOALLOC_MAX_D = 1024

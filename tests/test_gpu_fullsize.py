@@ -95,16 +95,18 @@ def test_batch512_full_solve_sampled(P):
 def test_lsq_8192x1024_full_size(P, precision):
     """The benchmark's least-squares swarm (N = 8192, D = 1024, M = 4096) in the
     launch configuration it times (graph-captured iterations): gbest's FP64
-    fitness never increases and equals ||A g - b||^2 recomputed on the host in
-    FP64; sampled particles' pbest_fit equal the tensor-core fitness of their
-    pbest_pos (cupso_lsq_eval); every position stays within the bounds."""
+    fitness never increases and equals the oracle's ||A g - b||^2; sampled
+    improvers of the last iteration hold the oracle's displacement-form fitness
+    of their new position around that iteration's gbest; every position stays
+    within the bounds."""
     import torch
+    from oracle import oracle as O
     from paper_2205_01313_gb300 import workloads as Wl
+    from tests.test_gpu_lsq import _check_improvers_displacement
     cfg = Wl.lsq_config()
     N, D, M = cfg["N"], cfg["D"], cfg["M"]
     A, b, _ = Wl.lsq_problem(M, D, seed=cfg["seed"])
     dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
-    A64, b64 = A.astype(np.float64), b.astype(np.float64)
     lo, hi, vmax = cfg["bounds"]
     with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"]) as s:
         s.set_lsq(dA.data_ptr(), db.data_ptr(), M, precision)
@@ -114,25 +116,17 @@ def test_lsq_8192x1024_full_size(P, precision):
             g64 = s.gbest_f64()
             rc, fit, idx, pos = s.gbest()
             assert rc == P.CUPSO_OK and g64 <= prev
-            r = A64 @ pos.astype(np.float64) - b64
-            exact = float(r @ r)
+            exact = O.lsq_f64(A, b, pos)
             assert abs(g64 - exact) <= 1e-9 * exact
             prev = g64
+        before = s.state()
+        g = s.gbest()[3]
+        s.step(1)
         st = s.state()
     assert np.all((st["pos"] >= np.float32(lo)) & (st["pos"] <= np.float32(hi)))
     assert np.all(np.abs(st["v"]) <= np.float32(vmax))
-    rng = np.random.default_rng(3)
-    sample = rng.choice(N, 64, replace=False)
-    X = st["pbest_pos"][sample]
-    if precision == "fp8":
-        X = np.vstack([X, np.full((1, D), max(abs(lo), abs(hi)), np.float32)])   # the swarm's FP8 scale
-    dX = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    f = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
-    P.cupso_lsq_eval(dA.data_ptr(), db.data_ptr(), M, D, dX.data_ptr(), X.shape[0], P.LSQ_PRECISIONS[precision],
-                     f.data_ptr(), torch.cuda.current_stream().cuda_stream)
-    torch.cuda.synchronize()
-    got = f.cpu().numpy()[:len(sample)]
-    np.testing.assert_array_equal(st["pbest_fit"][sample].view(np.uint32), got.view(np.uint32))
+    assert (hi - lo) == 4.0      # the FP8 displacement scale of the tests, 448 / 4
+    _check_improvers_displacement(A, b, before, g, st, precision, sample=24)
 
 
 @pytest.mark.parametrize("mode", ["onchip", "sync", "tree"])

@@ -13,7 +13,9 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcupso_oracle.so")
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-          "-Wall", "-Wextra", "-D_DEFAULT_SOURCE"]
+          "-Wall", "-Wextra", "-D_DEFAULT_SOURCE",
+          # only ora_step_sync_threads (the all-cores baseline timing) is parallel
+          "-fopenmp"]
 
 
 def build_oracle(force: bool = False) -> str:

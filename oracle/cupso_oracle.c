@@ -503,6 +503,25 @@ int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_o
     return 0;
 }
 
+/* The same synchronous iterations with Steps 2-4 spread over `threads` host
+ * threads (OpenMP): particles are independent within an iteration (each reads
+ * only its own state and the gbest of the previous iteration), and Step 5 runs
+ * after all of them on one thread, so the result is identical to
+ * ora_step_sync's for any thread count. Used only to time the baseline on all
+ * host cores. */
+int ora_step_sync_threads(const ora_params* p, ora_state* s, int iters, int threads)
+{
+    if (check_params(p) || iters < 0 || threads < 1) return -1;
+    for (int k = 0; k < iters; ++k) {
+        uint32_t t = s->t + 1;
+#pragma omp parallel for num_threads(threads) schedule(static)
+        for (int i = 0; i < p->N; ++i) move_particle(p, s, t, i, NULL);
+        take_gbest(p, s, ora_argmin_pbest(p, s));           /* Step 5 */
+        s->t = t;
+    }
+    return 0;
+}
+
 int ora_step_serial(const ora_params* p, ora_state* s, int iters, const float* r_override)
 {
     if (check_params(p) || iters < 0) return -1;

@@ -122,6 +122,9 @@ int ora_init(const ora_params* p, ora_state* s);
  * non-null it holds r1,r2 for every (iteration, particle, dim):
  * r_override[((k*N + i)*D + d)*2 + {0,1}] for k < iters. */
 int ora_step_sync(const ora_params* p, ora_state* s, int iters, const float* r_override);
+/* ora_step_sync with Steps 2-4 on `threads` host threads (OpenMP over the
+ * independent particles; Step 5 serial): the same result for any count. */
+int ora_step_sync_threads(const ora_params* p, ora_state* s, int iters, int threads);
 
 /* The same, but with gbest updated inside the particle loop exactly as the
  * sequential Alg. 1 writes it (a later particle sees an earlier one's gbest). */

@@ -70,6 +70,8 @@ def lib():
         for name in ("ora_step_sync", "ora_step_serial"):
             getattr(L, name).argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int, f32p]
             getattr(L, name).restype = C.c_int
+        L.ora_step_sync_threads.argtypes = [C.POINTER(_Params), C.POINTER(_State), C.c_int, C.c_int]
+        L.ora_step_sync_threads.restype = C.c_int
         L.ora_move_one.argtypes = [C.POINTER(_Params), C.c_uint32, C.c_int, f32p, f32p, f32p, f32p, f32p, f32p]
         L.ora_move_one.restype = C.c_float
         L.ora_lsq_f32.argtypes = [f32p, f32p, C.c_int, C.c_int, f32p]
@@ -272,6 +274,12 @@ class Swarm:
         rc = lib().ora_step_sync(C.byref(self.p), C.byref(self.s), int(iters),
                                  _f32p(r) if r is not None else None)
         if rc != 0:
+            raise ValueError("oracle: invalid parameters")
+        return self
+
+    def step_sync_threads(self, iters, threads):
+        """step_sync with Steps 2-4 on `threads` host threads (identical result)."""
+        if lib().ora_step_sync_threads(C.byref(self.p), C.byref(self.s), int(iters), int(threads)) != 0:
             raise ValueError("oracle: invalid parameters")
         return self
 

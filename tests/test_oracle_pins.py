@@ -556,3 +556,16 @@ def test_lsq_disp_exact_on_representable_operands(fmt):
                 for m in range(5))
     assert O.lsq_disp(A, b, x, g, fmt, 1.0) == float(exact)
     assert O.lsq_f64(A, b, x) == float(exact)
+
+
+@pytest.mark.parametrize("fid", [1, 3])
+def test_threaded_sync_step_is_the_serial_one(fid):
+    """The all-cores baseline (Steps 2-4 over host threads, Step 5 serial) gives the
+    single-threaded oracle's state bit for bit, for any thread count."""
+    lo, hi, vmax = {1: (-5.12, 5.12, 1.024), 3: (-30.0, 30.0, 6.0)}[fid]
+    a = O.Swarm(3001, 9, lo, hi, vmax, 0.729, 1.49445, 1.49445, fid, 4).init().step_sync(6)
+    for threads in (1, 3, 8):
+        b = O.Swarm(3001, 9, lo, hi, vmax, 0.729, 1.49445, 1.49445, fid, 4).init().step_sync_threads(6, threads)
+        for k in ("pos", "v", "pbest_pos", "pbest_fit", "gbest_pos"):
+            np.testing.assert_array_equal(getattr(a, k).view(np.uint32), getattr(b, k).view(np.uint32))
+        assert a.gbest_idx == b.gbest_idx and a.t == b.t

@@ -33,11 +33,11 @@ METRIC = "particle·dim updates/s per fused iter vs HBM roofline; batched & BF16
 UNIT = "particle-dim updates/s"
 DEFAULT_WORKLOAD = "rosenbrock_1048576x64"
 FALLBACK_HBM_GBS = 6800.0
-# Every file compiled into the benchmark's kernel (sync_pipelined_kernel): a
+# Every file compiled into the benchmark's kernel (sync_panel_kernel): a
 # stored traffic figure is only used while their hash is unchanged.
-KERNEL_SOURCES = ["paper_2205_01313_gb300/csrc/kernels_pipelined.cu", "paper_2205_01313_gb300/csrc/stream_common.cuh",
+KERNEL_SOURCES = ["paper_2205_01313_gb300/csrc/kernels_panel.cu", "paper_2205_01313_gb300/csrc/stream_common.cuh",
                   "paper_2205_01313_gb300/csrc/cupso_device.cuh", "paper_2205_01313_gb300/csrc/cupso_internal.h"]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_sync_step_kernel.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_sync_panel_kernel.json")
 
 
 def parse():
@@ -58,7 +58,8 @@ def parse():
                     help="batch512: time the per-swarm plain path on every k-th swarm and scale up")
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto",
                                                        "queue", "queue_lock"])
-    ap.add_argument("--sync-kernel", default="auto", choices=["auto", "register", "pipelined3", "pipelined4"])
+    ap.add_argument("--sync-kernel", default="auto",
+                    choices=["auto", "register", "pipelined3", "pipelined4", "panel3", "panel6"])
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -265,7 +266,9 @@ def run_ours(a):
         if info["sync_tile"]:
             mode_used = "sync (tiled kernel, %d particles per tile)" % info["sync_tile"]
         else:
-            mode_used = "sync (%s kernel)" % ("pipelined, %d-stage ring" % info["sync_stages"]
+            mode_used = "sync (%s kernel)" % ("panel layout, %d-stage ring" % info["sync_stages"]
+                                              if info.get("sync_panel") else
+                                              "pipelined, %d-stage ring" % info["sync_stages"]
                                               if info["sync_stages"] else "register")
 
     for _ in range(a.warmup):

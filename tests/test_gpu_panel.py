@@ -1,0 +1,119 @@
+"""The SYNC step on the panel layout (state in panels of 8 dimensions) against
+the oracle, bit for bit: whole trajectories with captured graphs and a ragged
+particle count, a single step from an oracle-provided state, switches between
+the panel kernel and kernels on the dimension-major layout in the middle of a
+run (the state is converted between them), and checkpoint/resume through
+cupso_get_state / cupso_set_state while the state is in panels."""
+import numpy as np
+import pytest
+
+from tests.gpu_common import W, C12, BOUNDS, assert_state_equal, load_cupso, oracle_swarm, same_bits
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    return load_cupso()
+
+
+def _panel_swarm(P, fid, N, D, seed, kernel):
+    s = P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, seed)
+    s.set_mode("sync")
+    s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[kernel])
+    return s
+
+
+def test_panel_selection(P):
+    with P.Swarm(64, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:
+        i = s.info()
+        assert i["sync_panel"] == 1 and i["sync_stages"] == 6 and i["sync_ppt"] == 1
+    with P.Swarm(32, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # four panels: 3-stage ring
+        assert s.info()["sync_panel"] == 1 and s.info()["sync_stages"] == 3
+    with P.Swarm(16, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # two panels: 3-stage ring
+        assert s.info()["sync_panel"] == 1 and s.info()["sync_stages"] == 3
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
+        assert s.info()["sync_panel"] == 0 and s.info()["sync_ppt"] == 4
+    with P.Swarm(12, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # D % 8 != 0: dimension-major
+        assert s.info()["sync_panel"] == 0
+    with P.Swarm(8, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:    # one panel: no ring of panels
+        assert s.info()["sync_panel"] == 0
+
+
+@pytest.mark.parametrize("kernel,D", [("panel3", 16), ("panel3", 24), ("panel6", 40), ("panel6", 64)])
+@pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
+def test_panel_trajectory_bit_exact(P, fid, kernel, D):
+    N, T = 3000, 40            # 94 units of 32 particles, the last one ragged; padded to 3072
+    with _panel_swarm(P, fid, N, D, 3, kernel) as s:
+        assert s.info()["sync_panel"] == 1
+        s.step(1)
+        s.step(16)     # one captured graph (chunk 16)
+        s.step(23)     # graph + remainder
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 3).init().step_sync(T)
+    assert rc == P.CUPSO_OK and st["t"] == T
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("kernel", ["panel3", "panel6"])
+def test_panel_single_step_from_shared_state(P, kernel):
+    rng = np.random.default_rng(5)
+    fid, N, D = 3, 2500, 32
+    lo, hi, vmax = BOUNDS[fid]
+    pos = rng.uniform(lo, hi, (N, D)).astype(np.float32)
+    v = rng.uniform(-vmax, vmax, (N, D)).astype(np.float32)
+    pb = rng.uniform(lo, hi, (N, D)).astype(np.float32)
+    from oracle import oracle as O
+    pf = np.array([O.fitness(fid, pb[i]) for i in range(N)], np.float32)
+    ref = oracle_swarm(fid, N, D, 8)
+    ref.set_state(pos, v, pb, pf, 41)
+    with _panel_swarm(P, fid, N, D, 8, kernel) as s:
+        s.set_state(pos, v, pb, pf, 41)
+        s.step(1)
+        st = s.state()
+        rc, fit, idx, gpos = s.gbest()
+    ref.step_sync(1)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(gpos, ref.gbest_pos)
+
+
+def test_panel_mode_switches_mid_run(P):
+    """Panel and dimension-major kernels alternate (the state is converted, with
+    pbest rows pending across the switches): the oracle's trajectory."""
+    fid, N, D = 1, 4100, 40
+    plan = [("sync", "panel6", 3), ("tree", None, 2), ("sync", "panel3", 4), ("sync", "pipelined3", 2),
+            ("sync", "panel6", 17), ("queue", None, 1), ("sync", "register", 1), ("sync", "panel3", 2)]
+    total = 0
+    with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 6) as s:
+        for mode, kernel, n in plan:
+            s.set_mode(mode)
+            if kernel:
+                s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[kernel])
+            s.step(n)
+            total += n
+            if mode == "tree":
+                s.state()          # a state read while the layout is dimension-major
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 6).init().step_sync(total)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+def test_panel_checkpoint_resume(P):
+    """cupso_get_state while the state is in panels (rows pending), cupso_set_state
+    into a new handle, continue on the panel kernel: the oracle's trajectory."""
+    fid, N, D = 3, 5000, 32
+    with _panel_swarm(P, fid, N, D, 9, "panel6") as s:
+        s.step(7)
+        ck = s.state()
+    with _panel_swarm(P, fid, N, D, 9, "panel6") as s2:
+        s2.set_state(ck["pos"], ck["v"], ck["pbest_pos"], ck["pbest_fit"], ck["t"])
+        s2.step(9)
+        st = s2.state()
+        rc, fit, idx, pos = s2.gbest()
+    ref = oracle_swarm(fid, N, D, 9).init().step_sync(16)
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)

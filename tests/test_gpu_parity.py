@@ -37,8 +37,10 @@ def gpu_swarm(P, fid, N, D, seed, mode, bounds=None, w=W, c1=C12, c2=C12):
 
 
 def test_sync_kernel_selection(P):
-    with gpu_swarm(P, 3, 1 << 20, 16, 1, "sync") as s:
+    with gpu_swarm(P, 3, 1 << 20, 15, 1, "sync") as s:
         assert s.info()["sync_ppt"] == 4           # a large swarm: 4 particles per thread
+    with gpu_swarm(P, 3, 1 << 20, 16, 1, "sync_pipelined4") as s:
+        assert s.info()["sync_ppt"] == 4 and s.info()["sync_panel"] == 0
     with gpu_swarm(P, 3, 5000, 7, 1, "sync") as s:
         assert s.info()["sync_ppt"] == 1           # a small one: more, smaller units
         assert s.info()["sync_stages"] == 4
@@ -58,8 +60,8 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_tile"] == 0
     with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to ~896 per SM
         assert s.info()["sync_tile"] == 128
-    with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming
-        assert s.info()["sync_tile"] == 0
+    with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming (panel layout)
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 1
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])

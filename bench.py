@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--mode", default="sync", choices=["sync", "tree", "tree_unrolled", "async", "onchip", "auto",
                                                        "queue", "queue_lock"])
     ap.add_argument("--sync-kernel", default="auto",
-                    choices=["auto", "register", "pipelined3", "pipelined4", "panel3", "panel6"])
+                    choices=["auto", "register", "pipelined3", "pipelined4", "panel8", "panel16"])
     ap.add_argument("--cpu-iters", type=int, default=4, help="oracle iterations in the cpu_baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -266,7 +266,7 @@ def run_ours(a):
         if info["sync_tile"]:
             mode_used = "sync (tiled kernel, %d particles per tile)" % info["sync_tile"]
         else:
-            mode_used = "sync (%s kernel)" % ("panel layout, %d-stage ring" % info["sync_stages"]
+            mode_used = "sync (%s kernel)" % ("panels of %d dimensions, %d-stage ring" % (info["sync_panel"], info["sync_stages"])
                                               if info.get("sync_panel") else
                                               "pipelined, %d-stage ring" % info["sync_stages"]
                                               if info["sync_stages"] else "register")

@@ -141,15 +141,16 @@ typedef enum {
                                          the (dimension pair, particle) items spread over threads;
                                          AUTO uses it for D >= 8 up to about 896 particles per SM
                                          (224 for D > 64 without cos(2 pi x) in the fitness)     */
-    CUPSO_SYNC_KERNEL_PANEL3 = 5,     /* the state in panels of 8 dimensions (one 32-byte sector per
-                                         particle and panel), two threads per particle (4 dimensions
-                                         each), rows staged through shared memory 2 half panels
-                                         ahead; D % 8 == 0, D >= 16. A particle whose pbest is
-                                         pending skips its pbest load and writes the row instead:
-                                         20 bytes per particle-dimension whatever fraction of the
-                                         swarm improves                                           */
-    CUPSO_SYNC_KERNEL_PANEL6 = 6      /* the same, 5 half panels ahead; D >= 40. AUTO takes the panel
-                                         kernel wherever the pipelined one would run and D allows */
+    CUPSO_SYNC_KERNEL_PANEL8 = 5,     /* the state in panels of 8 dimensions (each particle's 8 values
+                                         of a panel contiguous), two threads per particle, rows staged
+                                         through shared memory; D % 8 == 0, D >= 16. A particle whose
+                                         pbest is pending skips its pbest load and writes the row
+                                         instead: 20 bytes per particle-dimension whatever fraction of
+                                         the swarm improves                                       */
+    CUPSO_SYNC_KERNEL_PANEL16 = 6     /* the same with panels of 16 dimensions (64 bytes per particle,
+                                         the granularity of HBM reads), four threads per particle;
+                                         D % 16 == 0, D >= 32. AUTO takes 8-dimension panels wherever
+                                         the pipelined kernel would run and D % 8 == 0            */
 } cupso_sync_kernel;
 
 typedef struct {
@@ -166,7 +167,7 @@ typedef struct {
     float fitness_ms;     /* mean fitness-phase time of the timed LSQ iterations, 0 if none */
     int fitness_timed;    /* how many iterations that mean covers */
     uint64_t device_bytes;/* device memory held by the handle        */
-    int sync_panel;       /* 1: the SYNC step runs the panel kernel (state in panels of 8 dimensions) */
+    int sync_panel;       /* panel width (8 or 16) when the SYNC step runs the panel kernel, else 0 */
 } cupso_info;
 
 /* Create a swarm and run Step 1 of Alg. 1 (iteration t = 0) on the device:

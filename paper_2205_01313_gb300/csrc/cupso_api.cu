@@ -76,7 +76,7 @@ struct cupso_swarm {
     int ppt_option = 0;             // particles per thread of the pipelined kernel, 0 = automatic
     bool pipelined_ok = false;      // shared-memory limit raised for the pipelined kernels
     bool panel_ok = false;          // the same for the panel kernels (D % 8 == 0)
-    bool panel = false;             // x, v, pb are in the panel layout (kernels_panel.cu)
+    int panel = 0;                  // x, v, pb in the panel layout of this width (kernels_panel.cu), 0: dimension-major
     bool lazy_pending = false;      // the pipelined step may have left pbest rows unwritten
     // least-squares fitness (fitness_id CUPSO_LSQ), set by cupso_set_lsq
     struct Lsq {
@@ -149,20 +149,40 @@ int sync_stages(const cupso_swarm* h) {
     return (h->pipelined_ok && pipelined_supported(want, h->D)) ? want : 0;
 }
 
-// Ring depth of the panel SYNC kernel (the state in the panel layout), or 0
-// when the dimension-major kernels run. AUTO takes it wherever the pipelined
-// kernel would run and D is a multiple of 8 (at least 40 for its deepest ring).
-int panel_stages(const cupso_swarm* h) {
-    if (h->fp64 || !h->panel_ok || h->fid == CUPSO_LSQ) return 0;
+// The panel SYNC kernel (the state in the panel layout) when it runs: its
+// panel width and ring depth (5 panels where the panels allow, else 3); width
+// 0 when the dimension-major kernels run. AUTO takes 8-dimension panels
+// wherever the pipelined kernel would run and D % 8 == 0. (16-dimension
+// panels avoid reading a skipped pbest row with its 64-byte neighbour, but
+// four lanes per particle spend more on the ordered fitness sum than that
+// saves: Rosenbrock 2^20 x 64 on one GB300, 0.259 vs 0.241 ms per iteration
+// at half the swarm improving, 0.253 vs 0.224 ms with none improving.)
+struct PanelCfg {
+    int width = 0, stages = 0;
+};
+PanelCfg panel_cfg(const cupso_swarm* h) {
+    PanelCfg c;
+    if (h->fp64 || !h->panel_ok || h->fid == CUPSO_LSQ) return c;
+    int widths[2] = {0, 0};
     switch (h->sync_kernel) {
-        case CUPSO_SYNC_KERNEL_PANEL3: return panel_supported(3, h->D) ? 3 : 0;
-        case CUPSO_SYNC_KERNEL_PANEL6: return panel_supported(6, h->D) ? 6 : 0;
+        case CUPSO_SYNC_KERNEL_PANEL8: widths[0] = 8; break;
+        case CUPSO_SYNC_KERNEL_PANEL16: widths[0] = 16; break;
         case CUPSO_SYNC_KERNEL_AUTO:
-            if (sync_tile(h)) return 0;
-            if (panel_supported(6, h->D)) return 6;
-            return panel_supported(3, h->D) ? 3 : 0;
-        default: return 0;
+            if (sync_tile(h)) return c;
+            widths[0] = 8;
+            break;
+        default: return c;
     }
+    for (int w : widths) {
+        if (!w) continue;
+        for (int st : {5, 3})
+            if (panel_supported(w, st, h->D)) {
+                c.width = w;
+                c.stages = st;
+                return c;
+            }
+    }
+    return c;
 }
 
 // Particles per thread of the pipelined kernel: 4 when the swarm has enough
@@ -177,10 +197,12 @@ int sync_ppt(const cupso_swarm* h) {
 }
 
 int sync_grid(const cupso_swarm* h) {
-    if (const int ps = panel_stages(h)) {
-        // persistent: warps pull units of 32 particles from a counter
-        const int units = h->Np / 32;
-        int g = h->grid_override > 0 ? h->grid_override : h->num_sms * panel_blocks_per_sm(ps, h->fid, h->D);
+    const PanelCfg pc = panel_cfg(h);
+    if (pc.width) {
+        // persistent: warps pull units of 128 / width particles from a counter
+        const int units = h->Np / (128 / pc.width);
+        int g = h->grid_override > 0 ? h->grid_override
+                                     : h->num_sms * panel_blocks_per_sm(pc.width, pc.stages, h->fid, h->D);
         const int useful = (units + kBlock / 32 - 1) / (kBlock / 32);
         return g < useful ? g : useful;
     }
@@ -306,7 +328,8 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
     switch (mode) {
         case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
-            if (const int ps = panel_stages(h)) return launch_sync_panel(h->dev, h->fid, ps, sync_grid(h), st);
+            const PanelCfg pc = panel_cfg(h);
+            if (pc.width) return launch_sync_panel(h->dev, h->fid, pc.width, pc.stages, sync_grid(h), st);
             if (const int P = sync_tile(h))
                 return launch_sync_tiled(h->dev, h->fid, P, tiled_grid(h, P), st);
             const int stages = sync_stages(h);
@@ -328,7 +351,7 @@ int ensure_materialized(cupso_swarm* h) {
     cudaError_t e;
     if (h->panel) {
         const int grid = std::max(1, std::min(h->num_sms * 8, (h->Np + kBlock - 1) / kBlock));
-        e = launch_materialize_panel(h->dev, grid, h->stream);
+        e = launch_materialize_panel(h->dev, h->panel, grid, h->stream);
     } else {
         const int grid = std::max(1, std::min(h->num_sms * 8, (h->Np / 4 + kBlock - 1) / kBlock));
         e = launch_materialize(h->dev, grid, h->stream);
@@ -339,11 +362,12 @@ int ensure_materialized(cupso_swarm* h) {
 }
 
 // Puts pos, v and pbest_pos in the layout the next kernel reads: the panel
-// layout for the panel SYNC kernel, the dimension-major one for every other
-// kernel. Pending pbest rows are written back first; each array goes through
-// a temporary copy (one array's size, freed again). Not for stream capture.
-int ensure_layout(cupso_swarm* h, bool want_panel) {
-    if (h->fp64 || h->panel == want_panel) return CUPSO_OK;
+// layout of width `want` (8 or 16) for the panel SYNC kernel, the
+// dimension-major one (want 0) for every other kernel. Pending pbest rows are
+// written back first; each array goes through a temporary copy (one array's
+// size, freed again). Not for stream capture.
+int ensure_layout(cupso_swarm* h, int want) {
+    if (h->fp64 || h->panel == want) return CUPSO_OK;
     int rc = ensure_materialized(h);
     if (rc) return rc;
     drop_graph(h);
@@ -353,14 +377,19 @@ int ensure_layout(cupso_swarm* h, bool want_panel) {
     float* arrays[3] = {h->dev.x, h->dev.v, h->dev.pb};
     const int grid = h->num_sms * 8;
     cudaError_t e = cudaSuccess;
-    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
-        e = launch_relayout(arrays[a], static_cast<float*>(tmp), h->D, h->Np, want_panel, grid, h->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(arrays[a], tmp, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    // at most two passes: out of the current panel width, into the wanted one
+    const int passes[2][2] = {{h->panel, 0}, {want, 1}};
+    for (const auto& ps : passes) {
+        if (!ps[0]) continue;
+        for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+            e = launch_relayout(arrays[a], static_cast<float*>(tmp), h->D, h->Np, ps[0], ps[1] != 0, grid, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(arrays[a], tmp, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(e, "relayout");
-    h->panel = want_panel;
+    h->panel = want;
     return CUPSO_OK;
 }
 
@@ -502,7 +531,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     int cl = 0, per = 0;
     h->onchip_cluster = (fid != CUPSO_LSQ && onchip_fits(N, D, &cl, &per)) ? cl : 0;
     h->pipelined_ok = prepare_pipelined(D) == cudaSuccess;
-    h->panel_ok = fid != CUPSO_LSQ && D % 8 == 0 && panel_supported(3, D) && prepare_panel(D) == cudaSuccess;
+    h->panel_ok = fid != CUPSO_LSQ && panel_supported(8, 3, D) && prepare_panel(D) == cudaSuccess;
     cudaGetLastError();
 
     e = cudaMemsetAsync(base + o_words, 0, 128, h->stream);
@@ -742,7 +771,7 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             drop_graph(h);
             return CUPSO_OK;
         case CUPSO_OPT_SYNC_KERNEL:
-            if (value < CUPSO_SYNC_KERNEL_AUTO || value > CUPSO_SYNC_KERNEL_PANEL6)
+            if (value < CUPSO_SYNC_KERNEL_AUTO || value > CUPSO_SYNC_KERNEL_PANEL16)
                 return fail(CUPSO_ERR_INVALID_ARG, "unknown sync kernel%s");
             h->sync_kernel = (int)value;
             drop_graph(h);
@@ -807,13 +836,13 @@ int cupso_step(cupso_handle h, int iters) {
         h->t_host += (uint32_t)iters;
         return CUPSO_OK;
     }
-    const bool panel = !h->fp64 && mode == CUPSO_MODE_SYNC && panel_stages(h) > 0;
+    const int panel = (!h->fp64 && mode == CUPSO_MODE_SYNC) ? panel_cfg(h).width : 0;
     {
         const int rc = ensure_layout(h, panel);
         if (rc) return rc;
     }
     const bool pipelined =
-        panel || (!h->fp64 && mode == CUPSO_MODE_SYNC && sync_tile(h) == 0 && sync_stages(h) > 0);
+        panel != 0 || (!h->fp64 && mode == CUPSO_MODE_SYNC && sync_tile(h) == 0 && sync_stages(h) > 0);
     if (!pipelined) {
         const int rc = ensure_materialized(h);
         if (rc) return rc;
@@ -891,9 +920,10 @@ int cupso_get_state(cupso_handle h, float* pos, float* v, float* pbest_pos, floa
         if (!outs[a]) continue;
         stage.resize(D * Np);
         CUPSO_CUDA(cudaMemcpy(stage.data(), srcs[a], sizeof(float) * D * Np, cudaMemcpyDeviceToHost), "cudaMemcpy");
-        if (h->panel) {   // element (d, i) at ((d / 8) Np + i) 8 + d % 8
+        if (h->panel) {   // element (d, i) at ((d / W) Np + i) W + d % W
+            const size_t W = (size_t)h->panel;
             for (size_t i = 0; i < N; ++i)
-                for (size_t d = 0; d < D; ++d) outs[a][i * D + d] = stage[((d >> 3) * Np + i) * 8 + (d & 7)];
+                for (size_t d = 0; d < D; ++d) outs[a][i * D + d] = stage[((d / W) * Np + i) * W + (d % W)];
         } else {
             for (size_t i = 0; i < N; ++i)
                 for (size_t d = 0; d < D; ++d) outs[a][i * D + d] = stage[d * Np + i];
@@ -925,7 +955,7 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
     CUPSO_CUDA(cudaMemcpy(h->dev.pf, pf.data(), sizeof(float) * Np, cudaMemcpyHostToDevice), "cudaMemcpy");
     CUPSO_CUDA(cudaMemset(h->dev.pflag, 0, Np), "cudaMemset");
     h->lazy_pending = false;
-    h->panel = false;   // uploaded dimension-major
+    h->panel = 0;   // uploaded dimension-major
     if (h->lsq && lsq_approx(h->lsq->precision)) {
         // the given pbest_fit are approximate values: gbest only from FP64 rescoring
         CUPSO_CUDA(lsq_reset_gbest(h, h->dev.pf, t, h->stream), "lsq gbest");
@@ -1151,11 +1181,11 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
         info->sync_grid = tile ? std::min(tiled_grid(h, tile), (h->N + tile - 1) / tile) : sync_grid(h);
         info->async_grid = async_grid(h);
         info->onchip_cluster = h->onchip_cluster;
-        const int ps = panel_stages(h);
-        info->sync_stages = ps ? ps : (tile ? 0 : sync_stages(h));
-        info->sync_ppt = ps ? 1 : ((!tile && sync_stages(h)) ? sync_ppt(h) : 0);
-        info->sync_tile = ps ? 0 : tile;
-        info->sync_panel = ps ? 1 : 0;
+        const PanelCfg pc = panel_cfg(h);
+        info->sync_stages = pc.width ? pc.stages : (tile ? 0 : sync_stages(h));
+        info->sync_ppt = pc.width ? 1 : ((!tile && sync_stages(h)) ? sync_ppt(h) : 0);
+        info->sync_tile = pc.width ? 0 : tile;
+        info->sync_panel = pc.width;
     }
     info->fitness_ms = 0.0f;
     info->fitness_timed = 0;

@@ -48,14 +48,16 @@ cudaError_t launch_batch_step(const BatchDev& b, int stages, int minb, int grid,
 cudaError_t launch_batch_init(const BatchDev& b, int grid, cudaStream_t st);
 
 // Fused SYNC step on the panel layout (kernels_panel.cu): element (d, i) of
-// x, v, pb at ((d / 8) * Np + i) * 8 + d % 8.
-bool panel_supported(int stages, int D);
+// x, v, pb at ((d / W) * Np + i) * W + d % W, panel width W = 8 or 16, ring
+// depth 3 or 5 panels.
+bool panel_supported(int width, int stages, int D);
 cudaError_t prepare_panel(int D);
-int panel_blocks_per_sm(int stages, int fid, int D);
-cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int stages, int grid, cudaStream_t st);
-cudaError_t launch_materialize_panel(const SwarmDev& s, int grid, cudaStream_t st);
-// dst = src in the other layout (dimension-major <-> panel); D % 8 == 0.
-cudaError_t launch_relayout(const float* src, float* dst, int D, int Np, bool to_panel, int grid, cudaStream_t st);
+int panel_blocks_per_sm(int width, int stages, int fid, int D);
+cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int width, int stages, int grid, cudaStream_t st);
+cudaError_t launch_materialize_panel(const SwarmDev& s, int width, int grid, cudaStream_t st);
+// dst = src in the other layout (dimension-major <-> panel of width W); D % W == 0.
+cudaError_t launch_relayout(const float* src, float* dst, int D, int Np, int width, bool to_panel, int grid,
+                            cudaStream_t st);
 
 // Least-squares fitness (kernels_lsq.cu).
 struct LsqTcPlan {

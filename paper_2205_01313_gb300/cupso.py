@@ -37,7 +37,7 @@ CUPSO_OPT_GRID = 5
 CUPSO_OPT_SYNC_KERNEL = 6
 CUPSO_OPT_TIME_FITNESS = 7
 CUPSO_OPT_PARTICLES_PER_THREAD = 8
-SYNC_KERNELS = {"auto": 0, "register": 1, "pipelined3": 2, "pipelined4": 3, "tiled": 4, "panel3": 5, "panel6": 6}
+SYNC_KERNELS = {"auto": 0, "register": 1, "pipelined3": 2, "pipelined4": 3, "tiled": 4, "panel8": 5, "panel16": 6}
 CUPSO_OPT_FAULT_HOLD_LOCK = 100
 
 # The names the library must export (every function of include/cupso.h).

@@ -1,4 +1,4 @@
-"""The SYNC step on the panel layout (state in panels of 8 dimensions) against
+"""The SYNC step on the panel layout (state in panels of 8 or 16 dimensions) against
 the oracle, bit for bit: whole trajectories with captured graphs and a ragged
 particle count, a single step from an oracle-provided state, switches between
 the panel kernel and kernels on the dimension-major layout in the middle of a
@@ -25,27 +25,32 @@ def _panel_swarm(P, fid, N, D, seed, kernel):
 
 
 def test_panel_selection(P):
+    """AUTO: 8-dimension panels, the deepest ring the panels allow (5, else 3);
+    none for D % 8 != 0 or a single panel. 16-dimension panels on request."""
+    want = {64: (8, 5), 32: (8, 5), 48: (8, 5), 16: (8, 3), 24: (8, 3), 40: (8, 5), 12: (0, None), 8: (0, None)}
+    for D, (width, stages) in want.items():
+        with P.Swarm(D, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:
+            i = s.info()
+            assert i["sync_panel"] == width, D
+            if width:
+                assert i["sync_stages"] == stages and i["sync_ppt"] == 1, D
     with P.Swarm(64, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:
-        i = s.info()
-        assert i["sync_panel"] == 1 and i["sync_stages"] == 6 and i["sync_ppt"] == 1
-    with P.Swarm(32, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # four panels: 3-stage ring
-        assert s.info()["sync_panel"] == 1 and s.info()["sync_stages"] == 3
-    with P.Swarm(16, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # two panels: 3-stage ring
-        assert s.info()["sync_panel"] == 1 and s.info()["sync_stages"] == 3
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["panel16"])
+        assert s.info()["sync_panel"] == 16 and s.info()["sync_stages"] == 5
+    with P.Swarm(32, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["panel16"])
+        assert s.info()["sync_panel"] == 16 and s.info()["sync_stages"] == 3
         s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS["pipelined4"])
         assert s.info()["sync_panel"] == 0 and s.info()["sync_ppt"] == 4
-    with P.Swarm(12, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:   # D % 8 != 0: dimension-major
-        assert s.info()["sync_panel"] == 0
-    with P.Swarm(8, 1 << 20, BOUNDS[3], W, C12, C12, 3, 1, mode="sync") as s:    # one panel: no ring of panels
-        assert s.info()["sync_panel"] == 0
 
 
-@pytest.mark.parametrize("kernel,D", [("panel3", 16), ("panel3", 24), ("panel6", 40), ("panel6", 64)])
+@pytest.mark.parametrize("kernel,D", [("panel8", 16), ("panel8", 40), ("panel16", 32), ("panel16", 64),
+                                      ("panel16", 48)])
 @pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
 def test_panel_trajectory_bit_exact(P, fid, kernel, D):
     N, T = 3000, 40            # 94 units of 32 particles, the last one ragged; padded to 3072
     with _panel_swarm(P, fid, N, D, 3, kernel) as s:
-        assert s.info()["sync_panel"] == 1
+        assert s.info()["sync_panel"] == int(kernel[5:])
         s.step(1)
         s.step(16)     # one captured graph (chunk 16)
         s.step(23)     # graph + remainder
@@ -57,7 +62,7 @@ def test_panel_trajectory_bit_exact(P, fid, kernel, D):
     assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
 
 
-@pytest.mark.parametrize("kernel", ["panel3", "panel6"])
+@pytest.mark.parametrize("kernel", ["panel8", "panel16"])
 def test_panel_single_step_from_shared_state(P, kernel):
     rng = np.random.default_rng(5)
     fid, N, D = 3, 2500, 32
@@ -82,9 +87,10 @@ def test_panel_single_step_from_shared_state(P, kernel):
 def test_panel_mode_switches_mid_run(P):
     """Panel and dimension-major kernels alternate (the state is converted, with
     pbest rows pending across the switches): the oracle's trajectory."""
-    fid, N, D = 1, 4100, 40
-    plan = [("sync", "panel6", 3), ("tree", None, 2), ("sync", "panel3", 4), ("sync", "pipelined3", 2),
-            ("sync", "panel6", 17), ("queue", None, 1), ("sync", "register", 1), ("sync", "panel3", 2)]
+    fid, N, D = 1, 4100, 64
+    plan = [("sync", "panel16", 3), ("sync", "panel8", 2), ("tree", None, 2), ("sync", "panel8", 4),
+            ("sync", "pipelined3", 2), ("sync", "panel16", 17), ("queue", None, 1), ("sync", "register", 1),
+            ("sync", "panel8", 2)]
     total = 0
     with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 6) as s:
         for mode, kernel, n in plan:
@@ -106,10 +112,10 @@ def test_panel_checkpoint_resume(P):
     """cupso_get_state while the state is in panels (rows pending), cupso_set_state
     into a new handle, continue on the panel kernel: the oracle's trajectory."""
     fid, N, D = 3, 5000, 32
-    with _panel_swarm(P, fid, N, D, 9, "panel6") as s:
+    with _panel_swarm(P, fid, N, D, 9, "panel16") as s:
         s.step(7)
         ck = s.state()
-    with _panel_swarm(P, fid, N, D, 9, "panel6") as s2:
+    with _panel_swarm(P, fid, N, D, 9, "panel16") as s2:
         s2.set_state(ck["pos"], ck["v"], ck["pbest_pos"], ck["pbest_fit"], ck["t"])
         s2.step(9)
         st = s2.state()

@@ -61,7 +61,7 @@ def test_sync_kernel_selection(P):
     with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to ~896 per SM
         assert s.info()["sync_tile"] == 128
     with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming (panel layout)
-        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 1
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])

@@ -94,6 +94,10 @@ struct cupso_swarm {
         LsqGram gram;                    // FP64 A^T A etc. for the rescoring when D <= M
         void* gram_buf = nullptr;
         bool time_fitness = false;       // CUPSO_OPT_TIME_FITNESS
+        // the residual offsets of a new gbest are computed on a side stream while the
+        // next move runs (fork and join events, also inside captured graphs)
+        cudaStream_t side = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
         std::vector<cudaEvent_t> ev;     // pairs around the fitness phase
         double fitness_ms_sum = 0.0;
         int fitness_timed = 0;
@@ -274,8 +278,16 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         return lsq_launch_select_exact(h->dev, L.f, L.flags, grid, st);
     }
-    // the move writes the tensor-core operand too; the fitness is then the product alone
-    cudaError_t e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms, st);
+    // The residual offsets of the gbest this iteration moves towards (recomputed
+    // only if the last acceptance moved it) run beside the move, which is
+    // bound by HBM; the product, which adds them, waits for both. The move
+    // writes the tensor-core operand too; the fitness is then the product alone.
+    cudaError_t e = cudaEventRecord(L.fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(L.side, L.fork, 0);
+    if (e == cudaSuccess) e = lsq_launch_offsets(h->dev, L.A, L.b, L.M, L.tc.roff, L.tc.roff_stale, h->num_sms, L.side);
+    if (e == cudaSuccess) e = cudaEventRecord(L.join, L.side);
+    if (e == cudaSuccess) e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, L.join, 0);
     if (e != cudaSuccess) return e;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (L.time_fitness) {
@@ -290,9 +302,10 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
         L.ev.push_back(e0);
         L.ev.push_back(e1);
     }
+    // offsets for the gbest this iteration accepts: at the start of the next one
     return lsq_launch_gbest_approx(h->dev, nullptr, L.tc.part, lsq_tc_partials(L.tc.plan), 0, true, L.A, L.b, L.M,
                                    L.cand, L.partial, L.chunks, L.g64, reinterpret_cast<unsigned int*>(h->dev.pflag),
-                                   grid, L.gram, L.tc.roff, L.tc.roff_stale, h->num_sms, st);
+                                   grid, L.gram, nullptr, L.tc.roff_stale, h->num_sms, st);
 }
 
 // gbest of an approximate-fitness swarm from scratch, with `fit` (device, [Np])
@@ -981,6 +994,9 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     drop_graph(h);
     if (h->lsq) {
         for (cudaEvent_t ev : h->lsq->ev) cudaEventDestroy(ev);
+        if (h->lsq->fork) cudaEventDestroy(h->lsq->fork);
+        if (h->lsq->join) cudaEventDestroy(h->lsq->join);
+        if (h->lsq->side) cudaStreamDestroy(h->lsq->side);
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
         if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);
@@ -1020,6 +1036,9 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     CUPSO_CUDA(cudaMemsetAsync(L->cand + (size_t)nblk * 16 + 16, 0, sizeof(unsigned long long), h->stream),
                "cudaMemsetAsync");
     if (lsq_approx(precision)) {
+        CUPSO_CUDA(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        CUPSO_CUDA(cudaEventCreateWithFlags(&L->fork, cudaEventDisableTiming), "cudaEventCreate");
+        CUPSO_CUDA(cudaEventCreateWithFlags(&L->join, cudaEventDisableTiming), "cudaEventCreate");
         // FP8 scale of the operand: displacements between two points of the box
         // are at most max_pos - min_pos in magnitude
         const float span = h->dev.hi - h->dev.lo;
@@ -1223,6 +1242,9 @@ int cupso_destroy(cupso_handle h) {
     drop_graph(h);
     if (h->lsq) {
         for (cudaEvent_t ev : h->lsq->ev) cudaEventDestroy(ev);
+        if (h->lsq->fork) cudaEventDestroy(h->lsq->fork);
+        if (h->lsq->join) cudaEventDestroy(h->lsq->join);
+        if (h->lsq->side) cudaStreamDestroy(h->lsq->side);
         lsq_free_tc(&h->lsq->tc);
         if (h->lsq->buf) cudaFree(h->lsq->buf);
         if (h->lsq->gram_buf) cudaFree(h->lsq->gram_buf);

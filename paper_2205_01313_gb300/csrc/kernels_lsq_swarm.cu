@@ -313,29 +313,45 @@ __device__ __forceinline__ void warp_top(Item item, int n, unsigned long long* o
 
 // Step 4 with an approximate fitness, and the 16 lowest keys among the
 // particles that improved (all particles when `all` is set: the first gbest).
-// One particle per thread: each warp finds its 16 lowest, warp 0 the block's
-// 16 of those (cand[block][16]); the last block to finish merges all blocks'
-// lists into top[16], ascending (kKeyNone where fewer). The fitness comes from
-// `fit`, or, with `part`, as the sum of the product's nparts partial sums in
-// their order.
-__global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
-                                                                 const float* __restrict__ fit,
-                                                                 const float* __restrict__ part, int nparts,
-                                                                 int all,
-                                                                 unsigned long long* __restrict__ cand,
-                                                                 unsigned int* __restrict__ flags,
-                                                                 unsigned long long* __restrict__ top,
-                                                                 unsigned int* __restrict__ ticket) {
-    __shared__ unsigned long long wtop[kBlock / 32][kCand];
+// One particle per thread, blocks of kSel threads (small, so that even a swarm
+// of a few thousand particles spreads over most SMs): each warp finds its 16
+// lowest, warp 0 the block's 16 of those (cand[block][16]); the last block to
+// finish merges all blocks' lists into top[16], ascending (kKeyNone where
+// fewer): a k-way merge of the sorted lists for up to kMergeLists * kSel
+// blocks, else a selection over all their keys (staged in shared memory when
+// they fit). The fitness comes from `fit`, or, with `part`, as the sum of the
+// product's nparts partial sums in their order.
+constexpr int kSel = 64;
+constexpr int kMergeLists = 4;     // block lists per thread of the last block's k-way merge
+constexpr int kMergeSmem = 4096;
+__global__ void __launch_bounds__(kSel) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
+                                                               const float* __restrict__ fit,
+                                                               const float* __restrict__ part, int nparts,
+                                                               int all,
+                                                               unsigned long long* __restrict__ cand,
+                                                               unsigned int* __restrict__ flags,
+                                                               unsigned long long* __restrict__ top,
+                                                               unsigned int* __restrict__ ticket) {
+    extern __shared__ unsigned long long merge_buf[];   // the last block: all blocks' lists, if they fit
+    __shared__ unsigned long long wtop[kSel / 32][kCand];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t i = (uint32_t)blockIdx.x * kBlock + threadIdx.x;
+    const uint32_t i = (uint32_t)blockIdx.x * kSel + threadIdx.x;
     unsigned long long key = kKeyNone;
     bool nan = false;
     if (i < (uint32_t)s.Np) {
         float f = 0.0f;
         if (part) {
-            for (int k = 0; k < nparts; ++k) f = __fadd_rn(f, __ldcg(part + (size_t)k * s.Np + i));
+            // in k order; eight loads in flight at a time
+            int k = 0;
+            for (; k + 8 <= nparts; k += 8) {
+                float v[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[e] = __ldcg(part + (size_t)(k + e) * s.Np + i);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f = __fadd_rn(f, v[e]);
+            }
+            for (; k < nparts; ++k) f = __fadd_rn(f, __ldcg(part + (size_t)k * s.Np + i));
         } else {
             f = fit[i];
         }
@@ -352,7 +368,7 @@ __global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_co
         nan = real && (f != f);
     }
     if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
-    constexpr int kPerLane = kBlock / 32 * kCand / 32;   // the block's warp lists, over warp 0's lanes
+    constexpr int kPerLane = kSel / 32 * kCand / 32;   // the block's warp lists, over warp 0's lanes
     warp_top<1>([&](int) { return key; }, 1, wtop[warp]);
     __syncthreads();
     const unsigned long long* flat = &wtop[0][0];
@@ -365,13 +381,140 @@ __global__ void __launch_bounds__(kBlock) lsq_select_cand_kernel(const __grid_co
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int n = (int)gridDim.x * kCand;
+    const int nb = (int)gridDim.x, n = nb * kCand;
     const int tid = (int)threadIdx.x;
-    const int per = tid < n ? (n - tid + kBlock - 1) / kBlock : 0;   // this thread's entries: tid + kBlock q
-    warp_top<0>([&](int q) { return __ldcg(cand + tid + (size_t)kBlock * q); }, per, wtop[warp]);
-    __syncthreads();
-    if (warp == 0) warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, top);
+    if (nb <= kMergeLists * kSel) {
+        // k-way merge of the blocks' ascending lists: thread t owns lists
+        // t, t + kSel, ...; each round the smallest head over the block is
+        // taken and its list advances (keys are unique, so one owner moves)
+        __shared__ unsigned long long wmin[kSel / 32];
+        int head[kMergeLists];
+        unsigned long long hv[kMergeLists];
+#pragma unroll
+        for (int q = 0; q < kMergeLists; ++q) {
+            const int b = tid + kSel * q;
+            head[q] = 0;
+            hv[q] = b < nb ? __ldcg(cand + (size_t)b * kCand) : kKeyNone;
+        }
+        for (int r = 0; r < kCand; ++r) {
+            unsigned long long lm = kKeyNone;
+#pragma unroll
+            for (int q = 0; q < kMergeLists; ++q) lm = hv[q] < lm ? hv[q] : lm;
+            const unsigned long long wm = warp_min_u64(lm);
+            if (lane == 0) wmin[warp] = wm;
+            __syncthreads();
+            unsigned long long m = wmin[0];
+#pragma unroll
+            for (int w = 1; w < kSel / 32; ++w) m = wmin[w] < m ? wmin[w] : m;
+            __syncthreads();
+            if (tid == 0) top[r] = m;
+            if (m != kKeyNone) {
+#pragma unroll
+                for (int q = 0; q < kMergeLists; ++q)
+                    if (hv[q] == m) {
+                        const int b = tid + kSel * q;
+                        ++head[q];
+                        hv[q] = head[q] < kCand ? __ldcg(cand + (size_t)b * kCand + head[q]) : kKeyNone;
+                    }
+            }
+        }
+    } else {
+        // many blocks: a selection over all their keys
+        const bool staged = n <= kMergeSmem;
+        if (staged) {
+            for (int e = tid; e < n; e += kSel) merge_buf[e] = __ldcg(cand + e);
+            __syncthreads();
+        }
+        const int per = tid < n ? (n - tid + kSel - 1) / kSel : 0;   // this thread's entries: tid + kSel q
+        warp_top<0>([&](int q) {
+            const size_t e = (size_t)tid + (size_t)kSel * q;
+            return staged ? merge_buf[e] : __ldcg(cand + e);
+        }, per, wtop[warp]);
+        __syncthreads();
+        if (warp == 0) warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, top);
+    }
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
+// Run by the last block of the rescoring kernel (any block size that is a
+// multiple of 32): warp w sums candidates w, w + warps, ... (lane l takes
+// chunks l, l + 32, ... in order, then a fixed butterfly); thread 0 compares.
+// When it accepts one, *stale is set: the reference point of the tensor-core
+// fitness moved, so its residual offsets must be recomputed.
+__device__ void accept_best(const SwarmDev& s, const float* __restrict__ src, const unsigned long long* __restrict__ top,
+                            const double* __restrict__ partial, int chunks, double* __restrict__ g64,
+                            int* __restrict__ stale) {
+    __shared__ double fsum[kCand];
+    __shared__ int s_best;
+    __shared__ double s_f;
+    const uint32_t t_prev = __ldcg(s.t_dev);
+    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    for (int c = warp; c < kCand; c += nw) {
+        double f = 0.0;
+        for (int h = lane; h < chunks; h += 32) f += __ldcg(partial + (size_t)c * chunks + h);
+        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
+        if (lane == 0) fsum[c] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int best = -1;
+        double bf = 0.0;
+        for (int c = 0; c < kCand; ++c) {
+            const unsigned long long k = top[c];
+            if (k == kKeyNone) break;
+            const double f = fsum[c];
+            const int i = (int)(k & 0xFFFFFFFFull);
+            if (f == f && (best < 0 || f < bf || (f == bf && i < best))) {
+                best = i;
+                bf = f;
+            }
+        }
+        s_best = (best >= 0 && bf < *g64) ? best : -1;
+        s_f = bf;
+    }
+    __syncthreads();
+    const int best = s_best;
+    for (int d = threadIdx.x; d < s.D; d += blockDim.x)
+        s.G[(size_t)nxt * s.D + d] = best >= 0 ? __ldcg(src + (size_t)d * s.Np + best) : s.G[(size_t)cur * s.D + d];
+    if (threadIdx.x == 0) {
+        if (best >= 0) {
+            *g64 = s_f;
+            const unsigned long long k = pack_key((float)s_f, (uint32_t)best);
+            s.gkey[0] = k;
+            s.gkey[1] = k;
+            if (stale) *stale = 1;
+        } else {
+            s.gkey[nxt] = s.gkey[cur];
+        }
+        *s.t_dev = t_prev + 1u;
+    }
+}
+
+// The rescoring blocks' hand-off: the last block to finish (ticket) runs the
+// acceptance; a null ticket skips it (a plain FP64 evaluation).
+struct AcceptArgs {
+    unsigned int* ticket;
+    const float* src;
+    const unsigned long long* top;
+    const double* partial;
+    int chunks;
+    double* g64;
+    int* stale;
+};
+
+__device__ __forceinline__ void last_block_accepts(const SwarmDev& s, const AcceptArgs& a) {
+    if (!a.ticket) return;
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    accept_best(s, a.src, a.top, a.partial, a.chunks, a.g64, a.stale);
+    if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
 // FP64 rescoring: partial[c][chunk] = sum over rows m of the chunk of
@@ -383,7 +526,8 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
                                                           const float* __restrict__ src,
                                                           const float* __restrict__ A, const float* __restrict__ b,
                                                           int M, const unsigned long long* __restrict__ top,
-                                                          int rows_per_chunk, double* __restrict__ partial) {
+                                                          int rows_per_chunk, double* __restrict__ partial,
+                                                          const AcceptArgs acc_args) {
     extern __shared__ double xc[];            // [D]
     __shared__ double wsum[8];
     const int c = blockIdx.x, chunk = blockIdx.y;
@@ -391,6 +535,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
     double* out = partial + ((size_t)c * gridDim.y + chunk);
     if (key == kKeyNone) {
         if (threadIdx.x == 0) *out = __longlong_as_double(0x7FF8000000000000ll);   // no candidate
+        last_block_accepts(s, acc_args);
         return;
     }
     const uint32_t i = (uint32_t)(key & 0xFFFFFFFFull);
@@ -423,6 +568,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_kernel(const __grid_constant_
         for (int w = 0; w < 8; ++w) tot += wsum[w];
         *out = tot;
     }
+    last_block_accepts(s, acc_args);
 }
 
 // FP64 Gram form of the rescoring, for D <= M: with Gm = A^T A, c = A^T b,
@@ -442,7 +588,8 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
                                                                const double* __restrict__ cvec, double bb,
                                                                const unsigned long long* __restrict__ top,
                                                                int pairs_per_chunk, int chunks,
-                                                               double* __restrict__ partial) {
+                                                               double* __restrict__ partial,
+                                                               const AcceptArgs acc_args) {
     extern __shared__ double xg[];            // [4][D]
     __shared__ double wsum[8][4];
     const int grp = blockIdx.x, chunk = blockIdx.y;
@@ -523,6 +670,7 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
         partial[(size_t)(grp * 4 + q) * chunks + chunk] =
             live[q] ? tot : __longlong_as_double(0x7FF8000000000000ll);
     }
+    last_block_accepts(s, acc_args);
 }
 
 // Gm = A^T A (D x D), cvec = A^T b, in FP64 (one-time setup). 32 x 32 output
@@ -586,21 +734,49 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 __global__ void __launch_bounds__(256) lsq_offset_kernel(const __grid_constant__ SwarmDev s,
                                                          const float* __restrict__ A, const float* __restrict__ b,
                                                          int M, float* __restrict__ off, int* __restrict__ stale) {
+    extern __shared__ float gs[];   // gbest_pos [D]
     if (__ldcg(stale) == 0) return;
     const uint32_t t = __ldcg(s.t_dev);
     const float* g = s.G + (size_t)(t & 1u) * s.D;
+    const int D = s.D;
+    for (int d = threadIdx.x; d < D; d += blockDim.x) gs[d] = __ldcg(g + d);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    // rows as float4 when they are 16-byte aligned: eight loads in flight per lane
+    const bool vec = (D & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
     for (int m = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); m < M; m += warps) {
-        const float* row = A + (size_t)m * s.D;
+        const float* row = A + (size_t)m * D;
         float p = 0.0f, c = 0.0f;   // running sum and its accumulated error
-        for (int d = lane; d < s.D; d += 32) {
-            const float a = __ldg(row + d), x = __ldcg(g + d);
+        auto term = [&](float a, float x) {
             const float h = __fmul_rn(a, x);
             const float r = __fmaf_rn(a, x, -h);   // exact: a x = h + r
             float q;
             two_sum(p, h, p, q);
             c = __fadd_rn(c, __fadd_rn(q, r));
+        };
+        if (vec) {
+            const int nv = D >> 2;
+            for (int v0 = 0; v0 < nv; v0 += 256) {
+                float4 a4[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int v = v0 + lane + 32 * k;
+                    a4[k] = v < nv ? __ldg(reinterpret_cast<const float4*>(row) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int v = v0 + lane + 32 * k;
+                    if (v < nv) {
+                        term(a4[k].x, gs[4 * v]);
+                        term(a4[k].y, gs[4 * v + 1]);
+                        term(a4[k].z, gs[4 * v + 2]);
+                        term(a4[k].w, gs[4 * v + 3]);
+                    }
+                }
+            }
+        } else {
+            for (int d = lane; d < D; d += 32) term(__ldg(row + d), gs[d]);
         }
         for (int o = 16; o > 0; o >>= 1) {
             const float p2 = __shfl_xor_sync(0xFFFFFFFFu, p, o), c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
@@ -621,62 +797,6 @@ __global__ void __launch_bounds__(256) lsq_offset_kernel(const __grid_constant__
             stale[1] = 0;
             stale[0] = 0;
         }
-    }
-}
-
-// Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
-// Warp c sums candidate c's chunks (in chunk order); thread 0 compares.
-// When it accepts one, *stale is set: the reference point of the tensor-core
-// fitness moved, so its residual offsets must be recomputed.
-__global__ void __launch_bounds__(512) lsq_accept_kernel(const __grid_constant__ SwarmDev s,
-                                                         const float* __restrict__ src,
-                                                         const unsigned long long* __restrict__ top,
-                                                         const double* __restrict__ partial, int chunks,
-                                                         double* __restrict__ g64, int* __restrict__ stale) {
-    __shared__ double fsum[kCand];
-    __shared__ int s_best;
-    __shared__ double s_f;
-    const uint32_t t_prev = __ldcg(s.t_dev);
-    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < kCand) {
-        double f = 0.0;   // lane l: chunks l, l + 32, ... in order; then a fixed tree
-        for (int h = lane; h < chunks; h += 32) f += partial[(size_t)warp * chunks + h];
-        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
-        if (lane == 0) fsum[warp] = f;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int best = -1;
-        double bf = 0.0;
-        for (int c = 0; c < kCand; ++c) {
-            const unsigned long long k = top[c];
-            if (k == kKeyNone) break;
-            const double f = fsum[c];
-            const int i = (int)(k & 0xFFFFFFFFull);
-            if (f == f && (best < 0 || f < bf || (f == bf && i < best))) {
-                best = i;
-                bf = f;
-            }
-        }
-        s_best = (best >= 0 && bf < *g64) ? best : -1;
-        s_f = bf;
-    }
-    __syncthreads();
-    const int best = s_best;
-    for (int d = threadIdx.x; d < s.D; d += blockDim.x)
-        s.G[(size_t)nxt * s.D + d] = best >= 0 ? src[(size_t)d * s.Np + best] : s.G[(size_t)cur * s.D + d];
-    if (threadIdx.x == 0) {
-        if (best >= 0) {
-            *g64 = s_f;
-            const unsigned long long k = pack_key((float)s_f, (uint32_t)best);
-            s.gkey[0] = k;
-            s.gkey[1] = k;
-            if (stale) *stale = 1;
-        } else {
-            s.gkey[nxt] = s.gkey[cur];
-        }
-        *s.t_dev = t_prev + 1u;
     }
 }
 
@@ -733,7 +853,7 @@ cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigne
     return cudaGetLastError();
 }
 
-int lsq_cand_blocks(int Np) { return (Np + kBlock - 1) / kBlock; }
+int lsq_cand_blocks(int Np) { return (Np + kSel - 1) / kSel; }
 
 cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec,
                             cudaStream_t st) {
@@ -746,7 +866,14 @@ cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double
 cudaError_t lsq_launch_offsets(const SwarmDev& s, const float* A, const float* b, int M, float* off, int* stale,
                                int num_sms, cudaStream_t st) {
     const int grid = std::max(1, std::min(num_sms * 4, (M + 7) / 8));
-    lsq_offset_kernel<<<grid, 256, 0, st>>>(s, A, b, M, off, stale);
+    const size_t smem = sizeof(float) * (size_t)s.D;   // gbest_pos in shared memory
+    if (smem > 48 * 1024) {
+        if (smem > 227 * 1024) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaFuncSetAttribute(lsq_offset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    lsq_offset_kernel<<<grid, 256, smem, st>>>(s, A, b, M, off, stale);
     return cudaGetLastError();
 }
 
@@ -757,7 +884,10 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const f
     const int nblk = lsq_cand_blocks(s.Np);
     unsigned long long* top = cand + (size_t)nblk * kCand;
     unsigned int* ticket = reinterpret_cast<unsigned int*>(top + kCand);
-    lsq_select_cand_kernel<<<nblk, kBlock, 0, st>>>(s, fit, part, nparts, all, cand, flags, top, ticket);
+    const int nkeys = nblk * kCand;
+    const size_t merge_smem =
+        (nblk > kMergeLists * kSel && nkeys <= kMergeSmem) ? sizeof(unsigned long long) * (size_t)nkeys : 0;
+    lsq_select_cand_kernel<<<nblk, kSel, merge_smem, st>>>(s, fit, part, nparts, all, cand, flags, top, ticket);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (!all && !lazy) {
@@ -768,18 +898,17 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const f
     // the candidates improved in this iteration (or, with `all`, are every
     // pbest): their pbest_pos is the position, pending write-back when lazy
     const float* src = (lazy && !all) ? s.x : s.pb;
+    // the last rescoring block accepts the best candidate (ticket: stale[2])
+    const AcceptArgs acc{reinterpret_cast<unsigned int*>(stale + 2), src, top, partial, chunks, g64, stale};
     if (gram.Gm) {
         const int pairs = ((s.D + 1) / 2 + chunks - 1) / chunks;
         lsq_rescore_gram_kernel<<<dim3(kCand / 4, chunks), 256, sizeof(double) * 4 * (size_t)s.D, st>>>(
-            s, src, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial);
+            s, src, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial, acc);
     } else {
         const int rows = (M + chunks - 1) / chunks;
         lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, src, A, b, M, top,
-                                                                                          rows, partial);
+                                                                                          rows, partial, acc);
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    lsq_accept_kernel<<<1, 512, 0, st>>>(s, src, top, partial, chunks, g64, stale);
     e = cudaGetLastError();
     if (e != cudaSuccess || !off) return e;
     return lsq_launch_offsets(s, A, b, M, off, stale, num_sms, st);
@@ -793,8 +922,9 @@ cudaError_t lsq_rescore_one(const SwarmDev& s, const float* A, const float* b, i
     cudaError_t e = cudaMemcpyAsync(scratch, top, sizeof(top), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     const int rows = (M + chunks - 1) / chunks;
+    const AcceptArgs none{nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     lsq_rescore_kernel<<<dim3(kCand, chunks), 256, sizeof(double) * (size_t)s.D, st>>>(s, s.pb, A, b, M, scratch,
-                                                                                      rows, partial);
+                                                                                      rows, partial, none);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     lsq_sum_one_kernel<<<1, 32, 0, st>>>(partial, chunks, g64);

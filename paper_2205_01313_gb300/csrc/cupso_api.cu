@@ -530,6 +530,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.c2 = c2;
     s.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
     s.key1 = (uint32_t)(seed >> 32);
+    philox_round_keys(s.key0, s.key1, s.rk0, s.rk1);
     s.swarm = swarm;
     s.wait_limit_ns = 2000000000ll;
     h->pbufs = paper_bufs_at(base + o_paper, h->Np, list_cap);

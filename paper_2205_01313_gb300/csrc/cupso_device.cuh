@@ -48,6 +48,10 @@ struct SwarmDev {
     float c1s, c2s;
     int fast_cr;                // c1s, c2s exact (normal or zero)
     int fast_clamp;             // no bound is +-0: clampf_minmax == clampf
+    // Philox round keys (key0 + r W0, key1 + r W1 for rounds r = 0..9), the same
+    // for every draw of the swarm: kernels that take them from here (the
+    // parameter space) skip the key additions of each round
+    uint32_t rk0[10], rk1[10];
 };
 
 // One swarm of a batch (kernels_batch.cu): its state in the batch arena and
@@ -97,6 +101,27 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
         k1 += W1;
     }
     return c;
+}
+
+// The same function with the round keys given (rk0[r] = k0 + r W0, rk1[r] =
+// k1 + r W1 modulo 2^32): identical words.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk0[r], lo1, hi0 ^ c.w ^ rk1[r], lo0);
+    }
+    return c;
+}
+
+// Host side: the round keys of key (k0, k1).
+inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk0)[10], uint32_t (&rk1)[10]) {
+    for (int r = 0; r < 10; ++r) {
+        rk0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
 }
 
 // One 32-bit word -> ((w >> 8) + 1) * 2^-24 in (0, 1]. (w >> 8) converts

@@ -205,6 +205,7 @@ int noalloc_step(int D, int N, const cupso_bounds* bounds, float w, float c1, fl
     s.c2 = c2;
     s.key0 = (uint32_t)(seed & 0xFFFFFFFFull);
     s.key1 = (uint32_t)(seed >> 32);
+    philox_round_keys(s.key0, s.key1, s.rk0, s.rk1);
     s.swarm = swarm_id;
     s.wait_limit_ns = 2000000000ll;
 

@@ -99,32 +99,69 @@ __device__ __forceinline__ void issue_panel(const SwarmDev& s, float4* my, uint3
     cp_commit();  // an empty group when there is nothing left to copy
 }
 
-// The running fitness state of lane `src`, for the fields the function uses.
+// The running fitness sums of lane `src`.
 template <int FIT>
 __device__ __forceinline__ void pull(FitAcc<FIT>& a, int src) {
     a.acc = __shfl_sync(0xFFFFFFFFu, a.acc, src);
     if constexpr (FIT == kAckley) a.acc2 = __shfl_sync(0xFFFFFFFFu, a.acc2, src);
-    if constexpr (FIT == kRosenbrock) a.prev = __shfl_sync(0xFFFFFFFFu, a.prev, src);
 }
 
 // Adds the fitness terms of this lane's four dimensions (d0 .. d0 + 3) in the
-// oracle's order: in phase k, the particle's lane k continues the sum of lane
-// k - 1 (lane 0 that of lane L - 1, which ended the previous panel). After the
+// oracle's order. The terms themselves do not depend on the running sum
+// (Rastrigin's x^2 - 10 cos 2 pi x + 10, Rosenbrock's 100 (x_{d+1} - x_d^2)^2 +
+// (1 - x_d)^2, the cubic's Horner value), so every lane computes its own at
+// once; only their folding into the sum, which keeps the order over d, passes
+// from lane to lane of the particle: in phase k the particle's lane k continues
+// the sum of lane k - 1 (lane 0 that of lane L - 1, which ended the previous
+// panel). Sphere and Ackley fold x with an fma, as the oracle does. After the
 // last phase, lane L - 1 of the particle holds the sum through its panel.
+// `carry` is x_{d0 - 1} for the particle's lane 0 (the last value of the
+// previous panel), updated here to this panel's last value.
 template <int FIT, int L>
-__device__ __forceinline__ void panel_sum(FitAcc<FIT>& a, const float4& X, int d0, int j, int lane_id) {
-    float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if constexpr (FitAcc<FIT>::kNeedsCos) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) c[k] = cos2pi(lane(X, k));
-    }
+__device__ __forceinline__ void panel_sum(FitAcc<FIT>& a, const float4& X, int d0, int j, int lane_id, float& carry) {
+    const float x[4] = {X.x, X.y, X.z, X.w};
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     const int base = lane_id - j;
+    if constexpr (FIT == kRastrigin) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = __fmaf_rn(x[k], x[k], __fmaf_rn(-10.0f, cos2pi(x[k]), 10.0f));
+    } else if constexpr (FIT == kAckley) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[k] = cos2pi(x[k]);
+    } else if constexpr (FIT == kCubicMax) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            t[k] = __fmaf_rn(__fmaf_rn(__fsub_rn(x[k], 0.8f), x[k], -1000.0f), x[k], 8000.0f);
+    } else if constexpr (FIT == kRosenbrock) {
+        // term of dimension d (d >= 1) from x_{d-1} and x_d
+        const float from_left = __shfl_sync(0xFFFFFFFFu, X.w, lane_id - 1 < base ? lane_id : lane_id - 1);
+        float prev = j == 0 ? carry : from_left;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float pp = __fmaf_rn(-prev, prev, x[k]);
+            const float qq = __fsub_rn(1.0f, prev);
+            t[k] = __fmaf_rn(__fmul_rn(100.0f, pp), pp, __fmul_rn(qq, qq));
+            prev = x[k];
+        }
+        carry = __shfl_sync(0xFFFFFFFFu, X.w, base + L - 1);
+    }
 #pragma unroll
     for (int ph = 0; ph < L; ++ph) {
         pull(a, base + (ph + L - 1) % L);
         if (j == ph) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a.add_c(d0 + k, lane(X, k), c[k]);
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (FIT == kSphere) {
+                    a.acc = __fmaf_rn(x[k], x[k], a.acc);
+                } else if constexpr (FIT == kAckley) {
+                    a.acc = __fmaf_rn(x[k], x[k], a.acc);
+                    a.acc2 = __fadd_rn(a.acc2, t[k]);
+                } else if constexpr (FIT == kRosenbrock) {
+                    if (d0 + k > 0) a.acc = __fadd_rn(a.acc, t[k]);
+                } else {
+                    a.acc = __fadd_rn(a.acc, t[k]);
+                }
+            }
         }
     }
 }
@@ -195,6 +232,7 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
     while (u_cur < nunits) {
         const uint32_t i = u_cur * PU + pl;
         FitAcc<FIT> acc;
+        float carry = 0.0f;   // Rosenbrock: x_{d-1} across panels
         float pf = 0.0f;
         for (int q = 0; q < Dq; ++q) {
             // keep STAGES-1 panels in flight: issue the panel STAGES-1 ahead
@@ -228,7 +266,7 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
             }
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)((d0 >> 1) + g), i, t, s.swarm), s.key0, s.key1);
+                const uint4 r = philox4x32_10_rk(make_uint4((uint32_t)((d0 >> 1) + g), i, t, s.swarm), s.rk0, s.rk1);
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     const int k = 2 * g + hh;
@@ -245,7 +283,7 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
             }
             st4(s.x + off, X);
             st4(s.v + off, V);
-            panel_sum<FIT, L>(acc, X, d0, j, lane_id);
+            panel_sum<FIT, L>(acc, X, d0, j, lane_id, carry);
             if (++stage == STAGES) stage = 0;
         }
         // Step 4 (strict improvement; the new pbest_pos is pos, flagged) and

@@ -132,8 +132,9 @@ typedef enum {
 
 /* The implementations of the SYNC step; all compute the same bits. */
 typedef enum {
-    CUPSO_SYNC_KERNEL_AUTO = 0,       /* tiled for small swarms, else the deepest pipelined
-                                         ring supported, else register                      */
+    CUPSO_SYNC_KERNEL_AUTO = 0,       /* tiled for small swarms, else the panel kernel where D
+                                         allows, else the deepest pipelined ring supported, else
+                                         register                                           */
     CUPSO_SYNC_KERNEL_REGISTER = 1,   /* loads straight into registers, 1024-particle tiles */
     CUPSO_SYNC_KERNEL_PIPELINED3 = 2, /* rows staged through shared memory, 2 pairs ahead   */
     CUPSO_SYNC_KERNEL_PIPELINED4 = 3, /* the same, 3 pairs ahead                            */
@@ -149,8 +150,9 @@ typedef enum {
                                          the swarm improves                                       */
     CUPSO_SYNC_KERNEL_PANEL16 = 6     /* the same with panels of 16 dimensions (64 bytes per particle,
                                          the granularity of HBM reads), four threads per particle;
-                                         D % 16 == 0, D >= 32. AUTO takes 8-dimension panels wherever
-                                         the pipelined kernel would run and D % 8 == 0            */
+                                         D % 16 == 0, D >= 32. AUTO, for D % 8 == 0: the tiled kernel
+                                         up to about 2^22 particle-dimensions, above that 16-dimension
+                                         panels for D >= 128 (or D >= 64 with N <= 262144), else 8 */
 } cupso_sync_kernel;
 
 typedef struct {

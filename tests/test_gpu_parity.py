@@ -54,14 +54,20 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_stages"] == 0
     with gpu_swarm(P, 1, 20000, 16, 1, "sync") as s:            # few particles per SM, D >= 8: tiled
         assert s.info()["sync_tile"] == 64 and s.info()["sync_stages"] == 0   # 64 x 16 items, 313 tiles
-    with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:
-        assert s.info()["sync_tile"] == 32
-    with gpu_swarm(P, 3, 65536, 128, 1, "sync") as s:           # narrow tiles, no cos: streaming from ~224 per SM
-        assert s.info()["sync_tile"] == 0
-    with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to ~896 per SM
-        assert s.info()["sync_tile"] == 128
-    with gpu_swarm(P, 1, 1 << 18, 16, 1, "sync") as s:          # enough particles: streaming (panel layout)
+    with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:           # 2^23 particle-dimensions: panels
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
+    with gpu_swarm(P, 1, 65536, 120, 1, "sync") as s:           # D % 8 == 0, 120 / 16 not whole: 8-wide
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
+    with gpu_swarm(P, 3, 65536, 127, 1, "sync") as s:           # D % 8 != 0, narrow tiles, no cos: from ~224 per SM
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 0
+    with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to 2^22 particle-dimensions
+        assert s.info()["sync_tile"] == 128
+    with gpu_swarm(P, 3, 1 << 18, 16, 1, "sync") as s:          # 2^22 with many particles: panel layout
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
+    with gpu_swarm(P, 1, 32768, 256, 1, "sync") as s:           # few particles, cos: tiled up to 2^23
+        assert s.info()["sync_tile"] > 0
+    with gpu_swarm(P, 3, 32768, 256, 1, "sync") as s:           # the same without cos: panels
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])

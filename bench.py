@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the batch and least-squares keys of the line")
+    ap.add_argument("--lsq-launches", default="", choices=["", "bf16", "fp8", "fp32", "fp64"],
+                    help="lsq8192: only 6 + 20 iterations of one precision, one launch per kernel "
+                         "(no graph), for a profiler's launch list")
     return ap.parse_args()
 
 
@@ -643,6 +646,30 @@ def lsq_report(P, stream, quick):
     }
 
 
+def lsq_launches(P, stream, prec):
+    """The least-squares workload in one precision: set-up, 6 iterations, then 20
+    timed ones, each iteration's kernels launched directly (no captured graph),
+    so that a profiler lists them one by one."""
+    import torch
+    cfg = workloads.lsq_config()
+    N, D, M = cfg["N"], cfg["D"], cfg["M"]
+    A, b, _ = workloads.lsq_problem(M, D, seed=cfg["seed"])
+    dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
+                 stream=stream.cuda_stream) as s:
+        s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
+        s.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)
+        s.step(6)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"workload": "lsq8192", "precision": prec, "iters_timed": 20,
+                "ms_per_iter": e0.elapsed_time(e1) / 20, "graph": "none (one launch per kernel)"}
+
+
 def run_lsq(a):
     import torch
 
@@ -651,6 +678,9 @@ def run_lsq(a):
     B.build()
     from paper_2205_01313_gb300 import cupso as P
     stream = torch.cuda.Stream()
+    if a.lsq_launches:
+        print(json.dumps(lsq_launches(P, stream, a.lsq_launches)), flush=True)
+        return
     r = lsq_report(P, stream, quick=False)
     out = {
         "metric": METRIC, "value": r["runs"]["bf16"]["pd_per_s"], "unit": UNIT, "n_gpus": 1,

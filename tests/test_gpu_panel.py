@@ -131,3 +131,46 @@ def test_panel_checkpoint_resume(P):
     ref = oracle_swarm(fid, N, D, 9).init().step_sync(16)
     assert_state_equal(st, ref)
     assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("kernel,D", [("panel8", 16), ("panel16", 32)])
+@pytest.mark.parametrize("N", [1, 17, 130])
+@pytest.mark.parametrize("fid", [0, 3])
+def test_panel_tiny_and_ragged_swarms(P, fid, N, D, kernel):
+    """Swarms smaller than one warp unit or one 128-particle pad: padded
+    particles move but never win; trajectories bit-exact with the oracle."""
+    with _panel_swarm(P, fid, N, D, 5, kernel) as s:
+        assert s.info()["sync_panel"] == int(kernel[5:])
+        s.step(12)
+        st = s.state()
+        rc, fit, idx, pos = s.gbest()
+    ref = oracle_swarm(fid, N, D, 5).init().step_sync(12)
+    assert rc == P.CUPSO_OK
+    assert_state_equal(st, ref)
+    assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+@pytest.mark.parametrize("kernel", ["panel8", "panel16"])
+def test_panel_nan_fitness_sets_status(P, kernel):
+    """A NaN fitness (inf - inf inside the cubic at +-1e30) sets the sticky status;
+    the particle never becomes pbest or gbest; the step is the oracle's."""
+    fid, N, D = 4, 300, 16
+    bounds = (-1e30, 1e30, 1.0)
+    rng = np.random.default_rng(2)
+    pos = rng.uniform(-1, 1, (N, D)).astype(np.float32)
+    pos[77, :2] = [1e30, -1e30]
+    from oracle import oracle as O
+    pf = np.array([O.fitness(fid, p) for p in pos], np.float32)
+    assert np.isnan(pf[77])
+    with P.Swarm(D, N, bounds, W, C12, C12, fid, 1) as s:
+        s.set_mode("sync")
+        s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[kernel])
+        s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+        s.step(1)
+        rc, fit, idx, _ = s.gbest()
+        st = s.state()
+        assert rc == P.CUPSO_ERR_NAN and idx != 77
+    ref = oracle_swarm(fid, N, D, 1, bounds=bounds)
+    ref.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+    ref.step_sync(1)
+    assert_state_equal(st, ref)

@@ -129,11 +129,11 @@ int sync_tile(const cupso_swarm* h) {
     const bool has_cos = h->fid == CUPSO_RASTRIGIN || h->fid == CUPSO_ACKLEY;
     if (h->panel_ok && h->D % 8 == 0) {
         // against the panel kernel (sweep on one GB300, N = 8192 .. 524288, D = 16 .. 256,
-        // Rosenbrock and Rastrigin): the tiled kernel is the faster one below 2^22
-        // particle-dimensions per iteration, and for swarms of up to 32768 particles up
-        // to 2^22 (2^23 with cos(2 pi x) in the fitness); the panel kernel above
+        // Rosenbrock and Rastrigin): the tiled kernel is the faster one up to 2^22
+        // particle-dimensions per iteration -- without cos(2 pi x) in the fitness only
+        // up to D = 64 -- and the panel kernel above
         const long long pd = (long long)h->N * h->D, cut = 1ll << 22;
-        const bool tiled = pd < cut || (h->N <= 32768 && pd <= (has_cos ? 2 * cut : cut));
+        const bool tiled = pd <= cut && (has_cos || h->D <= 64);
         return tiled ? tiled_particles(h->N, h->D, h->num_sms) : 0;
     }
     const long long per_sm = (has_cos || h->D <= 64) ? 896 : 224;
@@ -166,9 +166,9 @@ int sync_stages(const cupso_swarm* h) {
 // panel width and ring depth (5 panels where the panels allow, else 3); width
 // 0 when the dimension-major kernels run. AUTO takes the panel kernel for
 // D % 8 == 0 wherever the tiled kernel is not the faster one; 16-dimension
-// panels for D >= 128, or D >= 64 with up to 262144 particles (their units of
-// 8 particles spread a smaller swarm more evenly), 8-dimension panels
-// otherwise (Rosenbrock 2^20 x 64: a tie, 0.239 ms per iteration either way).
+// panels for D >= 128 except between 8192 and 65536 particles, 8-dimension
+// panels otherwise (Rosenbrock 2^20 x 64: a tie, 0.239 ms per iteration
+// either way).
 struct PanelCfg {
     int width = 0, stages = 0;
 };
@@ -181,9 +181,9 @@ PanelCfg panel_cfg(const cupso_swarm* h) {
         case CUPSO_SYNC_KERNEL_PANEL16: widths[0] = 16; break;
         case CUPSO_SYNC_KERNEL_AUTO:
             if (sync_tile(h)) return c;
-            // 16-dimension panels (units of 8 particles) where the swarm's units are few or
-            // long, 8 otherwise (the same sweep)
-            if (h->D % 16 == 0 && (h->D >= 128 || (h->D >= 64 && h->N <= 262144))) widths[0] = 16;
+            // 16-dimension panels for long particles (D >= 128) outside 8192 < N < 65536,
+            // 8 otherwise (the same sweep; the two are within a few percent elsewhere)
+            if (h->D % 16 == 0 && h->D >= 128 && (h->N <= 8192 || h->N >= 65536)) widths[0] = 16;
             widths[1] = 8;
             break;
         default: return c;

@@ -35,8 +35,8 @@
 // keeps the oracle's order over d, passes from lane to lane of the particle,
 // the running sum carried by a shuffle. Loads are staged through a per-thread
 // cp.async ring of STAGES panels (pos, v and pbest_pos: three 16-byte slots
-// each), STAGES - 1 ahead of the one computed; warps take two units at a time
-// from a counter.
+// each), STAGES - 1 ahead of the one computed; warps take units from a counter
+// (two at a time when the swarm has many per warp).
 #include <cuda_runtime.h>
 
 #include "cupso_device.cuh"
@@ -63,9 +63,15 @@ __device__ __forceinline__ size_t panel_off(const SwarmDev& s, int q, uint32_t i
     return ((size_t)q * (size_t)s.Np + (size_t)i) * W;
 }
 
-// Hands out units to the warps: one counter increment per two units.
+// Hands out units to the warps: for a swarm with many units per warp, one
+// counter increment per two units (fewer atomics on one address); for one
+// with few, one per unit, since the iteration lasts as long as the warp with
+// the most units and a two-unit grain doubles that excess.
 struct UnitFeed {
     uint32_t spare = 0xFFFFFFFFu;   // the second unit of the last fetch, if not yet taken
+    bool pairs;
+    __device__ __forceinline__ explicit UnitFeed(uint32_t nunits)
+        : pairs(nunits >= 8u * gridDim.x * (blockDim.x >> 5)) {}
     __device__ __forceinline__ uint32_t next(const SwarmDev& s, int lane_id) {
         if (spare != 0xFFFFFFFFu) {
             const uint32_t u = spare;
@@ -75,6 +81,7 @@ struct UnitFeed {
         uint32_t k = 0;
         if (lane_id == 0) k = atomicAdd(s.work, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
+        if (!pairs) return k;
         spare = 2u * k + 1u;
         return 2u * k;
     }
@@ -218,7 +225,7 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
     float4* my = ring + threadIdx.x;
     constexpr uint32_t kNone = 0xFFFFFFFFu;
 
-    UnitFeed feed;
+    UnitFeed feed(nunits);
     uint32_t u_cur = feed.next(s, lane_id);
     uint32_t fl_cur = u_cur < nunits ? (uint32_t)__ldcg(s.pflag + u_cur * PU + pl) : 0u;
     uint32_t u_nxt = kNone, fl_nxt = 0u;

@@ -62,12 +62,12 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 0
     with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to 2^22 particle-dimensions
         assert s.info()["sync_tile"] == 128
-    with gpu_swarm(P, 3, 1 << 18, 16, 1, "sync") as s:          # 2^22 with many particles: panel layout
-        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
-    with gpu_swarm(P, 1, 32768, 256, 1, "sync") as s:           # few particles, cos: tiled up to 2^23
+    with gpu_swarm(P, 3, 1 << 18, 16, 1, "sync") as s:          # 2^22, D <= 64: still tiled
         assert s.info()["sync_tile"] > 0
-    with gpu_swarm(P, 3, 32768, 256, 1, "sync") as s:           # the same without cos: panels
-        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
+    with gpu_swarm(P, 1, 32768, 256, 1, "sync") as s:           # 2^23: panels (8 wide at this N)
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
+    with gpu_swarm(P, 3, 16384, 128, 1, "sync") as s:           # 2^21 but D > 64, no cos: panels
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])

@@ -126,8 +126,18 @@ typedef enum {
                                      BF16/FP8: the tensor-core product alone (the move kernel
                                      before it writes the operand; the selection after it adds the
                                      product's partial sums) */
-    CUPSO_OPT_FAULT_HOLD_LOCK = 100 /* test hook: ASYNC starts with the gbest lock held, so every
-                                       lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
+    CUPSO_OPT_ITERS_PER_LAUNCH = 9, /* SYNC step on the panel layout: iterations per launch of a
+                                       cupso_step call. 1: one kernel per iteration (graphs per
+                                       CUPSO_OPT_GRAPH_CHUNK); n > 1: up to n per cooperative launch,
+                                       all CTAs resident, a grid barrier between iterations (each
+                                       wait bounded by CUPSO_OPT_WAIT_LIMIT_NS); 0 (default): up to
+                                       4096. Same results either way. */
+    CUPSO_OPT_FAULT_HOLD_LOCK = 100, /* test hook: ASYNC starts with the gbest lock held, so every
+                                        lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
+    CUPSO_OPT_FAULT_STALL_BARRIER = 101 /* test hook: a multi-iteration panel launch waits for one CTA
+                                           more than it has, so its first barrier wait expires and
+                                           reports CUPSO_ERR_DEVICE_TIMEOUT; the swarm's state is then
+                                           undefined (CUPSO_OPT_CLEAR_STATUS resets the counters) */
 } cupso_option;
 
 /* The implementations of the SYNC step; all compute the same bits. */
@@ -171,6 +181,7 @@ typedef struct {
     int fitness_timed;    /* how many iterations that mean covers */
     uint64_t device_bytes;/* device memory held by the handle        */
     int sync_panel;       /* panel width (8 or 16) when the SYNC step runs the panel kernel, else 0 */
+    int sync_iters_per_launch; /* most iterations one SYNC launch runs (CUPSO_OPT_ITERS_PER_LAUNCH) */
 } cupso_info;
 
 /* Create a swarm and run Step 1 of Alg. 1 (iteration t = 0) on the device:

@@ -70,6 +70,8 @@ struct cupso_swarm {
     int graph_mode = -1, graph_len = 0;
     uint32_t t_host = 0;
     int hold_lock = 0;
+    int stall_barrier = 0;          // test hook: the multi-iteration panel launch waits for one CTA more
+    int iters_per_launch = 0;       // panel SYNC step: iterations per launch, 0 = automatic
     int grid_override = 0;
     int onchip_cluster = 0;
     int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
@@ -236,6 +238,19 @@ int sync_grid(const cupso_swarm* h) {
     return g < ntiles ? g : ntiles;
 }
 
+// Iterations per launch of the panel SYNC step: the option, else all of a
+// cupso_step call up to kPanelMaxIters.
+int panel_iters_per_launch(const cupso_swarm* h) {
+    return h->iters_per_launch > 0 ? h->iters_per_launch : kPanelMaxIters;
+}
+
+// CTAs of a multi-iteration panel launch: the SYNC grid, at most what the SMs
+// hold at once (a cooperative launch).
+int panel_persist_grid(const cupso_swarm* h, const PanelCfg& pc) {
+    const int resident = h->num_sms * panel_blocks_per_sm(pc.width, pc.stages, h->fid, h->D);
+    return std::min(sync_grid(h), resident);
+}
+
 // ASYNC uses small CTAs when the swarm is small, so that it still spreads
 // over many independently running CTAs.
 int async_block(const cupso_swarm* h) {
@@ -353,7 +368,7 @@ cudaError_t launch_one(cupso_swarm* h, int mode, cudaStream_t st) {
         case kModeLsq: return launch_lsq_iteration(h, st);
         case CUPSO_MODE_SYNC: {
             const PanelCfg pc = panel_cfg(h);
-            if (pc.width) return launch_sync_panel(h->dev, h->fid, pc.width, pc.stages, sync_grid(h), st);
+            if (pc.width) return launch_sync_panel(h->dev, h->fid, pc.width, pc.stages, sync_grid(h), 1, false, st);
             if (const int P = sync_tile(h))
                 return launch_sync_tiled(h->dev, h->fid, P, tiled_grid(h, P), st);
             const int stages = sync_stages(h);
@@ -530,6 +545,7 @@ int create_swarm(int D, int N, const cupso_bounds* b, float w, float c1, float c
     s.lock = w32 + 3;
     s.seq = w32 + 4;
     s.work = w32 + 5;
+    s.bar = w32 + 6;
     s.N = N;
     s.D = D;
     s.Np = h->Np;
@@ -788,7 +804,10 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             drop_graph(h);
             return CUPSO_OK;
         case CUPSO_OPT_CLEAR_STATUS:
+            // with the status, the counters a wait that expired may have left behind
             CUPSO_CUDA(cudaMemsetAsync(h->dev.status, 0, sizeof(unsigned), h->stream), "cudaMemsetAsync");
+            CUPSO_CUDA(cudaMemsetAsync(h->dev.ticket, 0, sizeof(unsigned), h->stream), "cudaMemsetAsync");
+            CUPSO_CUDA(cudaMemsetAsync(h->dev.work, 0, 2 * sizeof(unsigned), h->stream), "cudaMemsetAsync");
             return CUPSO_OK;
         case CUPSO_OPT_GRID:
             if (value < 0 || value > (1 << 20)) return fail(CUPSO_ERR_INVALID_ARG, "grid out of range%s");
@@ -812,8 +831,16 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
             h->ppt_option = (int)value;
             drop_graph(h);
             return CUPSO_OK;
+        case CUPSO_OPT_ITERS_PER_LAUNCH:
+            if (value < 0 || value > kPanelMaxIters)
+                return fail(CUPSO_ERR_INVALID_ARG, "iterations per launch out of range%s");
+            h->iters_per_launch = (int)value;
+            return CUPSO_OK;
         case CUPSO_OPT_FAULT_HOLD_LOCK:
             h->hold_lock = value ? 1 : 0;
+            return CUPSO_OK;
+        case CUPSO_OPT_FAULT_STALL_BARRIER:
+            h->stall_barrier = value ? 1 : 0;
             return CUPSO_OK;
         default:
             return fail(CUPSO_ERR_INVALID_ARG, "unknown option%s");
@@ -885,6 +912,21 @@ int cupso_step(cupso_handle h, int iters) {
         if (e != cudaSuccess) return cuda_fail(e, "on-chip launch");
     } else {
         int left = iters;
+        const int P = panel ? panel_iters_per_launch(h) : 1;
+        if (P > 1 && left > 1) {
+            // several iterations per cooperative launch, a grid barrier between them
+            const PanelCfg pc = panel_cfg(h);
+            const int grid = panel_persist_grid(h, pc);
+            while (left > 1) {
+                const int n = std::min(left, P);
+                e = cudaMemsetAsync(h->dev.work, 0, 2 * sizeof(unsigned), h->stream);
+                if (e == cudaSuccess)
+                    e = launch_sync_panel(h->dev, h->fid, pc.width, pc.stages, grid, n, h->stall_barrier != 0,
+                                          h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "panel launch");
+                left -= n;
+            }
+        }
         const int L = h->graph_chunk;
         if (L > 1 && left >= L) {
             int rc = ensure_graph(h, mode, L);
@@ -1207,6 +1249,7 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
         info->sync_ppt = 0;
         info->sync_tile = 0;
         info->sync_panel = 0;
+        info->sync_iters_per_launch = 1;
     } else {
         const int tile = sync_tile(h);
         info->sync_grid = tile ? std::min(tiled_grid(h, tile), (h->N + tile - 1) / tile) : sync_grid(h);
@@ -1217,6 +1260,7 @@ int cupso_get_info(cupso_handle h, cupso_info* info) {
         info->sync_ppt = pc.width ? 1 : ((!tile && sync_stages(h)) ? sync_ppt(h) : 0);
         info->sync_tile = pc.width ? 0 : tile;
         info->sync_panel = pc.width;
+        info->sync_iters_per_launch = pc.width ? panel_iters_per_launch(h) : 1;
     }
     info->fitness_ms = 0.0f;
     info->fitness_timed = 0;

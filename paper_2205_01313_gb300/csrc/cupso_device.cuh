@@ -29,6 +29,7 @@ struct SwarmDev {
     unsigned int* status;       // sticky error bits (kStatus*)
     unsigned long long* aux;    // tree baseline: one key per block of the first kernel
     unsigned int* work;         // pipelined step: next 128-particle unit to hand out
+    unsigned int* bar;          // panel step over several iterations: grid-barrier counter
     // Lazy pbest (pipelined step): byte i is 1 when particle i improved in the
     // last iteration and its pbest_pos row has not been written yet; its
     // pbest_pos is then its pos. NULL or all-zero means pb is complete.

@@ -53,7 +53,11 @@ cudaError_t launch_batch_init(const BatchDev& b, int grid, cudaStream_t st);
 bool panel_supported(int width, int stages, int D);
 cudaError_t prepare_panel(int D);
 int panel_blocks_per_sm(int width, int stages, int fid, int D);
-cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int width, int stages, int grid, cudaStream_t st);
+// Iterations of one panel launch; more than one is a cooperative launch with a
+// grid barrier per iteration (every CTA resident; see kernels_panel.cu).
+constexpr int kPanelMaxIters = 4096;
+cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int width, int stages, int grid, int iters,
+                              bool stall_barrier, cudaStream_t st);
 cudaError_t launch_materialize_panel(const SwarmDev& s, int width, int grid, cudaStream_t st);
 // dst = src in the other layout (dimension-major <-> panel of width W); D % W == 0.
 cudaError_t launch_relayout(const float* src, float* dst, int D, int Np, int width, bool to_panel, int grid,

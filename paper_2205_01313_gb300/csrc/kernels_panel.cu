@@ -63,15 +63,17 @@ __device__ __forceinline__ size_t panel_off(const SwarmDev& s, int q, uint32_t i
     return ((size_t)q * (size_t)s.Np + (size_t)i) * W;
 }
 
-// Hands out units to the warps: for a swarm with many units per warp, one
+// Hands out the units after the warps' own first ones (units base, base + 1,
+// ...; base = the number of warps): for a swarm with many units per warp, one
 // counter increment per two units (fewer atomics on one address); for one
 // with few, one per unit, since the iteration lasts as long as the warp with
 // the most units and a two-unit grain doubles that excess.
 struct UnitFeed {
     uint32_t spare = 0xFFFFFFFFu;   // the second unit of the last fetch, if not yet taken
+    uint32_t base;
     bool pairs;
-    __device__ __forceinline__ explicit UnitFeed(uint32_t nunits)
-        : pairs(nunits >= 8u * gridDim.x * (blockDim.x >> 5)) {}
+    __device__ __forceinline__ UnitFeed(uint32_t nunits, uint32_t nwarps)
+        : base(nwarps), pairs(nunits >= 8u * nwarps) {}
     __device__ __forceinline__ uint32_t next(const SwarmDev& s, int lane_id) {
         if (spare != 0xFFFFFFFFu) {
             const uint32_t u = spare;
@@ -81,9 +83,9 @@ struct UnitFeed {
         uint32_t k = 0;
         if (lane_id == 0) k = atomicAdd(s.work, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (!pairs) return k;
-        spare = 2u * k + 1u;
-        return 2u * k;
+        if (!pairs) return base + k;
+        spare = base + 2u * k + 1u;
+        return base + 2u * k;
     }
 };
 
@@ -173,17 +175,10 @@ __device__ __forceinline__ void panel_sum(FitAcc<FIT>& a, const float4& X, int d
     }
 }
 
-// Last-CTA-done epilogue on the panel layout: gbest_pos from the winner's
-// pbest_pos (or from pos when its row is still pending).
+// gbest_pos of iteration parity nxt from the winner's pbest_pos (or from pos
+// when its row is still pending); run by the last CTA of an iteration.
 template <int W>
-__device__ __forceinline__ void finish_iteration_panel(const SwarmDev& s, int cur, int nxt, uint32_t t_new) {
-    __shared__ int s_last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(s.ticket, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+__device__ __forceinline__ void gather_gbest_panel(const SwarmDev& s, int nxt) {
     const unsigned long long knew = __ldcg(s.gkey + nxt);
     const uint32_t g = (uint32_t)(knew & 0xFFFFFFFFull);
     if (g < (uint32_t)s.N) {
@@ -192,50 +187,33 @@ __device__ __forceinline__ void finish_iteration_panel(const SwarmDev& s, int cu
         for (int d = threadIdx.x; d < s.D; d += blockDim.x)
             s.G[(size_t)nxt * s.D + d] = __ldcg(src + panel_off<W>(s, d / W, g) + (d % W));
     }
-    if (threadIdx.x == 0) {
-        s.gkey[cur] = knew;
-        *s.t_dev = t_new;
-        *s.ticket = 0u;
-        *s.work = 0u;
-    }
 }
 
-}  // namespace
+__device__ __forceinline__ unsigned int ld_acquire_gpu_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 
-// Requires D % W == 0, D / W >= STAGES - 1, Np a multiple of 128 and s.pflag,
-// s.work set (work zero at launch). FAST selects move_one_fast (requires
-// s.fast_cr and s.fast_clamp).
+// One iteration of a warp's units: first u_cur, whose first STAGES - 1 panels
+// the ring already holds (fl_cur: its particles' pending flags), then those
+// the feed hands out. Returns the lane's Step-5 candidate (a key below K, or
+// none); the ring is empty on return.
 template <int FIT, int W, int STAGES, bool FAST>
-__global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_constant__ SwarmDev s) {
+__device__ __forceinline__ unsigned long long panel_units(const SwarmDev& s, float4* my, const float* Gs,
+                                                          UnitFeed& feed, uint32_t u_cur, uint32_t fl_cur,
+                                                          uint32_t nunits, uint32_t t, unsigned long long K,
+                                                          bool& nan) {
     constexpr int L = W / 4;              // lanes per particle
     constexpr uint32_t PU = 32 / L;       // particles per warp unit
-    extern __shared__ float4 ring[];      // [STAGES][3][kBlock], then gbest_pos [D]
-    float* Gs = reinterpret_cast<float*>(ring + STAGES * 3 * kBlock);
-    const uint32_t t_prev = __ldcg(s.t_dev);
-    const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
-    const uint32_t t = t_prev + 1u;
-    const unsigned long long K = __ldcg(s.gkey + cur);  // gbest at the end of t-1
-    for (int d = threadIdx.x; d < s.D; d += blockDim.x) Gs[d] = __ldcg(s.G + (size_t)cur * s.D + d);
-    __syncthreads();
-
+    constexpr uint32_t kNone = 0xFFFFFFFFu;
     const int lane_id = threadIdx.x & 31, j = lane_id % L;
     const uint32_t pl = (uint32_t)(lane_id / L);
     const int D = s.D, Dq = D / W;
-    const uint32_t nunits = (uint32_t)s.Np / PU;
-    float4* my = ring + threadIdx.x;
-    constexpr uint32_t kNone = 0xFFFFFFFFu;
-
-    UnitFeed feed(nunits);
-    uint32_t u_cur = feed.next(s, lane_id);
-    uint32_t fl_cur = u_cur < nunits ? (uint32_t)__ldcg(s.pflag + u_cur * PU + pl) : 0u;
     uint32_t u_nxt = kNone, fl_nxt = 0u;
-#pragma unroll
-    for (int k = 0; k < STAGES - 1; ++k) issue_panel<W>(s, my, u_cur, k, k, nunits, lane_id, fl_cur);
     int iq = STAGES - 1;  // panel of the next issue, counted from the current unit
     int stage = 0;        // ring stage of the panel being computed
-
     unsigned long long best = kKeyNone;
-    bool nan = false;
     while (u_cur < nunits) {
         const uint32_t i = u_cur * PU + pl;
         FitAcc<FIT> acc;
@@ -315,10 +293,102 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
         iq -= Dq;
     }
     cp_wait<0>();
-    best = warp_min_u64(best);
-    if (lane_id == 0 && best < K) atomicMin(s.gkey + nxt, best);
+    return best;
+}
+
+}  // namespace
+
+// `iters` synchronous iterations. Requires D % W == 0, D / W >= STAGES - 1,
+// Np a multiple of 128, s.pflag, s.work and s.bar set, work and bar zero at
+// launch. FAST selects move_one_fast (requires s.fast_cr and s.fast_clamp).
+//
+// Each warp takes unit (its warp index) first in every iteration, then units
+// from the counter. With more than one iteration, every CTA must be resident
+// (a cooperative launch): an iteration ends in a grid barrier on s.bar -- each
+// CTA arrives once; the last to arrive gathers gbest_pos and releases the
+// others -- and while a CTA waits, its warps already load the first panels of
+// their own unit for the next iteration (rows they wrote themselves, so they
+// need nothing from the barrier). The wait is bounded by s.wait_limit_ns: on
+// expiry the timeout status is set and the CTA stops. `expect` is the number
+// of arrivals that completes a barrier: gridDim.x (one more only to test that
+// bound).
+template <int FIT, int W, int STAGES, bool FAST>
+__global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_constant__ SwarmDev s, int iters,
+                                                               unsigned int expect) {
+    constexpr int L = W / 4;
+    constexpr uint32_t PU = 32 / L;
+    extern __shared__ float4 ring[];      // [STAGES][3][kBlock], then gbest_pos [D]
+    float* Gs = reinterpret_cast<float*>(ring + STAGES * 3 * kBlock);
+    __shared__ int s_last, s_ok;
+    const int lane_id = threadIdx.x & 31;
+    const uint32_t pl = (uint32_t)(lane_id / L);
+    const uint32_t nunits = (uint32_t)s.Np / PU;
+    const uint32_t nwarps = gridDim.x * (kBlock / 32);
+    const uint32_t u0 = blockIdx.x * (kBlock / 32) + (uint32_t)(threadIdx.x >> 5);
+    float4* my = ring + threadIdx.x;
+    const uint32_t t_prev = __ldcg(s.t_dev);
+
+    uint32_t fl0 = u0 < nunits ? (uint32_t)__ldcg(s.pflag + u0 * PU + pl) : 0u;
+#pragma unroll
+    for (int k = 0; k < STAGES - 1; ++k) issue_panel<W>(s, my, u0, k, k, nunits, lane_id, fl0);
+    bool nan = false;
+    for (int it = 0; it < iters; ++it) {
+        const uint32_t t = t_prev + 1u + (uint32_t)it;
+        const int cur = (int)((t - 1u) & 1u), nxt = cur ^ 1;
+        const unsigned long long K = __ldcg(s.gkey + cur);  // gbest at the end of t-1
+        for (int d = threadIdx.x; d < s.D; d += blockDim.x) Gs[d] = __ldcg(s.G + (size_t)cur * s.D + d);
+        __syncthreads();
+        UnitFeed feed(nunits, nwarps);
+        unsigned long long best = panel_units<FIT, W, STAGES, FAST>(s, my, Gs, feed, u0, fl0, nunits, t, K, nan);
+        best = warp_min_u64(best);
+        if (lane_id == 0 && best < K) atomicMin(s.gkey + nxt, best);
+
+        // arrival; the last CTA completes Step 5 and releases the barrier
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(s.bar, 1u) == (uint32_t)(it + 1) * (expect + 1u) - 2u;
+        __syncthreads();
+        const bool final_it = it + 1 == iters;
+        if (s_last) {
+            __threadfence();
+            gather_gbest_panel<W>(s, nxt);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s.gkey[cur] = __ldcg(s.gkey + nxt);
+                *s.t_dev = t;
+                *s.work = 0u;
+                if (final_it) *s.bar = 0u;
+                __threadfence();
+                if (!final_it) atomicAdd(s.bar, 1u);
+            }
+        }
+        if (final_it) break;
+
+        // the first panels of this warp's own unit for the next iteration
+        fl0 = u0 < nunits ? (uint32_t)__ldcg(s.pflag + u0 * PU + pl) : 0u;
+#pragma unroll
+        for (int k = 0; k < STAGES - 1; ++k) issue_panel<W>(s, my, u0, k, k, nunits, lane_id, fl0);
+        if (threadIdx.x == 0) {
+            const uint32_t target = (uint32_t)(it + 1) * (expect + 1u);
+            const long long deadline = global_ns() + s.wait_limit_ns;
+            int ok = 1;
+            while (ld_acquire_gpu_u32(s.bar) < target) {
+                if (global_ns() > deadline) {
+                    ok = 0;
+                    atomicOr(s.status, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(32);
+            }
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            cp_wait<0>();
+            break;
+        }
+    }
     if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
-    finish_iteration_panel<W>(s, cur, nxt, t);
 }
 
 // Writes back every pending pbest_pos row on the panel layout (pbest_pos :=
@@ -420,12 +490,17 @@ int panel_blocks_per_sm(int width, int stages, int fid, int D) {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int width, int stages, int grid, cudaStream_t st) {
-    if (!panel_supported(width, stages, s.D) || !s.pflag || !s.work || s.Np % 128 != 0) return cudaErrorInvalidValue;
+cudaError_t launch_sync_panel(const SwarmDev& s, int fid, int width, int stages, int grid, int iters,
+                              bool stall_barrier, cudaStream_t st) {
+    if (!panel_supported(width, stages, s.D) || !s.pflag || !s.work || !s.bar || s.Np % 128 != 0 || iters < 1 ||
+        iters > kPanelMaxIters || grid < 1 || (unsigned long long)iters * ((unsigned long long)grid + 2ull) >= (1ull << 32))
+        return cudaErrorInvalidValue;
     const void* k = panel_kernel(width, stages, s.fast_cr && s.fast_clamp, fid);
     if (!k) return cudaErrorInvalidValue;
-    void* args[] = {const_cast<SwarmDev*>(&s)};
-    return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, panel_smem(stages, s.D), st);
+    unsigned int expect = (unsigned int)grid + (stall_barrier ? 1u : 0u);
+    void* args[] = {const_cast<SwarmDev*>(&s), &iters, &expect};
+    if (iters == 1) return cudaLaunchKernel(k, dim3(grid), dim3(kBlock), args, panel_smem(stages, s.D), st);
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(kBlock), args, panel_smem(stages, s.D), st);
 }
 
 cudaError_t launch_materialize_panel(const SwarmDev& s, int width, int grid, cudaStream_t st) {

@@ -37,8 +37,10 @@ CUPSO_OPT_GRID = 5
 CUPSO_OPT_SYNC_KERNEL = 6
 CUPSO_OPT_TIME_FITNESS = 7
 CUPSO_OPT_PARTICLES_PER_THREAD = 8
+CUPSO_OPT_ITERS_PER_LAUNCH = 9
 SYNC_KERNELS = {"auto": 0, "register": 1, "pipelined3": 2, "pipelined4": 3, "tiled": 4, "panel8": 5, "panel16": 6}
 CUPSO_OPT_FAULT_HOLD_LOCK = 100
+CUPSO_OPT_FAULT_STALL_BARRIER = 101
 
 # The names the library must export (every function of include/cupso.h).
 ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_step", "cupso_get_gbest",
@@ -68,7 +70,7 @@ class cupso_info(C.Structure):
                 ("sync_grid", C.c_int), ("async_grid", C.c_int), ("onchip_cluster", C.c_int),
                 ("sync_stages", C.c_int), ("sync_ppt", C.c_int), ("sync_tile", C.c_int), ("fitness_ms", C.c_float),
                 ("fitness_timed", C.c_int),
-                ("device_bytes", C.c_uint64), ("sync_panel", C.c_int)]
+                ("device_bytes", C.c_uint64), ("sync_panel", C.c_int), ("sync_iters_per_launch", C.c_int)]
 
 
 class cupso_problem(C.Structure):

@@ -42,6 +42,35 @@ def test_library_exports_every_declared_symbol(P):
     assert sorted(P.ABI_FUNCTIONS) == declared_functions()
 
 
+def _header_enum(prefix):
+    txt = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(%s\w*)\s*=\s*(-?\d+)" % prefix, txt)}
+
+
+def test_binding_constants_match_the_header(P):
+    """Every option, mode, SYNC kernel and return code the header defines has
+    the same value in the Python binding."""
+    for prefix in ("CUPSO_OPT_", "CUPSO_MODE_", "CUPSO_ERR_", "CUPSO_OK"):
+        for name, value in _header_enum(prefix).items():
+            assert getattr(P, name) == value, name
+    kernels = _header_enum("CUPSO_SYNC_KERNEL_")
+    assert {k: kernels["CUPSO_SYNC_KERNEL_" + k.upper()] for k in P.SYNC_KERNELS} == P.SYNC_KERNELS
+    assert len(P.SYNC_KERNELS) == len(kernels)
+
+
+def test_info_struct_matches_the_header(P):
+    """cupso_info's fields, in order, as the binding lays them out."""
+    txt = open(HEADER).read()
+    body = re.search(r"typedef struct \{((?:(?!typedef).)*?)\} cupso_info;", txt, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [n.strip() for n in decl.split(None, 1)[1].split(",")]
+    assert [f[0] for f in P.cupso_info._fields_] == names
+
+
 def test_status_strings(P):
     assert P.status_string(0) == "ok"
     assert "timed out" in P.status_string(P.CUPSO_ERR_DEVICE_TIMEOUT)

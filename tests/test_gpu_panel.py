@@ -4,6 +4,8 @@ particle count, a single step from an oracle-provided state, switches between
 the panel kernel and kernels on the dimension-major layout in the middle of a
 run (the state is converted between them), and checkpoint/resume through
 cupso_get_state / cupso_set_state while the state is in panels."""
+import time
+
 import numpy as np
 import pytest
 
@@ -56,13 +58,19 @@ def test_panel_selection(P):
 @pytest.mark.parametrize("kernel,D", [("panel8", 16), ("panel8", 40), ("panel16", 32), ("panel16", 64),
                                       ("panel16", 48)])
 @pytest.mark.parametrize("fid", [0, 1, 2, 3, 4])
-def test_panel_trajectory_bit_exact(P, fid, kernel, D):
+@pytest.mark.parametrize("ipl", [1, 5, 0])
+def test_panel_trajectory_bit_exact(P, fid, kernel, D, ipl):
+    """ipl 1: one launch per iteration (a captured graph of 16, then single
+    launches); 5: cooperative launches of up to 5 iterations with a grid
+    barrier between them; 0 (default): one launch per cupso_step call."""
     N, T = 3000, 40            # 94 units of 32 particles, the last one ragged; padded to 3072
     with _panel_swarm(P, fid, N, D, 3, kernel) as s:
+        s.set_option(P.CUPSO_OPT_ITERS_PER_LAUNCH, ipl)
         assert s.info()["sync_panel"] == int(kernel[5:])
+        assert s.info()["sync_iters_per_launch"] == (ipl or 4096)
         s.step(1)
-        s.step(16)     # one captured graph (chunk 16)
-        s.step(23)     # graph + remainder
+        s.step(16)
+        s.step(23)
         st = s.state()
         rc, fit, idx, pos = s.gbest()
     ref = oracle_swarm(fid, N, D, 3).init().step_sync(T)
@@ -175,3 +183,71 @@ def test_panel_nan_fitness_sets_status(P, kernel):
     ref.set_state(pos, np.zeros_like(pos), pos, pf, 0)
     ref.step_sync(1)
     assert_state_equal(st, ref)
+
+
+@pytest.mark.parametrize("ipl", [2, 3, 0])
+def test_panel_multi_iteration_launch_shapes(P, ipl):
+    """Cooperative launches of several iterations on grids of every kind: more
+    warps than units (each warp's own first unit is all there is), a CTA count
+    asked for above what the SMs hold (the launch is clamped to it), and odd
+    step lengths that leave single launches behind: the oracle's trajectory."""
+    cases = [(3, 130, 16, "panel8", 0), (1, 2000, 32, "panel16", 0), (3, 20000, 24, "panel8", 1 << 16),
+             (2, 9000, 48, "panel16", 3)]
+    for fid, N, D, kernel, grid in cases:
+        with _panel_swarm(P, fid, N, D, 11, kernel) as s:
+            s.set_option(P.CUPSO_OPT_ITERS_PER_LAUNCH, ipl)
+            if grid:
+                s.set_option(P.CUPSO_OPT_GRID, grid)
+            for n in (7, 1, 4, 3):
+                s.step(n)
+            st = s.state()
+            rc, fit, idx, pos = s.gbest()
+        ref = oracle_swarm(fid, N, D, 11).init().step_sync(15)
+        assert rc == P.CUPSO_OK, (fid, N, D)
+        assert_state_equal(st, ref)
+        assert idx == ref.gbest_idx and same_bits(fit, ref.gbest_fit) and same_bits(pos, ref.gbest_pos)
+
+
+def test_panel_launch_forms_agree_at_scale(P):
+    """Rastrigin 65536 x 128 (16-dimension panels), 60 iterations in one
+    cupso_step call: one cooperative launch and one launch per iteration give
+    the same state, bit for bit."""
+    fid, N, D = 1, 65536, 128
+    out = []
+    for ipl in (0, 1):
+        with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 2, mode="sync") as s:
+            s.set_option(P.CUPSO_OPT_ITERS_PER_LAUNCH, ipl)
+            assert s.info()["sync_panel"] == 16
+            s.step(60)
+            rc, fit, idx, pos = s.gbest()
+            assert rc == P.CUPSO_OK
+            out.append((s.state(), idx, fit, pos))
+    (a, ia, fa, pa), (b, ib, fb, pb) = out
+    for k in ("pos", "v", "pbest_pos", "pbest_fit"):
+        assert np.array_equal(a[k].view(np.uint32), b[k].view(np.uint32)), k
+    assert ia == ib and same_bits(fa, fb) and same_bits(pa, pb)
+
+
+def test_panel_barrier_wait_expires_and_reports(P):
+    """A multi-iteration launch whose barrier waits for one CTA more than it has:
+    every wait ends at the limit, the step reports CUPSO_ERR_DEVICE_TIMEOUT, and
+    the context stays usable (status cleared, the swarm steps again, and a new
+    swarm still follows the oracle)."""
+    fid, N, D = 3, 20000, 32
+    with _panel_swarm(P, fid, N, D, 7, "panel8") as s:
+        s.set_option(P.CUPSO_OPT_WAIT_LIMIT_NS, 50_000_000)      # 50 ms
+        s.set_option(P.CUPSO_OPT_FAULT_STALL_BARRIER, 1)
+        t0 = time.time()
+        s.step(3)
+        rc, _, _, _ = s.gbest()
+        assert rc == P.CUPSO_ERR_DEVICE_TIMEOUT
+        assert time.time() - t0 < 30
+        s.set_option(P.CUPSO_OPT_FAULT_STALL_BARRIER, 0)
+        s.set_option(P.CUPSO_OPT_CLEAR_STATUS, 1)
+        s.step(4)
+        rc, _, _, _ = s.gbest()
+        assert rc == P.CUPSO_OK
+    with _panel_swarm(P, fid, 3000, 16, 5, "panel8") as s2:
+        s2.step(9)
+        st = s2.state()
+    assert_state_equal(st, oracle_swarm(fid, 3000, 16, 5).init().step_sync(9))

@@ -161,9 +161,8 @@ typedef enum {
     CUPSO_SYNC_KERNEL_PANEL16 = 6     /* the same with panels of 16 dimensions (64 bytes per particle,
                                          the granularity of HBM reads), four threads per particle;
                                          D % 16 == 0, D >= 32. AUTO, for D % 8 == 0: the tiled kernel
-                                         up to 2^22 particle-dimensions (D <= 64 unless the fitness
-                                         has cos 2 pi x), above that 16-dimension panels for
-                                         D >= 128 outside 8192 < N < 65536, else 8                 */
+                                         below 2^17 particle-dimensions, above that 16-dimension
+                                         panels for D >= 128 or N <= 8192, else 8                  */
 } cupso_sync_kernel;
 
 typedef struct {

@@ -130,13 +130,12 @@ int sync_tile(const cupso_swarm* h) {
     if (h->sync_kernel != CUPSO_SYNC_KERNEL_AUTO || h->D < 8) return 0;
     const bool has_cos = h->fid == CUPSO_RASTRIGIN || h->fid == CUPSO_ACKLEY;
     if (h->panel_ok && h->D % 8 == 0) {
-        // against the panel kernel (sweep on one GB300, N = 8192 .. 524288, D = 16 .. 256,
-        // Rosenbrock and Rastrigin): the tiled kernel is the faster one up to 2^22
-        // particle-dimensions per iteration -- without cos(2 pi x) in the fitness only
-        // up to D = 64 -- and the panel kernel above
-        const long long pd = (long long)h->N * h->D, cut = 1ll << 22;
-        const bool tiled = pd <= cut && (has_cos || h->D <= 64);
-        return tiled ? tiled_particles(h->N, h->D, h->num_sms) : 0;
+        // against the panel kernel running each cupso_step call in one cooperative
+        // launch (sweep on one GB300, N = 4096 .. 262144, D = 16 .. 256, Rosenbrock and
+        // Rastrigin, steps of 96 iterations): the tiled kernel is the faster one only
+        // below 2^17 particle-dimensions
+        const long long pd = (long long)h->N * h->D;
+        return pd < (1ll << 17) ? tiled_particles(h->N, h->D, h->num_sms) : 0;
     }
     const long long per_sm = (has_cos || h->D <= 64) ? 896 : 224;
     if ((long long)h->N > per_sm * h->num_sms) return 0;
@@ -168,9 +167,8 @@ int sync_stages(const cupso_swarm* h) {
 // panel width and ring depth (5 panels where the panels allow, else 3); width
 // 0 when the dimension-major kernels run. AUTO takes the panel kernel for
 // D % 8 == 0 wherever the tiled kernel is not the faster one; 16-dimension
-// panels for D >= 128 except between 8192 and 65536 particles, 8-dimension
-// panels otherwise (Rosenbrock 2^20 x 64: a tie, 0.239 ms per iteration
-// either way).
+// panels for D >= 128 or up to 8192 particles, 8-dimension panels otherwise
+// (Rosenbrock 2^20 x 64: a tie, 0.239 ms per iteration either way).
 struct PanelCfg {
     int width = 0, stages = 0;
 };
@@ -183,9 +181,11 @@ PanelCfg panel_cfg(const cupso_swarm* h) {
         case CUPSO_SYNC_KERNEL_PANEL16: widths[0] = 16; break;
         case CUPSO_SYNC_KERNEL_AUTO:
             if (sync_tile(h)) return c;
-            // 16-dimension panels for long particles (D >= 128) outside 8192 < N < 65536,
-            // 8 otherwise (the same sweep; the two are within a few percent elsewhere)
-            if (h->D % 16 == 0 && h->D >= 128 && (h->N <= 8192 || h->N >= 65536)) widths[0] = 16;
+            // 16-dimension panels (units of 8 particles) for long particles (D >= 128)
+            // and for swarms of up to 8192 particles, 8 otherwise (the same sweep; where
+            // the other width wins, by at most 10 %, the units divide unevenly over
+            // the warps)
+            if (h->D % 16 == 0 && (h->D >= 128 || h->N <= 8192)) widths[0] = 16;
             widths[1] = 8;
             break;
         default: return c;

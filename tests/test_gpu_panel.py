@@ -29,8 +29,8 @@ def _panel_swarm(P, fid, N, D, seed, kernel):
 def test_panel_selection(P):
     """AUTO on a large swarm: 16-dimension panels for D >= 128, 8 below (the deepest
     ring the panels allow, 5, else 3); none for D % 8 != 0 or a single panel.
-    Smaller swarms: the tiled kernel up to 2^22 particle-dimensions (D <= 64
-    without cos(2 pi x)), 8-dimension panels between 8192 and 65536 particles."""
+    Smaller swarms: 16-dimension panels up to 8192 particles, the tiled kernel
+    below 2^17 particle-dimensions."""
     want = {64: (8, 5), 32: (8, 5), 48: (8, 5), 16: (8, 3), 24: (8, 3), 40: (8, 5), 128: (16, 5), 12: (0, None),
             8: (0, None)}
     for D, (width, stages) in want.items():
@@ -39,9 +39,10 @@ def test_panel_selection(P):
             assert i["sync_panel"] == width, D
             if width:
                 assert i["sync_stages"] == stages and i["sync_ppt"] == 1, D
-    for N, D, fid, width, tile in [(131072, 64, 3, 8, False), (65536, 128, 1, 16, False), (65536, 64, 1, 0, True),
-                                   (65536, 32, 3, 0, True), (262144, 32, 3, 8, False), (8192, 128, 3, 16, False),
-                                   (32768, 128, 3, 8, False), (32768, 128, 1, 0, True)]:
+    for N, D, fid, width, tile in [(131072, 64, 3, 8, False), (65536, 128, 1, 16, False), (65536, 64, 1, 8, False),
+                                   (65536, 32, 3, 8, False), (262144, 32, 3, 8, False), (8192, 128, 3, 16, False),
+                                   (32768, 128, 3, 16, False), (16384, 64, 1, 8, False), (8192, 32, 3, 16, False),
+                                   (4096, 16, 1, 0, True), (2048, 32, 3, 0, True)]:
         with P.Swarm(D, N, BOUNDS[fid], W, C12, C12, fid, 1, mode="sync") as s:
             i = s.info()
             assert i["sync_panel"] == width and (i["sync_tile"] > 0) == tile, (N, D, fid)

@@ -52,22 +52,22 @@ def test_sync_kernel_selection(P):
         assert s.info()["sync_stages"] == 3
     with gpu_swarm(P, 3, 5000, 2, 1, "sync_pipelined4") as s:   # too few dimension pairs: register kernel
         assert s.info()["sync_stages"] == 0
-    with gpu_swarm(P, 1, 20000, 16, 1, "sync") as s:            # few particles per SM, D >= 8: tiled
-        assert s.info()["sync_tile"] == 64 and s.info()["sync_stages"] == 0   # 64 x 16 items, 313 tiles
+    with gpu_swarm(P, 1, 20000, 15, 1, "sync") as s:            # few particles per SM, D % 8 != 0: tiled
+        assert s.info()["sync_tile"] > 0 and s.info()["sync_stages"] == 0
+    with gpu_swarm(P, 1, 4096, 16, 1, "sync") as s:             # below 2^17 particle-dimensions: tiled
+        assert s.info()["sync_tile"] > 0 and s.info()["sync_panel"] == 0
     with gpu_swarm(P, 1, 65536, 128, 1, "sync") as s:           # 2^23 particle-dimensions: panels
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
     with gpu_swarm(P, 1, 65536, 120, 1, "sync") as s:           # D % 8 == 0, 120 / 16 not whole: 8-wide
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
     with gpu_swarm(P, 3, 65536, 127, 1, "sync") as s:           # D % 8 != 0, narrow tiles, no cos: from ~224 per SM
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 0
-    with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # wide tiles: tiled up to 2^22 particle-dimensions
-        assert s.info()["sync_tile"] == 128
-    with gpu_swarm(P, 3, 1 << 18, 16, 1, "sync") as s:          # 2^22, D <= 64: still tiled
-        assert s.info()["sync_tile"] > 0
-    with gpu_swarm(P, 1, 32768, 256, 1, "sync") as s:           # 2^23: panels (8 wide at this N)
+    with gpu_swarm(P, 3, 65536, 32, 1, "sync") as s:            # 2^21, D < 128, N > 8192: 8-wide panels
         assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
-    with gpu_swarm(P, 3, 16384, 128, 1, "sync") as s:           # 2^21 but D > 64, no cos: panels
-        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 8
+    with gpu_swarm(P, 3, 8192, 32, 1, "sync") as s:             # 2^18 with at most 8192 particles: 16-wide
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
+    with gpu_swarm(P, 1, 32768, 256, 1, "sync") as s:           # D >= 128: 16-wide
+        assert s.info()["sync_tile"] == 0 and s.info()["sync_panel"] == 16
 
 
 @pytest.mark.parametrize("N,D", [(1, 1), (5, 3), (127, 2), (129, 5), (3000, 7), (1024, 32)])

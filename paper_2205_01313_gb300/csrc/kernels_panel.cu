@@ -64,16 +64,21 @@ __device__ __forceinline__ size_t panel_off(const SwarmDev& s, int q, uint32_t i
 }
 
 // Hands out the units after the warps' own first ones (units base, base + 1,
-// ...; base = the number of warps): for a swarm with many units per warp, one
-// counter increment per two units (fewer atomics on one address); for one
-// with few, one per unit, since the iteration lasts as long as the warp with
-// the most units and a two-unit grain doubles that excess.
+// ...; base = the number of warps). For a swarm with many units per warp, one
+// counter increment per two units (fewer atomics on one address) until the
+// last two units per warp, which go out one at a time: an iteration lasts as
+// long as the warp with the most work, and a two-unit grain at the end would
+// double that excess. A swarm with few units per warp gets single units only.
 struct UnitFeed {
     uint32_t spare = 0xFFFFFFFFu;   // the second unit of the last fetch, if not yet taken
     uint32_t base;
-    bool pairs;
-    __device__ __forceinline__ UnitFeed(uint32_t nunits, uint32_t nwarps)
-        : base(nwarps), pairs(nunits >= 8u * nwarps) {}
+    uint32_t npairs;                // fetches 0 .. npairs - 1 hand out two units
+    __device__ __forceinline__ UnitFeed(uint32_t nunits, uint32_t nwarps) : base(nwarps), npairs(0u) {
+        if (nunits >= 8u * nwarps) {
+            const uint32_t dyn = nunits - nwarps, tail = 2u * nwarps;
+            npairs = (dyn - tail) / 2u;
+        }
+    }
     __device__ __forceinline__ uint32_t next(const SwarmDev& s, int lane_id) {
         if (spare != 0xFFFFFFFFu) {
             const uint32_t u = spare;
@@ -83,7 +88,7 @@ struct UnitFeed {
         uint32_t k = 0;
         if (lane_id == 0) k = atomicAdd(s.work, 1u);
         k = __shfl_sync(0xFFFFFFFFu, k, 0);
-        if (!pairs) return base + k;
+        if (k >= npairs) return base + npairs + k;   // single units after the pairs: 2 npairs + (k - npairs)
         spare = base + 2u * k + 1u;
         return base + 2u * k;
     }
@@ -175,15 +180,17 @@ __device__ __forceinline__ void panel_sum(FitAcc<FIT>& a, const float4& X, int d
     }
 }
 
-// gbest_pos of iteration parity nxt from the winner's pbest_pos (or from pos
-// when its row is still pending); run by the last CTA of an iteration.
+// gbest_pos of iteration parity nxt from the winner's pbest_pos, or from pos
+// when its row is still pending -- exactly when the key improved in this
+// iteration (K: the key it started from): the winner then improved its own
+// pbest, and a gbest particle that did not improve has had its row written
+// in this iteration. Run by the last CTA of an iteration.
 template <int W>
-__device__ __forceinline__ void gather_gbest_panel(const SwarmDev& s, int nxt) {
+__device__ __forceinline__ void gather_gbest_panel(const SwarmDev& s, int nxt, unsigned long long K) {
     const unsigned long long knew = __ldcg(s.gkey + nxt);
     const uint32_t g = (uint32_t)(knew & 0xFFFFFFFFull);
     if (g < (uint32_t)s.N) {
-        const bool lazy = __ldcg(s.pflag + g) != 0;
-        const float* src = lazy ? s.x : s.pb;
+        const float* src = knew < K ? s.x : s.pb;
         for (int d = threadIdx.x; d < s.D; d += blockDim.x)
             s.G[(size_t)nxt * s.D + d] = __ldcg(src + panel_off<W>(s, d / W, g) + (d % W));
     }
@@ -351,7 +358,7 @@ __global__ void __launch_bounds__(kBlock, 3) sync_panel_kernel(const __grid_cons
         const bool final_it = it + 1 == iters;
         if (s_last) {
             __threadfence();
-            gather_gbest_panel<W>(s, nxt);
+            gather_gbest_panel<W>(s, nxt, K);
             __syncthreads();
             if (threadIdx.x == 0) {
                 s.gkey[cur] = __ldcg(s.gkey + nxt);

@@ -1099,7 +1099,7 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         const float sx = std::isfinite(span) && span > 0.0f ? 448.0f / span : 1.0f;
         rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
         if (rc) return rc;
-        if (h->D <= M && (size_t)h->D * h->D <= ((size_t)1 << 26)) {
+        if (h->D <= M && h->D <= kGramMaxD) {
             // FP64 Gram data: A^T A, A^T b (device) and b^T b (host, from b)
             CUPSO_CUDA(cudaMalloc(&L->gram_buf, sizeof(double) * ((size_t)h->D * h->D + h->D)), "cudaMalloc (gram)");
             L->gram.Gm = static_cast<double*>(L->gram_buf);

@@ -129,11 +129,15 @@ cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigne
 // Blocks of the candidate selection (one particle per thread).
 int lsq_cand_blocks(int Np);
 // FP64 Gram data of the rescoring (Gm = A^T A, cvec = A^T b, bb = b^T b); Gm null: direct form.
+// The Gram form keeps 4 candidates x D doubles in shared memory per block.
+constexpr int kGramMaxD = 6144;
 struct LsqGram {
     double* Gm = nullptr;
     double* cvec = nullptr;
     double bb = 0.0;
 };
+// Gm, cvec from A and b; raises the rescoring kernel's shared-memory limit for
+// D (D <= kGramMaxD).
 cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, cudaStream_t st);
 // Steps 4-5 with an approximate fitness. lazy: flags is s.pflag and the
 // improved particles' pbest_pos rows are left to the next move (and to the

@@ -446,14 +446,21 @@ __device__ void accept_best(const SwarmDev& s, const float* __restrict__ src, co
                             const double* __restrict__ partial, int chunks, double* __restrict__ g64,
                             int* __restrict__ stale) {
     __shared__ double fsum[kCand];
+    __shared__ unsigned long long skey[kCand];
     __shared__ int s_best;
-    __shared__ double s_f;
+    __shared__ double s_f, s_g64;
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    // the candidate list and gbest's FP64 value, read at once
+    if (threadIdx.x < kCand) skey[threadIdx.x] = top[threadIdx.x];
+    if (threadIdx.x == 32) s_g64 = __ldcg(g64);
+    __syncthreads();
     for (int c = warp; c < kCand; c += nw) {
         double f = 0.0;
-        for (int h = lane; h < chunks; h += 32) f += __ldcg(partial + (size_t)c * chunks + h);
+        if (skey[c] != kKeyNone)
+#pragma unroll 4
+            for (int h = lane; h < chunks; h += 32) f += __ldcg(partial + (size_t)c * chunks + h);
         for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
         if (lane == 0) fsum[c] = f;
     }
@@ -462,7 +469,7 @@ __device__ void accept_best(const SwarmDev& s, const float* __restrict__ src, co
         int best = -1;
         double bf = 0.0;
         for (int c = 0; c < kCand; ++c) {
-            const unsigned long long k = top[c];
+            const unsigned long long k = skey[c];
             if (k == kKeyNone) break;
             const double f = fsum[c];
             const int i = (int)(k & 0xFFFFFFFFull);
@@ -471,7 +478,7 @@ __device__ void accept_best(const SwarmDev& s, const float* __restrict__ src, co
                 bf = f;
             }
         }
-        s_best = (best >= 0 && bf < *g64) ? best : -1;
+        s_best = (best >= 0 && bf < s_g64) ? best : -1;
         s_f = bf;
     }
     __syncthreads();
@@ -857,8 +864,14 @@ int lsq_cand_blocks(int Np) { return (Np + kSel - 1) / kSel; }
 
 cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec,
                             cudaStream_t st) {
+    if (D > kGramMaxD) return cudaErrorInvalidValue;
     lsq_gram_kernel<<<dim3((D + 31) / 32, (D + 31) / 32), 256, 0, st>>>(A, b, M, D, Gm, cvec);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the rescoring keeps 4 candidates x D doubles in shared memory: past the
+    // default 48 KB from D = 1537 on
+    return cudaFuncSetAttribute(lsq_rescore_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(double) * 4 * (size_t)D));
 }
 
 // cand: [blocks * 16] + [16] scratch; partial: [16 * chunks]; flags: [Np / 4].

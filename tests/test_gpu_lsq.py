@@ -142,11 +142,13 @@ def test_lsq_exact_swarm_bit_exact(P, precision, N, D, M):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
-@pytest.mark.parametrize("N,D,M", [(2000, 96, 640), (1000, 200, 120)])
+@pytest.mark.parametrize("N,D,M", [(2000, 96, 640), (1000, 200, 120), (300, 1600, 1664)])
 def test_lsq_approx_swarm_gbest_is_fp64_verified(P, precision, N, D, M):
     """pbest follows the approximate fitness; gbest only moves to FP64-verified
     improvements: its FP64 fitness never increases and equals the oracle's
-    ||A g - b||^2. D <= M rescores in the Gram form (A^T A), D > M row by row."""
+    ||A g - b||^2. D <= M rescores in the Gram form (A^T A), D > M row by row;
+    D = 1600 holds 50 KB of candidates in shared memory, past the default
+    48 KB limit."""
     A, b, _ = _problem(M, D, 1, seed=11)
     with _lsq_swarm(P, A, b, N, 5, precision) as s:
         prev64 = s.gbest_f64()

@@ -452,8 +452,7 @@ def batch_report(P, a, stream, plain_every=1):
     """512 independent swarms (N ~ U{64..8192}, D ~ U{8..256}, fitness cycling
     sphere/Rastrigin/Ackley/Rosenbrock), 500 iterations each, solved (1) by
     cupso_solve_batch and (2) plain: per swarm cupso_create, cupso_step(500)
-    (one launch per iteration, or for a swarm in the panel layout one
-    cooperative launch), cupso_get_gbest, cupso_destroy, on one stream -- timed on every
+    with one launch per iteration, cupso_get_gbest, cupso_destroy, on one stream -- timed on every
     `plain_every`-th swarm and scaled by particle-dimension updates. Both through
     the public API with host results. Correctness: swarms re-solved alone
     through the batch API must reproduce the batched results bit for bit."""
@@ -478,7 +477,8 @@ def batch_report(P, a, stream, plain_every=1):
         p = probs[k]
         h = P.cupso_create(p["D"], p["N"], p["bounds"], p["w"], p["c1"], p["c2"], p["fitness_id"], p["seed"])
         P.cupso_set_stream(h, stream.cuda_stream)
-        P.cupso_set_option(h, P.CUPSO_OPT_GRAPH_CHUNK, 0)   # no graph capture for a one-off swarm
+        P.cupso_set_option(h, P.CUPSO_OPT_GRAPH_CHUNK, 0)       # one launch per iteration,
+        P.cupso_set_option(h, P.CUPSO_OPT_ITERS_PER_LAUNCH, 1)  # also for a swarm in the panel layout
         # cupso_create draws with swarm id 0, so this trajectory differs from the batch's
         # (same work, other random streams); only its time is used here
         P.cupso_step(h, iters)
@@ -507,8 +507,7 @@ def batch_report(P, a, stream, plain_every=1):
                     "api": "cupso_solve_batch (init + 500 iterations + host results)"},
         "plain": {"seconds": plain_s, "sampled_swarms": len(sample), "sampled_seconds": plain_sample_s,
                   "value": total_pd / plain_s, "unit": UNIT,
-                  "api": "per swarm: cupso_create, cupso_step(500) (one launch per iteration; panel-layout "
-                         "swarms: one cooperative launch), cupso_get_gbest, "
+                  "api": "per swarm: cupso_create, cupso_step(500) one launch per iteration, cupso_get_gbest, "
                          "cupso_destroy; every %d-th swarm timed, scaled by particle-dimension updates"
                          % max(1, plain_every)},
         "batched_over_plain": plain_s / batched_s,

@@ -214,6 +214,19 @@ CUPSO_API int cupso_step(cupso_handle h, int iters);
  * are filled in that case too. */
 CUPSO_API int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx_out);
 
+/* The same result without waiting, for a loop that reads every step's gbest
+ * while the next steps run. cupso_gbest_post queues, on the handle's stream
+ * after the work queued so far, a snapshot of gbest (fitness key, index,
+ * position, sticky status) into result slot `slot` (0 or 1) and its copy to
+ * host memory on a second stream; it does not wait. cupso_gbest_wait waits for
+ * the copy of `slot` and returns it as cupso_get_gbest does (outputs may be
+ * NULL; the sticky status as the return value). A slot holds one result:
+ * wait for it before posting to it again (posting again first is
+ * CUPSO_ERR_INVALID_ARG; so is waiting on a slot with nothing posted).
+ * Single-precision swarms only. */
+CUPSO_API int cupso_gbest_post(cupso_handle h, int slot);
+CUPSO_API int cupso_gbest_wait(cupso_handle h, int slot, float* fit_out, float* pos_out, int64_t* idx_out);
+
 /* Wait, then copy the swarm state to host arrays in particle-major layout:
  * pos, v, pbest_pos are [N][D] (element i*D + d), pbest_fit is [N]; *t_out =
  * iterations completed. Any pointer may be NULL. */

@@ -108,6 +108,15 @@ struct cupso_swarm {
     // pinned host staging of the gbest reads (allocated on first use)
     void* pinned = nullptr;
     size_t pinned_bytes = 0;
+    // result slots of cupso_gbest_post / _wait (allocated on first use): a
+    // device record and a pinned host copy per slot, the copy stream, and per
+    // slot the events of the snapshot and of its copy
+    char* rec_dev = nullptr;
+    char* rec_host = nullptr;
+    cudaStream_t rec_stream = nullptr;
+    cudaEvent_t rec_ev[2] = {nullptr, nullptr};
+    cudaEvent_t rec_done[2] = {nullptr, nullptr};
+    bool rec_posted[2] = {false, false};
 };
 
 namespace {
@@ -757,6 +766,38 @@ int cupso::solve_one_plain(const cupso_problem& p, int iters, cupso_result& r, c
 
 void cupso::set_cuda_error(cudaError_t e, const char* where) { cuda_fail(e, where); }
 
+namespace {
+
+// Bytes of one result record: key at 0, status at 8, position from 32.
+size_t rec_bytes(int D) { return (32 + sizeof(float) * (size_t)D + 255) / 256 * 256; }
+
+// gbest of one parity -- its key, the sticky status and its position -- into
+// a contiguous record.
+__global__ void gbest_record_kernel(const unsigned long long* __restrict__ key, const unsigned* __restrict__ status,
+                                    const float* __restrict__ G, int D, char* __restrict__ rec) {
+    float* pos = reinterpret_cast<float*>(rec + 32);
+    for (int d = threadIdx.x; d < D; d += blockDim.x) pos[d] = __ldcg(G + d);
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<unsigned long long*>(rec) = __ldcg(key);
+        *reinterpret_cast<unsigned*>(rec + 8) = __ldcg(status);
+    }
+}
+
+int ensure_records(cupso_swarm* h) {
+    if (h->rec_dev) return CUPSO_OK;
+    const size_t bytes = 2 * rec_bytes(h->D);
+    CUPSO_CUDA(cudaMalloc(&h->rec_dev, bytes), "cudaMalloc (gbest records)");
+    CUPSO_CUDA(cudaMallocHost(&h->rec_host, bytes), "cudaMallocHost (gbest records)");
+    CUPSO_CUDA(cudaStreamCreateWithFlags(&h->rec_stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    for (int k = 0; k < 2; ++k) {
+        CUPSO_CUDA(cudaEventCreateWithFlags(&h->rec_ev[k], cudaEventDisableTiming), "cudaEventCreate");
+        CUPSO_CUDA(cudaEventCreateWithFlags(&h->rec_done[k], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    return CUPSO_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int cupso_create(int D, int N, const cupso_bounds* bounds, float w, float c1, float c2, int fitness_id,
@@ -969,6 +1010,51 @@ int cupso_get_gbest(cupso_handle h, float* fit_out, float* pos_out, int64_t* idx
     if (fit_out) *fit_out = key_to_fit(key);
     if (idx_out) *idx_out = (int64_t)(key & 0xFFFFFFFFull);
     rc = status_code(st);
+    if (rc) fail(rc, "device status set: %s", cupso_status_string(rc));
+    return rc;
+}
+
+int cupso_gbest_post(cupso_handle h, int slot) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (h->fp64) return fail(CUPSO_ERR_UNSUPPORTED, "double-precision swarm: use the _fp64 functions%s");
+    if (slot != 0 && slot != 1) return fail(CUPSO_ERR_INVALID_ARG, "slot must be 0 or 1%s");
+    if (h->rec_posted[slot]) return fail(CUPSO_ERR_INVALID_ARG, "slot already holds a result; wait for it first%s");
+    int rc = ensure_records(h);
+    if (rc) return rc;
+    const size_t rb = rec_bytes(h->D);
+    char* dev = h->rec_dev + (size_t)slot * rb;
+    const int cur = (int)(h->t_host & 1u);
+    // the snapshot follows the queued steps on the handle's stream; the next
+    // step cannot change what it copies (a step rewrites these words only
+    // after the stream reaches it). Its copy to the host runs on the second
+    // stream, beside the next steps.
+    gbest_record_kernel<<<1, 256, 0, h->stream>>>(h->dev.gkey + cur, h->dev.status, h->dev.G + (size_t)cur * h->D,
+                                                  h->D, dev);
+    CUPSO_CUDA(cudaGetLastError(), "gbest record launch");
+    CUPSO_CUDA(cudaEventRecord(h->rec_ev[slot], h->stream), "cudaEventRecord");
+    CUPSO_CUDA(cudaStreamWaitEvent(h->rec_stream, h->rec_ev[slot], 0), "cudaStreamWaitEvent");
+    CUPSO_CUDA(cudaMemcpyAsync(h->rec_host + (size_t)slot * rb, dev, rb, cudaMemcpyDeviceToHost, h->rec_stream),
+               "cudaMemcpyAsync");
+    CUPSO_CUDA(cudaEventRecord(h->rec_done[slot], h->rec_stream), "cudaEventRecord");
+    h->rec_posted[slot] = true;
+    return CUPSO_OK;
+}
+
+int cupso_gbest_wait(cupso_handle h, int slot, float* fit_out, float* pos_out, int64_t* idx_out) {
+    if (!h) return fail(CUPSO_ERR_INVALID_ARG, "handle is NULL%s");
+    if (slot != 0 && slot != 1) return fail(CUPSO_ERR_INVALID_ARG, "slot must be 0 or 1%s");
+    if (!h->rec_posted[slot]) return fail(CUPSO_ERR_INVALID_ARG, "nothing posted to this slot%s");
+    CUPSO_CUDA(cudaEventSynchronize(h->rec_done[slot]), "cudaEventSynchronize");
+    h->rec_posted[slot] = false;
+    const char* rec = h->rec_host + (size_t)slot * rec_bytes(h->D);
+    unsigned long long key = 0;
+    unsigned st = 0;
+    std::memcpy(&key, rec, 8);
+    std::memcpy(&st, rec + 8, 4);
+    if (pos_out) std::memcpy(pos_out, rec + 32, sizeof(float) * (size_t)h->D);
+    if (fit_out) *fit_out = key_to_fit(key);
+    if (idx_out) *idx_out = (int64_t)(key & 0xFFFFFFFFull);
+    const int rc = status_code(st);
     if (rc) fail(rc, "device status set: %s", cupso_status_string(rc));
     return rc;
 }
@@ -1307,6 +1393,17 @@ int cupso_destroy(cupso_handle h) {
         delete h->lsq;
         h->lsq = nullptr;
     }
+    if (h->rec_stream) {
+        cudaError_t e = cudaStreamSynchronize(h->rec_stream);
+        if (e != cudaSuccess && rc == CUPSO_OK) rc = cuda_fail(e, "cudaStreamSynchronize");
+        cudaStreamDestroy(h->rec_stream);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (h->rec_ev[k]) cudaEventDestroy(h->rec_ev[k]);
+        if (h->rec_done[k]) cudaEventDestroy(h->rec_done[k]);
+    }
+    if (h->rec_dev) cudaFree(h->rec_dev);
+    if (h->rec_host) cudaFreeHost(h->rec_host);
     if (h->arena) cudaFree(h->arena);
     if (h->pinned) cudaFreeHost(h->pinned);
     if (h->capture) cudaStreamDestroy(h->capture);

@@ -47,7 +47,7 @@ ABI_FUNCTIONS = ("cupso_create", "cupso_set_stream", "cupso_set_option", "cupso_
                  "cupso_get_state", "cupso_set_state", "cupso_get_info", "cupso_solve_batch", "cupso_destroy",
                  "cupso_status_string", "cupso_last_error", "cupso_tree_step_noalloc", "cupso_lsq_eval",
                  "cupso_set_lsq", "cupso_get_gbest_f64", "cupso_create_fp64", "cupso_get_gbest_fp64",
-                 "cupso_get_state_fp64", "cupso_set_state_fp64")
+                 "cupso_get_state_fp64", "cupso_set_state_fp64", "cupso_gbest_post", "cupso_gbest_wait")
 
 CUPSO_LSQ = 5
 CUPSO_LSQ_FP32, CUPSO_LSQ_BF16, CUPSO_LSQ_FP8, CUPSO_LSQ_FP64 = 0, 1, 2, 3
@@ -101,6 +101,8 @@ def _load():
     L.cupso_set_option.argtypes = [h, C.c_int, C.c_longlong]
     L.cupso_step.argtypes = [h, C.c_int]
     L.cupso_get_gbest.argtypes = [h, f32p, f32p, C.POINTER(C.c_int64)]
+    L.cupso_gbest_post.argtypes = [h, C.c_int]
+    L.cupso_gbest_wait.argtypes = [h, C.c_int, f32p, f32p, C.POINTER(C.c_int64)]
     L.cupso_get_state.argtypes = [h, f32p, f32p, f32p, f32p, C.POINTER(C.c_uint32)]
     L.cupso_set_state.argtypes = [h, f32p, f32p, f32p, f32p, C.c_uint32]
     L.cupso_get_info.argtypes = [h, C.POINTER(cupso_info)]
@@ -193,6 +195,22 @@ def cupso_get_gbest(h, D, pos_out=None):
     rc = _lib.cupso_get_gbest(h, C.byref(fit), _f32p(pos), C.byref(idx))
     if rc not in (CUPSO_OK, CUPSO_ERR_DEVICE_TIMEOUT, CUPSO_ERR_NAN):
         raise CupsoError(rc, "cupso_get_gbest")
+    return rc, np.float32(fit.value), int(idx.value), pos
+
+
+def cupso_gbest_post(h, slot):
+    """Queues a copy of the current gbest into result slot 0 or 1; does not wait."""
+    _check(_lib.cupso_gbest_post(h, int(slot)), "cupso_gbest_post")
+
+
+def cupso_gbest_wait(h, D, slot, pos_out=None):
+    """Waits for result slot `slot`; returns (status, fit, idx, pos) as cupso_get_gbest."""
+    pos = pos_out if pos_out is not None else np.empty(int(D), np.float32)
+    fit = C.c_float()
+    idx = C.c_int64()
+    rc = _lib.cupso_gbest_wait(h, int(slot), C.byref(fit), _f32p(pos), C.byref(idx))
+    if rc not in (CUPSO_OK, CUPSO_ERR_DEVICE_TIMEOUT, CUPSO_ERR_NAN):
+        raise CupsoError(rc, "cupso_gbest_wait")
     return rc, np.float32(fit.value), int(idx.value), pos
 
 
@@ -345,6 +363,12 @@ class Swarm:
         if self.fp64:
             return cupso_get_gbest_fp64(self.h, self.D)
         return cupso_get_gbest(self.h, self.D)
+
+    def gbest_post(self, slot):
+        cupso_gbest_post(self.h, slot)
+
+    def gbest_wait(self, slot, pos_out=None):
+        return cupso_gbest_wait(self.h, self.D, slot, pos_out)
 
     def state(self):
         if self.fp64:

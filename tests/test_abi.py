@@ -92,6 +92,14 @@ def test_invalid_arguments_rejected_on_host(P, args):
     assert P.last_error() != ""
 
 
+def test_result_slots_reject_a_null_handle(P):
+    """The asynchronous gbest reads check their handle on the host."""
+    lib = P.lib()
+    f, i = C.c_float(), C.c_int64()
+    assert lib.cupso_gbest_post(None, 0) == P.CUPSO_ERR_INVALID_ARG
+    assert lib.cupso_gbest_wait(None, 0, C.byref(f), None, C.byref(i)) == P.CUPSO_ERR_INVALID_ARG
+
+
 @pytest.mark.parametrize("args,code", [
     (dict(D=0, N=10), "INVALID_ARG"), (dict(D=3, N=10, bounds=(1.0, -1.0, 1.0)), "INVALID_ARG"),
     (dict(D=3, N=10, bounds=(-1.0, 1.0, -2.0)), "INVALID_ARG"), (dict(D=3, N=10, fid=9), "INVALID_ARG"),

@@ -161,9 +161,11 @@ def test_panel_tiny_and_ragged_swarms(P, fid, N, D, kernel):
 
 
 @pytest.mark.parametrize("kernel", ["panel8", "panel16"])
-def test_panel_nan_fitness_sets_status(P, kernel):
+@pytest.mark.parametrize("T", [1, 3])
+def test_panel_nan_fitness_sets_status(P, kernel, T):
     """A NaN fitness (inf - inf inside the cubic at +-1e30) sets the sticky status;
-    the particle never becomes pbest or gbest; the step is the oracle's."""
+    the particle never becomes pbest or gbest; the steps are the oracle's (three
+    iterations: one cooperative launch)."""
     fid, N, D = 4, 300, 16
     bounds = (-1e30, 1e30, 1.0)
     rng = np.random.default_rng(2)
@@ -176,13 +178,13 @@ def test_panel_nan_fitness_sets_status(P, kernel):
         s.set_mode("sync")
         s.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[kernel])
         s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
-        s.step(1)
+        s.step(T)
         rc, fit, idx, _ = s.gbest()
         st = s.state()
         assert rc == P.CUPSO_ERR_NAN and idx != 77
     ref = oracle_swarm(fid, N, D, 1, bounds=bounds)
     ref.set_state(pos, np.zeros_like(pos), pos, pf, 0)
-    ref.step_sync(1)
+    ref.step_sync(T)
     assert_state_equal(st, ref)
 
 
@@ -252,3 +254,52 @@ def test_panel_barrier_wait_expires_and_reports(P):
         s2.step(9)
         st = s2.state()
     assert_state_equal(st, oracle_swarm(fid, 3000, 16, 5).init().step_sync(9))
+
+
+@pytest.mark.parametrize("kernel,D", [("panel8", 64), ("pipelined4", 37)])
+def test_gbest_result_slots_match_blocking_reads(P, kernel, D):
+    """cupso_gbest_post / cupso_gbest_wait, a step ahead as a pipelined loop
+    uses them: every result equals what cupso_get_gbest gives at that step (a
+    twin swarm stepped and read in lock step), and the misuse of a slot is
+    refused on the host."""
+    fid, N, T = 3, 5000, 9
+    with _panel_swarm(P, fid, N, D, 4, kernel) as s, _panel_swarm(P, fid, N, D, 4, kernel) as twin:
+        want = []
+        for k in range(T):
+            twin.step(1)
+            want.append(twin.gbest())
+        got = []
+        for k in range(T):
+            s.step(1)
+            s.gbest_post(k & 1)
+            if k > 0:
+                got.append(s.gbest_wait((k - 1) & 1))
+        got.append(s.gbest_wait((T - 1) & 1))
+        for (rc, fit, idx, pos), (rc2, fit2, idx2, pos2) in zip(got, want):
+            assert rc == rc2 == P.CUPSO_OK and idx == idx2
+            assert same_bits(fit, fit2) and same_bits(pos, pos2)
+        with pytest.raises(P.CupsoError):
+            s.gbest_wait(0)                  # nothing posted
+        s.gbest_post(0)
+        with pytest.raises(P.CupsoError):
+            s.gbest_post(0)                  # still holds a result
+        assert s.gbest_wait(0)[0] == P.CUPSO_OK
+
+
+def test_gbest_result_slot_carries_the_status(P):
+    """A NaN fitness reaches the reader through a result slot as through
+    cupso_get_gbest."""
+    fid, N, D = 4, 300, 16
+    bounds = (-1e30, 1e30, 1.0)
+    rng = np.random.default_rng(2)
+    pos = rng.uniform(-1, 1, (N, D)).astype(np.float32)
+    pos[77, :2] = [1e30, -1e30]
+    from oracle import oracle as O
+    pf = np.array([O.fitness(fid, p) for p in pos], np.float32)
+    with P.Swarm(D, N, bounds, W, C12, C12, fid, 1) as s:
+        s.set_mode("sync")
+        s.set_state(pos, np.zeros_like(pos), pos, pf, 0)
+        s.step(2)
+        s.gbest_post(1)
+        rc, fit, idx, _ = s.gbest_wait(1)
+        assert rc == P.CUPSO_ERR_NAN and idx != 77

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant_
         const uint32_t i0 = (uint32_t)(it % groups) * 4u;
         uint4 r[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) r[j] = philox4x32_10(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.key0, s.key1);
+        for (int j = 0; j < 4; ++j) r[j] = philox4x32_10_rk(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.rk0, s.rk1);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int d = 2 * g + h;
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constan
                 uint4 r[4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    r[j] = philox4x32_10(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.key0, s.key1);
+                    r[j] = philox4x32_10_rk(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.rk0, s.rk1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int d = 2 * g + h;

@@ -64,9 +64,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="default workload: skip the batch and least-squares keys of the line")
-    ap.add_argument("--lsq-launches", default="", choices=["", "bf16", "fp8", "fp32", "fp64"],
+    ap.add_argument("--lsq-launches", default="", choices=["", "bf16", "fp8", "fp32", "fp64", "bf16_rescore_fp64"],
                     help="lsq8192: only 6 + 20 iterations of one precision, one launch per kernel "
-                         "(no graph), for a profiler's launch list")
+                         "(no graph), for a profiler's launch list; bf16_rescore_fp64: BF16 with the "
+                         "FP64 Gram rescoring instead of the float-float one")
     return ap.parse_args()
 
 
@@ -591,10 +592,14 @@ def lsq_report(P, stream, quick):
     dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
     timed = {"bf16": 60, "fp8": 60, "fp32": 5, "fp64": 2} if quick else {"bf16": 300, "fp8": 300, "fp32": 20,
                                                                          "fp64": 3}
+    # the BF16 iteration once more with the FP64 Gram rescoring (the default is float-float)
+    timed["bf16_rescore_fp64"] = timed["bf16"]
     iters = {}
-    for prec, T in timed.items():
+    for name, T in timed.items():
+        prec = name.split("_")[0]
         with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
                      stream=stream.cuda_stream) as s:
+            s.set_option(P.CUPSO_OPT_LSQ_RESCORE, 1 if name.endswith("rescore_fp64") else 0)
             s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
             s.step(3)
             torch.cuda.synchronize()
@@ -604,7 +609,7 @@ def lsq_report(P, stream, quick):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / T
-            iters[prec] = {"ms_per_iter": ms, "iters_timed": T, "pd_per_s": N * D / (ms / 1e3),
+            iters[name] = {"ms_per_iter": ms, "iters_timed": T, "pd_per_s": N * D / (ms / 1e3),
                            "gbest_residual_f64": s.gbest_f64()}
     # the product alone, CUDA events around each of 50 launches inside further iterations
     fit_ms = {}
@@ -650,6 +655,7 @@ def lsq_report(P, stream, quick):
         "workload": "lsq8192", "N": N, "D": D, "M": M, "bounds": cfg["bounds"],
         "ms_per_iter": {k: v["ms_per_iter"] for k, v in iters.items()}, "runs": iters,
         "bf16_over_fp32": fp32 / bf, "fp8_over_fp32": fp32 / iters["fp8"]["ms_per_iter"],
+        "rescoring": "Gram form, off-diagonal part in float-float (bf16_rescore_fp64: FP64 arithmetic)",
         "fitness_product_ms": fit_ms,
         "roofline": {"bound": "tensor", "kernel": "lsq_tc_kernel<bf16>", "achieved": flops / (fit_ms["bf16"] / 1e3) / 1e12,
                      "peak": peak, "unit": "TFLOP/s", "frac": flops / (fit_ms["bf16"] / 1e3) / 1e12 / peak,
@@ -668,8 +674,10 @@ def lsq_launches(P, stream, prec):
     N, D, M = cfg["N"], cfg["D"], cfg["M"]
     A, b, _ = workloads.lsq_problem(M, D, seed=cfg["seed"])
     dA, db = torch.from_numpy(A).cuda(), torch.from_numpy(b).cuda()
+    name, prec = prec, prec.split("_")[0]
     with P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], P.CUPSO_LSQ, cfg["seed"],
                  stream=stream.cuda_stream) as s:
+        s.set_option(P.CUPSO_OPT_LSQ_RESCORE, 1 if name.endswith("rescore_fp64") else 0)
         s.set_lsq(dA.data_ptr(), db.data_ptr(), M, prec)
         s.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)
         s.step(6)
@@ -679,7 +687,7 @@ def lsq_launches(P, stream, prec):
         s.step(20)
         e1.record(stream)
         torch.cuda.synchronize()
-        return {"workload": "lsq8192", "precision": prec, "iters_timed": 20,
+        return {"workload": "lsq8192", "precision": name, "iters_timed": 20,
                 "ms_per_iter": e0.elapsed_time(e1) / 20, "graph": "none (one launch per kernel)"}
 
 

@@ -132,6 +132,12 @@ typedef enum {
                                        all CTAs resident, a grid barrier between iterations (each
                                        wait bounded by CUPSO_OPT_WAIT_LIMIT_NS); 0 (default): up to
                                        4096. Same results either way. */
+    CUPSO_OPT_LSQ_RESCORE = 10,   /* BF16 / FP8 least-squares swarm with D <= M: arithmetic of
+                                     the Gram-form rescoring of its gbest candidates. 0 (default):
+                                     the off-diagonal part of x^T (A^T A) x in float-float (pairs
+                                     of binary32 values, about 2^-44 of the terms' magnitudes);
+                                     1: binary64 throughout. The diagonal, linear and constant
+                                     terms are binary64 either way. */
     CUPSO_OPT_FAULT_HOLD_LOCK = 100, /* test hook: ASYNC starts with the gbest lock held, so every
                                         lock wait must expire and report CUPSO_ERR_DEVICE_TIMEOUT */
     CUPSO_OPT_FAULT_STALL_BARRIER = 101 /* test hook: a multi-iteration panel launch waits for one CTA
@@ -255,14 +261,20 @@ CUPSO_API int cupso_set_state(cupso_handle h, const float* pos, const float* v, 
  * by |x - g|, which shrinks as the swarm converges, instead of by |x|. In the
  * BF16 and FP8 modes the pbest decisions use the approximate fitness, while a
  * global best is accepted only after the (up to) 16 improved particles with
- * the lowest approximate fitness are rescored in FP64; gbest_fit is then that
- * FP64 value (rounded to float). This call evaluates the fitness of every
+ * the lowest approximate fitness are rescored in extended precision; gbest_fit
+ * is then that value (rounded to float). For D <= M (and D <= 6144) the
+ * rescoring takes the Gram form x^T G x - 2 c^T x + b^T b with G = A^T A and
+ * c = A^T b formed once here in FP64, its off-diagonal part in float-float
+ * or FP64 arithmetic (CUPSO_OPT_LSQ_RESCORE); otherwise it sums the residuals
+ * (A x - b)_m^2 in FP64 directly. This call evaluates the fitness of every
  * particle's pbest_pos (the end of Step 1 for such a swarm) and the gbest, and
  * waits. Steps of a CUPSO_LSQ swarm fail until it has been called. */
 CUPSO_API int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M, int precision);
 
-/* FP64 fitness ||A g - b||^2 of the current gbest_pos g of a least-squares
- * swarm (the residual by which the precision modes are compared). Waits. */
+/* Fitness ||A g - b||^2 of the current gbest_pos g of a least-squares swarm
+ * (the residual by which the precision modes are compared), as a double: FP32
+ * and FP64 swarms rescore g in FP64; BF16 and FP8 swarms return the value
+ * their rescoring accepted g with (see cupso_set_lsq). Waits. */
 CUPSO_API int cupso_get_gbest_f64(cupso_handle h, double* fit_out);
 
 /* Double-precision swarm: the paper's own precision (Sec. 5.1 runs FP64).

@@ -72,6 +72,7 @@ struct cupso_swarm {
     int hold_lock = 0;
     int stall_barrier = 0;          // test hook: the multi-iteration panel launch waits for one CTA more
     int iters_per_launch = 0;       // panel SYNC step: iterations per launch, 0 = automatic
+    int lsq_rescore = 0;            // CUPSO_OPT_LSQ_RESCORE: 0 float-float, 1 FP64
     int grid_override = 0;
     int onchip_cluster = 0;
     int sync_kernel = 0;            // CUPSO_SYNC_KERNEL_*
@@ -86,14 +87,14 @@ struct cupso_swarm {
         const float* b = nullptr;   // [M], borrowed
         int M = 0, precision = 0;
         LsqTcState tc;              // BF16 / FP8 operands and plan
-        void* buf = nullptr;        // f [Np] | cand [blocks*16 + 16 + ticket] | partial [16 * chunks] | g64
+        void* buf = nullptr;        // f [Np] | cand [lists*16 + 16 + ticket] | partial [16 * chunks] | g64
         float* f = nullptr;
         unsigned long long* cand = nullptr;
         double* partial = nullptr;
         double* g64 = nullptr;
         unsigned int* flags = nullptr;   // [Np / 4]: improved this iteration (one byte per particle)
         int chunks = 32;                 // pieces of the FP64 rescoring per candidate (set with A)
-        LsqGram gram;                    // FP64 A^T A etc. for the rescoring when D <= M
+        LsqGram gram;                    // A^T A etc. for the Gram-form rescoring when D <= M
         void* gram_buf = nullptr;
         bool time_fitness = false;       // CUPSO_OPT_TIME_FITNESS
         // the residual offsets of a new gbest are computed on a side stream while the
@@ -344,7 +345,7 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
 }
 
 // gbest of an approximate-fitness swarm from scratch, with `fit` (device, [Np])
-// as every particle's approximate fitness: the 16 lowest are rescored in FP64
+// as every particle's approximate fitness: the 16 lowest are rescored
 // and the best becomes gbest (and the reference point of the tensor-core
 // fitness, whose offsets are recomputed). t_dev ends at t.
 cudaError_t lsq_reset_gbest(cupso_swarm* h, const float* fit, uint32_t t, cudaStream_t st) {
@@ -877,6 +878,12 @@ int cupso_set_option(cupso_handle h, int key, long long value) {
                 return fail(CUPSO_ERR_INVALID_ARG, "iterations per launch out of range%s");
             h->iters_per_launch = (int)value;
             return CUPSO_OK;
+        case CUPSO_OPT_LSQ_RESCORE:
+            if (value != 0 && value != 1) return fail(CUPSO_ERR_INVALID_ARG, "rescoring: 0 (float-float) or 1 (FP64)%s");
+            h->lsq_rescore = (int)value;
+            if (h->lsq) h->lsq->gram.ff = value == 0;
+            drop_graph(h);
+            return CUPSO_OK;
         case CUPSO_OPT_FAULT_HOLD_LOCK:
             h->hold_lock = value ? 1 : 0;
             return CUPSO_OK;
@@ -1110,7 +1117,7 @@ int cupso_set_state(cupso_handle h, const float* pos, const float* v, const floa
     h->lazy_pending = false;
     h->panel = 0;   // uploaded dimension-major
     if (h->lsq && lsq_approx(h->lsq->precision)) {
-        // the given pbest_fit are approximate values: gbest only from FP64 rescoring
+        // the given pbest_fit are approximate values: gbest only from the rescoring
         CUPSO_CUDA(lsq_reset_gbest(h, h->dev.pf, t, h->stream), "lsq gbest");
     } else {
         CUPSO_CUDA(launch_recompute(h->dev, t, h->stream), "recompute launch");
@@ -1150,7 +1157,7 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
     L->b = b_dev;
     L->M = M;
     L->precision = precision;
-    const int nblk = lsq_cand_blocks(h->Np);
+    const int nlists = lsq_cand_lists(h->Np);
     // FP64 rescoring in pieces of at most 8 row pairs of A^T A (one per warp of
     // a block), as many pieces as give every SM two of the 4 x pieces blocks
     {
@@ -1159,21 +1166,23 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         const int per = std::min(8, std::max(1, (npairs + target - 1) / target));
         L->chunks = std::max(32, (npairs + per - 1) / per);
     }
-    // candidates: 16 per block, the merged 16, and the merging ticket
-    const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nblk * 16 + 17), 256) +
-                         align_up(sizeof(double) * 16 * L->chunks, 256) + align_up((size_t)h->Np, 256) + 256;
+    // candidates: 16 per list, the merged 16, and the merging ticket; partial
+    // sums: 16 per piece of the row-wise rescoring or tile of the float-float one
+    const int npart = std::max(L->chunks, lsq_ff_tiles(h->D));
+    const size_t bytes = align_up(sizeof(float) * h->Np, 256) + align_up(sizeof(unsigned long long) * (nlists * 16 + 17), 256) +
+                         align_up(sizeof(double) * 16 * npart, 256) + align_up((size_t)h->Np, 256) + 256;
     cudaError_t e = cudaMalloc(&L->buf, bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc (lsq)");
     char* p = static_cast<char*>(L->buf);
     L->f = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * h->Np, 256);
-    L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nblk * 16 + 17), 256);
-    L->partial = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * 16 * L->chunks, 256);
+    L->cand = reinterpret_cast<unsigned long long*>(p); p += align_up(sizeof(unsigned long long) * (nlists * 16 + 17), 256);
+    L->partial = reinterpret_cast<double*>(p); p += align_up(sizeof(double) * 16 * npart, 256);
     L->flags = reinterpret_cast<unsigned int*>(p); p += align_up((size_t)h->Np, 256);
     L->g64 = reinterpret_cast<double*>(p);
     const double inf = INFINITY;
     CUPSO_CUDA(cudaMemcpyAsync(L->g64, &inf, sizeof(double), cudaMemcpyHostToDevice, h->stream), "cudaMemcpyAsync");
     CUPSO_CUDA(cudaMemsetAsync(L->f, 0, sizeof(float) * h->Np, h->stream), "cudaMemsetAsync");
-    CUPSO_CUDA(cudaMemsetAsync(L->cand + (size_t)nblk * 16 + 16, 0, sizeof(unsigned long long), h->stream),
+    CUPSO_CUDA(cudaMemsetAsync(L->cand + (size_t)nlists * 16 + 16, 0, sizeof(unsigned long long), h->stream),
                "cudaMemsetAsync");
     if (lsq_approx(precision)) {
         CUPSO_CUDA(cudaStreamCreateWithFlags(&L->side, cudaStreamNonBlocking), "cudaStreamCreate");
@@ -1186,11 +1195,18 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
         if (rc) return rc;
         if (h->D <= M && h->D <= kGramMaxD) {
-            // FP64 Gram data: A^T A, A^T b (device) and b^T b (host, from b)
-            CUPSO_CUDA(cudaMalloc(&L->gram_buf, sizeof(double) * ((size_t)h->D * h->D + h->D)), "cudaMalloc (gram)");
+            // Gram data: A^T A, A^T b (device, FP64), A^T A again as binary32
+            // pairs for the float-float rescoring, and b^T b (host, from b)
+            const int ldf = (h->D + kFfTile - 1) / kFfTile * kFfTile;
+            const size_t n64 = align_up(sizeof(double) * ((size_t)h->D * h->D + h->D), 256);
+            CUPSO_CUDA(cudaMalloc(&L->gram_buf, n64 + sizeof(float2) * (size_t)ldf * ldf), "cudaMalloc (gram)");
             L->gram.Gm = static_cast<double*>(L->gram_buf);
             L->gram.cvec = L->gram.Gm + (size_t)h->D * h->D;
-            CUPSO_CUDA(lsq_launch_gram(A_dev, b_dev, M, h->D, L->gram.Gm, L->gram.cvec, h->stream), "gram launch");
+            L->gram.Gff = reinterpret_cast<float2*>(static_cast<char*>(L->gram_buf) + n64);
+            L->gram.ldf = ldf;
+            L->gram.ff = h->lsq_rescore == 0;
+            CUPSO_CUDA(lsq_launch_gram(A_dev, b_dev, M, h->D, L->gram.Gm, L->gram.cvec, L->gram.Gff, ldf, h->stream),
+                       "gram launch");
             std::vector<float> hb((size_t)M);
             CUPSO_CUDA(cudaMemcpyAsync(hb.data(), b_dev, sizeof(float) * M, cudaMemcpyDeviceToHost, h->stream),
                        "cudaMemcpyAsync");

@@ -126,19 +126,36 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
 cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int num_sms, cudaStream_t st);
 cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
                                     cudaStream_t st);
-// Blocks of the candidate selection (one particle per thread).
-int lsq_cand_blocks(int Np);
-// FP64 Gram data of the rescoring (Gm = A^T A, cvec = A^T b, bb = b^T b); Gm null: direct form.
-// The Gram form keeps 4 candidates x D doubles in shared memory per block.
+// Candidate lists of the selection (one of 16 keys per warp of 32 particles):
+// the candidate buffer holds lists x 16 keys, the merged 16 and a ticket.
+int lsq_cand_lists(int Np);
+// Gram data of the rescoring (Gm = A^T A, cvec = A^T b, bb = b^T b, all FP64);
+// Gm null: direct form. Gff: Gm as pairs (hi, lo) of binary32 values, ldf x ldf
+// with ldf = D rounded up to kFfTile and zeros outside D x D, for the
+// float-float rescoring (ff true); ff false rescores with FP64 arithmetic, whose
+// kernel keeps 4 candidates x D doubles in shared memory per block.
 constexpr int kGramMaxD = 6144;
+constexpr int kFfTile = 64;
 struct LsqGram {
     double* Gm = nullptr;
     double* cvec = nullptr;
     double bb = 0.0;
+    float2* Gff = nullptr;
+    int ldf = 0;
+    bool ff = true;
 };
-// Gm, cvec from A and b; raises the rescoring kernel's shared-memory limit for
-// D (D <= kGramMaxD).
-cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, cudaStream_t st);
+// Tiles of the float-float rescoring (the upper triangle of Gm in kFfTile
+// squares): four blocks each (4 candidates apiece), one partial sum per
+// candidate and tile.
+inline int lsq_ff_tiles(int D) {
+    const int nt = (D + kFfTile - 1) / kFfTile;
+    return nt * (nt + 1) / 2;
+}
+// Gm, cvec and Gff (ldf = D rounded up to kFfTile, zero-filled here) from A
+// and b; raises the FP64 rescoring kernel's shared-memory limit for D
+// (D <= kGramMaxD).
+cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, float2* Gff,
+                            int ldf, cudaStream_t st);
 // Steps 4-5 with an approximate fitness. lazy: flags is s.pflag and the
 // improved particles' pbest_pos rows are left to the next move (and to the
 // materialize kernel); otherwise they are copied here.

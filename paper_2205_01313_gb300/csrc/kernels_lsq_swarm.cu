@@ -8,8 +8,9 @@
 // gathers gbest_pos): bit-exact with the oracle. With the BF16/FP8 fitness the
 // pbest decisions use the approximate values, but no global best is accepted
 // on them: the (up to) 16 improved particles with the lowest approximate
-// fitness are rescored in FP64 and the best of them replaces gbest only if its
-// FP64 fitness is lower than gbest's (ties to the lower index).
+// fitness are rescored in extended precision (float-float or FP64 Gram form,
+// FP64 residuals when D > M) and the best of them replaces gbest only if its
+// rescored fitness is lower than gbest's (ties to the lower index).
 //
 // Every kernel reads the iteration counter from device memory, so a chain of
 // iterations can be captured in a CUDA graph.
@@ -27,7 +28,7 @@ namespace cupso {
 
 namespace {
 
-constexpr int kCand = 16;   // candidates rescored in FP64 per iteration
+constexpr int kCand = 16;   // candidates rescored per iteration
 
 }  // namespace
 
@@ -314,16 +315,84 @@ __device__ __forceinline__ void warp_top(Item item, int n, unsigned long long* o
 // Step 4 with an approximate fitness, and the 16 lowest keys among the
 // particles that improved (all particles when `all` is set: the first gbest).
 // One particle per thread, blocks of kSel threads (small, so that even a swarm
-// of a few thousand particles spreads over most SMs): each warp finds its 16
-// lowest, warp 0 the block's 16 of those (cand[block][16]); the last block to
-// finish merges all blocks' lists into top[16], ascending (kKeyNone where
-// fewer): a k-way merge of the sorted lists for up to kMergeLists * kSel
-// blocks, else a selection over all their keys (staged in shared memory when
-// they fit). The fitness comes from `fit`, or, with `part`, as the sum of the
-// product's nparts partial sums in their order.
+// of a few thousand particles spreads over most SMs). Each thread loads all
+// its partial sums at once (with its pbest_fit) and adds them in k order; each
+// warp sorts its 32 keys with a bitonic network of lane exchanges and writes
+// its 16 lowest as one ascending list (cand[list][16], list = 2 block + warp).
+// The last block to finish merges all lists into top[16], ascending (kKeyNone
+// where fewer): for up to 32 * kMergeLists lists, a k-way merge (the first
+// kStageDepth keys of every list staged in shared memory in one round, then
+// merged by warp 0 alone: each lane holds the heads of kMergeLists lists, a
+// warp minimum per round, no block barrier between rounds; a list's deeper
+// keys, needed only when it gives up more than kStageDepth of the 16, come
+// from global memory), else a selection over all their keys. The fitness
+// comes from `fit`, or, with `part`, as the sum of the product's nparts
+// partial sums in their order.
 constexpr int kSel = 64;
-constexpr int kMergeLists = 4;     // block lists per thread of the last block's k-way merge
-constexpr int kMergeSmem = 4096;
+constexpr int kSelWarps = kSel / 32;
+constexpr int kMergeLists = 8;     // lists per lane of the last block's k-way merge
+constexpr int kStageDepth = 4;     // keys of each list staged for the merge
+// top[16] = the 16 lowest keys of the nl ascending lists cand[list][16]
+// (kKeyNone where fewer), by one block of kSel threads.
+__device__ __forceinline__ void merge_lists(const unsigned long long* __restrict__ cand, int nl,
+                                         unsigned long long* __restrict__ top) {
+    __shared__ unsigned long long stage[32 * kMergeLists * kStageDepth];
+    __shared__ unsigned long long wtop[kSelWarps][kCand];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n = nl * kCand;
+    const int tid = (int)threadIdx.x;
+    if (nl <= 32 * kMergeLists) {
+        // k-way merge of the ascending lists: lane l of warp 0 owns lists l,
+        // l + 32, ...; each round the smallest head over the warp is taken and
+        // its list advances (keys are unique, so one owner moves)
+        constexpr int kPer = 32 * kMergeLists * kStageDepth / kSel;
+        unsigned long long v[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int e = tid + kSel * j, l = e / kStageDepth;
+            v[j] = l < nl ? __ldcg(cand + (size_t)l * kCand + e % kStageDepth) : kKeyNone;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) stage[tid + kSel * j] = v[j];
+        __syncthreads();
+        if (warp == 0) {
+            int head[kMergeLists];
+            unsigned long long hv[kMergeLists];
+#pragma unroll
+            for (int q = 0; q < kMergeLists; ++q) {
+                head[q] = 0;
+                hv[q] = stage[(lane + 32 * q) * kStageDepth];
+            }
+            for (int r = 0; r < kCand; ++r) {
+                unsigned long long lm = kKeyNone;
+#pragma unroll
+                for (int q = 0; q < kMergeLists; ++q) lm = hv[q] < lm ? hv[q] : lm;
+                const unsigned long long m = warp_min_u64(lm);
+                if (lane == 0) top[r] = m;
+                if (m != kKeyNone) {
+#pragma unroll
+                    for (int q = 0; q < kMergeLists; ++q)
+                        if (hv[q] == m) {
+                            const int b = lane + 32 * q, h = ++head[q];
+                            hv[q] = h < kStageDepth ? stage[b * kStageDepth + h]
+                                    : h < kCand   ? __ldcg(cand + (size_t)b * kCand + h)
+                                                  : kKeyNone;
+                        }
+                }
+            }
+        }
+    } else {
+        // many lists: a selection over all their keys, per warp then over the
+        // warps' lists
+        const int per = tid < n ? (n - tid + kSel - 1) / kSel : 0;   // this thread's entries: tid + kSel q
+        warp_top<0>([&](int q) { return __ldcg(cand + (size_t)tid + (size_t)kSel * q); }, per, wtop[warp]);
+        __syncthreads();
+        constexpr int kPerLane = kSelWarps * kCand / 32;
+        const unsigned long long* flat = &wtop[0][0];
+        if (warp == 0) warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, top);
+    }
+}
+
 __global__ void __launch_bounds__(kSel) lsq_select_cand_kernel(const __grid_constant__ SwarmDev s,
                                                                const float* __restrict__ fit,
                                                                const float* __restrict__ part, int nparts,
@@ -332,34 +401,32 @@ __global__ void __launch_bounds__(kSel) lsq_select_cand_kernel(const __grid_cons
                                                                unsigned int* __restrict__ flags,
                                                                unsigned long long* __restrict__ top,
                                                                unsigned int* __restrict__ ticket) {
-    extern __shared__ unsigned long long merge_buf[];   // the last block: all blocks' lists, if they fit
-    __shared__ unsigned long long wtop[kSel / 32][kCand];
     __shared__ int s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t i = (uint32_t)blockIdx.x * kSel + threadIdx.x;
     unsigned long long key = kKeyNone;
     bool nan = false;
     if (i < (uint32_t)s.Np) {
+        const bool real = i < (uint32_t)s.N;
+        const float pf = (!all && real) ? s.pf[i] : 0.0f;
         float f = 0.0f;
         if (part) {
-            // in k order; eight loads in flight at a time
-            int k = 0;
-            for (; k + 8 <= nparts; k += 8) {
-                float v[8];
+            // in k order; up to 32 loads in flight
+            for (int k0 = 0; k0 < nparts; k0 += 32) {
+                float v[32];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = __ldcg(part + (size_t)(k + e) * s.Np + i);
+                for (int e = 0; e < 32; ++e) v[e] = k0 + e < nparts ? __ldcg(part + (size_t)(k0 + e) * s.Np + i) : 0.0f;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) f = __fadd_rn(f, v[e]);
+                for (int e = 0; e < 32; ++e)
+                    if (k0 + e < nparts) f = __fadd_rn(f, v[e]);
             }
-            for (; k < nparts; ++k) f = __fadd_rn(f, __ldcg(part + (size_t)k * s.Np + i));
         } else {
             f = fit[i];
         }
-        const bool real = i < (uint32_t)s.N;
         // strict improvement; the byte flag tells the next move (or the
         // pbest copy) that pbest_pos must become pos
         unsigned char fl = 0;
-        if (!all && real && f < s.pf[i]) {
+        if (!all && real && f < pf) {
             s.pf[i] = f;
             fl = 1;
         }
@@ -367,76 +434,35 @@ __global__ void __launch_bounds__(kSel) lsq_select_cand_kernel(const __grid_cons
         if (real && (all || fl)) key = pack_key(f, i);
         nan = real && (f != f);
     }
-    if (__syncthreads_or(nan) && threadIdx.x == 0) atomicOr(s.status, kStatusNaN);
-    constexpr int kPerLane = kSel / 32 * kCand / 32;   // the block's warp lists, over warp 0's lanes
-    warp_top<1>([&](int) { return key; }, 1, wtop[warp]);
+    if (__any_sync(0xFFFFFFFFu, nan) && lane == 0) atomicOr(s.status, kStatusNaN);
+    // the warp's keys ascending over its lanes: for each size k of the bitonic
+    // sequences, exchanges at distances k/2 .. 1; the lower lane of a pair keeps
+    // the smaller key where its k-block ascends, the larger where it descends
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, key, j);
+            const bool lower = (lane & j) == 0, asc = (lane & k) == 0;
+            key = (lower == asc) ? (o < key ? o : key) : (o > key ? o : key);
+        }
+    }
+    if (lane < kCand) cand[((size_t)blockIdx.x * kSelWarps + warp) * kCand + lane] = key;
+    // the last block merges: the lists are written (barrier), thread 0 releases
+    // them with its ticket and, in the last block, acquires all the others
     __syncthreads();
-    const unsigned long long* flat = &wtop[0][0];
-    if (warp == 0)
-        warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, cand + (size_t)blockIdx.x * kCand);
-    // the last block merges
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (s_last) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
-    const int nb = (int)gridDim.x, n = nb * kCand;
-    const int tid = (int)threadIdx.x;
-    if (nb <= kMergeLists * kSel) {
-        // k-way merge of the blocks' ascending lists: thread t owns lists
-        // t, t + kSel, ...; each round the smallest head over the block is
-        // taken and its list advances (keys are unique, so one owner moves)
-        __shared__ unsigned long long wmin[kSel / 32];
-        int head[kMergeLists];
-        unsigned long long hv[kMergeLists];
-#pragma unroll
-        for (int q = 0; q < kMergeLists; ++q) {
-            const int b = tid + kSel * q;
-            head[q] = 0;
-            hv[q] = b < nb ? __ldcg(cand + (size_t)b * kCand) : kKeyNone;
-        }
-        for (int r = 0; r < kCand; ++r) {
-            unsigned long long lm = kKeyNone;
-#pragma unroll
-            for (int q = 0; q < kMergeLists; ++q) lm = hv[q] < lm ? hv[q] : lm;
-            const unsigned long long wm = warp_min_u64(lm);
-            if (lane == 0) wmin[warp] = wm;
-            __syncthreads();
-            unsigned long long m = wmin[0];
-#pragma unroll
-            for (int w = 1; w < kSel / 32; ++w) m = wmin[w] < m ? wmin[w] : m;
-            __syncthreads();
-            if (tid == 0) top[r] = m;
-            if (m != kKeyNone) {
-#pragma unroll
-                for (int q = 0; q < kMergeLists; ++q)
-                    if (hv[q] == m) {
-                        const int b = tid + kSel * q;
-                        ++head[q];
-                        hv[q] = head[q] < kCand ? __ldcg(cand + (size_t)b * kCand + head[q]) : kKeyNone;
-                    }
-            }
-        }
-    } else {
-        // many blocks: a selection over all their keys
-        const bool staged = n <= kMergeSmem;
-        if (staged) {
-            for (int e = tid; e < n; e += kSel) merge_buf[e] = __ldcg(cand + e);
-            __syncthreads();
-        }
-        const int per = tid < n ? (n - tid + kSel - 1) / kSel : 0;   // this thread's entries: tid + kSel q
-        warp_top<0>([&](int q) {
-            const size_t e = (size_t)tid + (size_t)kSel * q;
-            return staged ? merge_buf[e] : __ldcg(cand + e);
-        }, per, wtop[warp]);
-        __syncthreads();
-        if (warp == 0) warp_top<kPerLane>([&](int q) { return flat[lane + 32 * q]; }, kPerLane, top);
-    }
+    merge_lists(cand, (int)gridDim.x * kSelWarps, top);
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// Accepts the best rescored candidate if it beats gbest in FP64; rolls t.
+// Accepts the best rescored candidate if its rescored value beats gbest's; rolls t.
 // Run by the last block of the rescoring kernel (any block size that is a
 // multiple of 32): warp w sums candidates w, w + warps, ... (lane l takes
 // chunks l, l + 32, ... in order, then a fixed butterfly); thread 0 compares.
@@ -452,17 +478,43 @@ __device__ void accept_best(const SwarmDev& s, const float* __restrict__ src, co
     const uint32_t t_prev = __ldcg(s.t_dev);
     const int cur = (int)(t_prev & 1u), nxt = cur ^ 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
-    // the candidate list and gbest's FP64 value, read at once
+    // the candidate list, gbest's FP64 value and the candidates' partial sums,
+    // read at once (up to 256 pieces per candidate: 8 loads per lane for each
+    // of the warp's two candidates in flight together); a candidate's sum
+    // runs over its pieces lane + 32 k in k order, then a fixed butterfly.
+    // Absent candidates (past the first kKeyNone) are summed but never read.
     if (threadIdx.x < kCand) skey[threadIdx.x] = top[threadIdx.x];
     if (threadIdx.x == 32) s_g64 = __ldcg(g64);
-    __syncthreads();
-    for (int c = warp; c < kCand; c += nw) {
-        double f = 0.0;
-        if (skey[c] != kKeyNone)
-#pragma unroll 4
-            for (int h = lane; h < chunks; h += 32) f += __ldcg(partial + (size_t)c * chunks + h);
-        for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
-        if (lane == 0) fsum[c] = f;
+    for (int c0 = warp; c0 < kCand; c0 += 2 * nw) {
+        const int c1 = c0 + nw < kCand ? c0 + nw : -1;
+        double f0 = 0.0, f1 = 0.0;
+        if (chunks <= 256) {
+            double v0[8], v1[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int h = lane + 32 * k;
+                v0[k] = h < chunks ? __ldcg(partial + (size_t)c0 * chunks + h) : 0.0;
+                v1[k] = (c1 >= 0 && h < chunks) ? __ldcg(partial + (size_t)c1 * chunks + h) : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                f0 += v0[k];
+                f1 += v1[k];
+            }
+        } else {
+            for (int h = lane; h < chunks; h += 32) {
+                f0 += __ldcg(partial + (size_t)c0 * chunks + h);
+                if (c1 >= 0) f1 += __ldcg(partial + (size_t)c1 * chunks + h);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            f0 += __shfl_xor_sync(0xFFFFFFFFu, f0, o);
+            f1 += __shfl_xor_sync(0xFFFFFFFFu, f1, o);
+        }
+        if (lane == 0) {
+            fsum[c0] = f0;
+            if (c1 >= 0) fsum[c1] = f1;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -514,12 +566,16 @@ struct AcceptArgs {
 __device__ __forceinline__ void last_block_accepts(const SwarmDev& s, const AcceptArgs& a) {
     if (!a.ticket) return;
     __shared__ int s_last;
-    __threadfence();
+    // the block's partial sums are written (barrier); thread 0 releases them
+    // with its ticket and, in the last block, acquires the others' for all
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1;
+    if (threadIdx.x == 0) {
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        s_last = atomicAdd(a.ticket, 1u) == gridDim.x * gridDim.y - 1;
+        if (s_last) asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     accept_best(s, a.src, a.top, a.partial, a.chunks, a.g64, a.stale);
     if (threadIdx.x == 0) *a.ticket = 0u;
 }
@@ -680,11 +736,202 @@ __global__ void __launch_bounds__(256) lsq_rescore_gram_kernel(const __grid_cons
     last_block_accepts(s, acc_args);
 }
 
+// (hi, lo) += p + e: Knuth's TwoSum of hi and p (exact: hi' + t = hi + p), the
+// error t and e collected in lo. Rounded operations only, none contracted.
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float p, float e) {
+    const float s = __fadd_rn(hi, p);
+    const float z = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, z)), __fsub_rn(p, z));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+}
+
+// The Gram-form rescoring of lsq_rescore_gram_kernel with the off-diagonal
+// part in float-float arithmetic (unevaluated sums hi + lo of two binary32
+// values, Dekker 1971), which the GB300 runs on its binary32 pipes, 64 times
+// its binary64 rate. Each entry Gm_rc is held as gh + gl (gh = Gm_rc rounded
+// to binary32, gl = the rest, rounded): x_r gh = p + e exactly (e by one fma),
+// p enters the running hi by TwoSum, e and x_r gl the running lo. Per column c
+// of a tile the sum over its rows runs in float-float, is multiplied by x_c
+// the same way, and the columns of a candidate are added in float-float in a
+// fixed order before one conversion to FP64. The diagonal and linear terms
+// x_r (Gm_rr x_r - 2 c_r) stay in FP64 (D per candidate). Relative to the sum
+// of the terms' magnitudes the result is within a few units of 2^-44, beside
+// the FP64 Gram form's own cancellation error, which near a minimum dominates
+// both.
+//
+// Block = (tile (tr, tc), tr <= tc, of the upper triangle in kFfTile squares;
+// candidate quarter cq): blocks 4 k .. 4 k + 3 share tile k, so that a GPU of
+// 152 SMs holds several blocks per SM and no SM gets a whole tile more than
+// another. Thread (rq = tid / 64, c = tid % 64) takes column c of the tile,
+// rows 16 rq .. 16 rq + 15, and the block's 4 candidates at once (one Gram
+// entry and one float4 of coordinates from shared memory serve 4 terms).
+// Entries on or below the diagonal of a diagonal tile are zeroed in shared
+// memory (their terms are then exact zeros); the diagonal tile also adds the
+// FP64 diagonal and linear terms of its rows, and tile 0 adds bb.
+// partial[cand][tile].
+__global__ void __launch_bounds__(256) lsq_rescore_gram_ff_kernel(const __grid_constant__ SwarmDev s,
+                                                                  const float* __restrict__ src,
+                                                                  const float2* __restrict__ Gff, int ldf,
+                                                                  const double* __restrict__ Gm,
+                                                                  const double* __restrict__ cvec, double bb,
+                                                                  const unsigned long long* __restrict__ top,
+                                                                  int ntiles, double* __restrict__ partial,
+                                                                  const AcceptArgs acc_args) {
+    constexpr int T = kFfTile, Q = 4, RQ = 4;
+    static_assert(T == 64 && kCand == 4 * Q, "thread layout: 64 columns x 4 row quarters, 4 candidates each");
+    __shared__ __align__(16) float2 gt[T][T];   // (gh, gl) of the tile, row-major
+    __shared__ __align__(16) float4 xr[T], xc[T];   // the 4 candidates' coordinates of the tile's rows / columns
+    __shared__ uint32_t cid[Q];
+    __shared__ float rh[8][Q], rl[8][Q];        // per warp
+    __shared__ double rd[8][Q];
+    const int D = s.D;
+    const int nt = ldf / T;
+    const int tile = (int)blockIdx.x >> 2, cq = (int)blockIdx.x & 3;
+    int tr = 0, k = tile;
+    while (k >= nt - tr) {
+        k -= nt - tr;
+        ++tr;
+    }
+    const int tc = tr + k;
+    const bool diag = tr == tc;
+    const int r0 = tr * T, c0 = tc * T;
+    if (threadIdx.x < Q) {
+        const unsigned long long key = top[Q * cq + threadIdx.x];
+        cid[threadIdx.x] = key == kKeyNone ? 0xFFFFFFFFu : (uint32_t)(key & 0xFFFFFFFFull);
+    }
+    __syncthreads();
+    {
+        // the tile: 64 rows x 32 float4 (two entries each); the 4 candidates'
+        // coordinates of its rows and columns: 2 x 4 x 64 gathered values
+        float4 g[8];
+        float xv[2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = (int)threadIdx.x + 256 * j;
+            g[j] = *reinterpret_cast<const float4*>(Gff + (size_t)(r0 + (e >> 5)) * ldf + c0 + 2 * (e & 31));
+        }
+        const int q = (int)threadIdx.x >> 6, dd = (int)threadIdx.x & 63;
+        const uint32_t i = cid[q];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {   // j = 0: rows, 1: columns
+            const int d = (j ? c0 : r0) + dd;
+            xv[j] = (i != 0xFFFFFFFFu && d < D) ? __ldcg(src + (size_t)d * s.Np + i) : 0.0f;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int e = (int)threadIdx.x + 256 * j;
+            const int rr = e >> 5, cc = 2 * (e & 31);
+            float4 v = g[j];
+            if (diag && cc <= rr) v.x = v.y = 0.0f;
+            if (diag && cc + 1 <= rr) v.z = v.w = 0.0f;
+            *reinterpret_cast<float4*>(&gt[rr][cc]) = v;
+        }
+        reinterpret_cast<float*>(&xr[dd])[q] = xv[0];
+        reinterpret_cast<float*>(&xc[dd])[q] = xv[1];
+    }
+    __syncthreads();
+    const int rq = (int)threadIdx.x >> 6, c = (int)threadIdx.x & 63;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    float wh[Q] = {0.f, 0.f, 0.f, 0.f}, wl[Q] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int j = 0; j < T / RQ; ++j) {
+        const int r = rq * (T / RQ) + j;
+        const float4 x4 = xr[r];
+        const float2 gv = gt[r][c];
+        const float xq[Q] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const float p = __fmul_rn(xq[q], gv.x);
+            const float e = __fmaf_rn(xq[q], gv.x, -p);   // exact: x gh = p + e
+            ff_acc(wh[q], wl[q], p, __fmaf_rn(xq[q], gv.y, e));
+        }
+    }
+    // times x_c
+    float sh[Q], sl[Q];
+    {
+        const float4 x4 = xc[c];
+        const float xq[Q] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            sh[q] = __fmul_rn(wh[q], xq[q]);
+            sl[q] = __fmaf_rn(wl[q], xq[q], __fmaf_rn(wh[q], xq[q], -sh[q]));
+        }
+    }
+    // the warp's 32 columns, a fixed pattern: lanes l and l ^ 1 split the 4
+    // candidates (the lower lane keeps 0 and 1), lanes l and l ^ 2 split those
+    // two, then three butterfly levels; lane 4 q' + 2 b + a ends with candidate
+    // 2 a + b's sum over the warp (lanes 0, 1, 2, 3 hold candidates 0, 2, 1, 3)
+    const bool up1 = (lane & 1) != 0, up2 = (lane & 2) != 0;
+    // level 1: keep candidates 2 up1 + {0, 1}, send the other pair
+    float a0h = up1 ? sh[2] : sh[0], a0l = up1 ? sl[2] : sl[0];
+    float a1h = up1 ? sh[3] : sh[1], a1l = up1 ? sl[3] : sl[1];
+    {
+        const float g0h = up1 ? sh[0] : sh[2], g0l = up1 ? sl[0] : sl[2];
+        const float g1h = up1 ? sh[1] : sh[3], g1l = up1 ? sl[1] : sl[3];
+        const float o0h = __shfl_xor_sync(0xFFFFFFFFu, g0h, 1), o0l = __shfl_xor_sync(0xFFFFFFFFu, g0l, 1);
+        const float o1h = __shfl_xor_sync(0xFFFFFFFFu, g1h, 1), o1l = __shfl_xor_sync(0xFFFFFFFFu, g1l, 1);
+        ff_acc(a0h, a0l, o0h, o0l);
+        ff_acc(a1h, a1l, o1h, o1l);
+    }
+    // level 2: keep candidate 2 up1 + up2, send the other one
+    float h1 = up2 ? a1h : a0h, l1 = up2 ? a1l : a0l;
+    {
+        const float gh = up2 ? a0h : a1h, gl = up2 ? a0l : a1l;
+        const float oh = __shfl_xor_sync(0xFFFFFFFFu, gh, 2), ol = __shfl_xor_sync(0xFFFFFFFFu, gl, 2);
+        ff_acc(h1, l1, oh, ol);
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        const float oh = __shfl_xor_sync(0xFFFFFFFFu, h1, o), ol = __shfl_xor_sync(0xFFFFFFFFu, l1, o);
+        ff_acc(h1, l1, oh, ol);
+    }
+    // x_r (Gm_rr x_r - 2 c_r) of row r0 + c for the 4 candidates, in the
+    // diagonal tile's warps 0 and 1, summed over each warp
+    double dq[Q] = {0.0, 0.0, 0.0, 0.0};
+    if (diag && rq == 0) {
+        const int d = r0 + c;
+        const float4 x4 = xr[c];
+        const float xq[Q] = {x4.x, x4.y, x4.z, x4.w};
+        if (d < D) {
+            const double gdd = __ldg(Gm + (size_t)d * D + d), c2 = -2.0 * __ldg(cvec + d);
+#pragma unroll
+            for (int q = 0; q < Q; ++q) dq[q] = (double)xq[q] * fma(gdd, (double)xq[q], c2);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dq[q] += __shfl_xor_sync(0xFFFFFFFFu, dq[q], o);
+    }
+    if (lane < 4) {
+        const int q = 2 * (lane & 1) + (lane >> 1);   // the candidate lane `lane` holds
+        rh[warp][q] = h1;
+        rl[warp][q] = l1;
+        rd[warp][q] = q == 0 ? dq[0] : q == 1 ? dq[1] : q == 2 ? dq[2] : dq[3];
+    }
+    __syncthreads();
+    if (threadIdx.x < Q) {
+        const int q = (int)threadIdx.x;
+        float h = rh[0][q], l = rl[0][q];
+        double dsum = rd[0][q];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) {
+            ff_acc(h, l, rh[w][q], rl[w][q]);
+            dsum += rd[w][q];
+        }
+        double tot = fma(2.0, (double)h + (double)l, dsum);
+        if (tile == 0) tot += bb;
+        partial[(size_t)(Q * cq + q) * ntiles + tile] =
+            cid[q] != 0xFFFFFFFFu ? tot : __longlong_as_double(0x7FF8000000000000ll);
+    }
+    last_block_accepts(s, acc_args);
+}
+
 // Gm = A^T A (D x D), cvec = A^T b, in FP64 (one-time setup). 32 x 32 output
 // tile per block, rows of A in order.
 __global__ void __launch_bounds__(256) lsq_gram_kernel(const float* __restrict__ A, const float* __restrict__ b,
                                                        int M, int D, double* __restrict__ Gm,
-                                                       double* __restrict__ cvec) {
+                                                       double* __restrict__ cvec, float2* __restrict__ Gff, int ldf) {
     __shared__ double ta[32][33], tb[32][33];
     const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -707,7 +954,12 @@ __global__ void __launch_bounds__(256) lsq_gram_kernel(const float* __restrict__
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int r = r0 + ty * 4 + k, c = c0 + tx;
-        if (r < D && c < D) Gm[(size_t)r * D + c] = acc[k];
+        if (r < D && c < D) {
+            Gm[(size_t)r * D + c] = acc[k];
+            // the same entry as hi + lo in binary32 for the float-float rescoring
+            const float hi = __double2float_rn(acc[k]);
+            Gff[(size_t)r * ldf + c] = make_float2(hi, __double2float_rn(acc[k] - (double)hi));
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x < 32) {
         const int r = r0 + threadIdx.x;
@@ -860,13 +1112,15 @@ cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigne
     return cudaGetLastError();
 }
 
-int lsq_cand_blocks(int Np) { return (Np + kSel - 1) / kSel; }
+int lsq_cand_lists(int Np) { return (Np + kSel - 1) / kSel * kSelWarps; }
 
-cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec,
-                            cudaStream_t st) {
-    if (D > kGramMaxD) return cudaErrorInvalidValue;
-    lsq_gram_kernel<<<dim3((D + 31) / 32, (D + 31) / 32), 256, 0, st>>>(A, b, M, D, Gm, cvec);
-    const cudaError_t e = cudaGetLastError();
+cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double* Gm, double* cvec, float2* Gff,
+                            int ldf, cudaStream_t st) {
+    if (D > kGramMaxD || ldf < D || ldf % kFfTile != 0) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(Gff, 0, sizeof(float2) * (size_t)ldf * ldf, st);
+    if (e != cudaSuccess) return e;
+    lsq_gram_kernel<<<dim3((D + 31) / 32, (D + 31) / 32), 256, 0, st>>>(A, b, M, D, Gm, cvec, Gff, ldf);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the rescoring keeps 4 candidates x D doubles in shared memory: past the
     // default 48 KB from D = 1537 on
@@ -874,8 +1128,9 @@ cudaError_t lsq_launch_gram(const float* A, const float* b, int M, int D, double
                                 (int)(sizeof(double) * 4 * (size_t)D));
 }
 
-// cand: [blocks * 16] + [16] scratch; partial: [16 * chunks]; flags: [Np / 4].
-// With Gm set (D <= M) the rescoring uses the FP64 Gram form.
+// cand: [lists * 16] + [16] + ticket; partial: [16 * chunks]; flags: [Np / 4].
+// With Gm set (D <= M) the rescoring uses the Gram form (float-float when
+// gram.ff, else FP64); without it the FP64 residuals row by row.
 cudaError_t lsq_launch_offsets(const SwarmDev& s, const float* A, const float* b, int M, float* off, int* stale,
                                int num_sms, cudaStream_t st) {
     const int grid = std::max(1, std::min(num_sms * 4, (M + 7) / 8));
@@ -894,13 +1149,10 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const f
                                     bool lazy, const float* A, const float* b, int M, unsigned long long* cand,
                                     double* partial, int chunks, double* g64, unsigned int* flags, int grid,
                                     const LsqGram& gram, float* off, int* stale, int num_sms, cudaStream_t st) {
-    const int nblk = lsq_cand_blocks(s.Np);
-    unsigned long long* top = cand + (size_t)nblk * kCand;
+    const int nblk = (s.Np + kSel - 1) / kSel;
+    unsigned long long* top = cand + (size_t)lsq_cand_lists(s.Np) * kCand;
     unsigned int* ticket = reinterpret_cast<unsigned int*>(top + kCand);
-    const int nkeys = nblk * kCand;
-    const size_t merge_smem =
-        (nblk > kMergeLists * kSel && nkeys <= kMergeSmem) ? sizeof(unsigned long long) * (size_t)nkeys : 0;
-    lsq_select_cand_kernel<<<nblk, kSel, merge_smem, st>>>(s, fit, part, nparts, all, cand, flags, top, ticket);
+    lsq_select_cand_kernel<<<nblk, kSel, 0, st>>>(s, fit, part, nparts, all, cand, flags, top, ticket);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (!all && !lazy) {
@@ -913,7 +1165,12 @@ cudaError_t lsq_launch_gbest_approx(const SwarmDev& s, const float* fit, const f
     const float* src = (lazy && !all) ? s.x : s.pb;
     // the last rescoring block accepts the best candidate (ticket: stale[2])
     const AcceptArgs acc{reinterpret_cast<unsigned int*>(stale + 2), src, top, partial, chunks, g64, stale};
-    if (gram.Gm) {
+    if (gram.Gm && gram.ff) {
+        const int nt = lsq_ff_tiles(s.D);
+        const AcceptArgs acc_ff{acc.ticket, src, top, partial, nt, g64, stale};
+        lsq_rescore_gram_ff_kernel<<<4 * nt, 256, 0, st>>>(s, src, gram.Gff, gram.ldf, gram.Gm, gram.cvec, gram.bb,
+                                                           top, nt, partial, acc_ff);
+    } else if (gram.Gm) {
         const int pairs = ((s.D + 1) / 2 + chunks - 1) / chunks;
         lsq_rescore_gram_kernel<<<dim3(kCand / 4, chunks), 256, sizeof(double) * 4 * (size_t)s.D, st>>>(
             s, src, gram.Gm, gram.cvec, gram.bb, top, pairs, chunks, partial, acc);

@@ -38,6 +38,7 @@ CUPSO_OPT_SYNC_KERNEL = 6
 CUPSO_OPT_TIME_FITNESS = 7
 CUPSO_OPT_PARTICLES_PER_THREAD = 8
 CUPSO_OPT_ITERS_PER_LAUNCH = 9
+CUPSO_OPT_LSQ_RESCORE = 10
 SYNC_KERNELS = {"auto": 0, "register": 1, "pipelined3": 2, "pipelined4": 3, "tiled": 4, "panel8": 5, "panel16": 6}
 CUPSO_OPT_FAULT_HOLD_LOCK = 100
 CUPSO_OPT_FAULT_STALL_BARRIER = 101

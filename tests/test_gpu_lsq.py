@@ -103,11 +103,15 @@ W, C12 = 0.729, 1.49445
 SX = np.float32(448.0) / np.float32(4.0)        # FP8 scale of a displacement within [-2, 2]
 
 
-def _lsq_swarm(P, A, b, N, seed, precision):
+RESCORE = {"ff": 0, "fp64": 1}      # CUPSO_OPT_LSQ_RESCORE: float-float or FP64 Gram form
+
+
+def _lsq_swarm(P, A, b, N, seed, precision, rescore="ff"):
     import torch
     dA = torch.from_numpy(A).cuda()
     db = torch.from_numpy(b).cuda()
     s = P.Swarm(A.shape[1], N, LSQ_BOUNDS, W, C12, C12, P.CUPSO_LSQ, seed)
+    s.set_option(P.CUPSO_OPT_LSQ_RESCORE, RESCORE[rescore])
     s.set_lsq(dA.data_ptr(), db.data_ptr(), A.shape[0], precision)
     s._keep = (dA, db)        # the library borrows A and b
     return s
@@ -142,15 +146,17 @@ def test_lsq_exact_swarm_bit_exact(P, precision, N, D, M):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
-@pytest.mark.parametrize("N,D,M", [(2000, 96, 640), (1000, 200, 120), (300, 1600, 1664)])
-def test_lsq_approx_swarm_gbest_is_fp64_verified(P, precision, N, D, M):
-    """pbest follows the approximate fitness; gbest only moves to FP64-verified
-    improvements: its FP64 fitness never increases and equals the oracle's
-    ||A g - b||^2. D <= M rescores in the Gram form (A^T A), D > M row by row;
-    D = 1600 holds 50 KB of candidates in shared memory, past the default
-    48 KB limit."""
+@pytest.mark.parametrize("N,D,M,rescore", [(2000, 96, 640, "ff"), (2000, 96, 640, "fp64"), (1000, 200, 120, "ff"),
+                                           (300, 1600, 1664, "ff"), (300, 1600, 1664, "fp64")])
+def test_lsq_approx_swarm_gbest_is_fp64_verified(P, precision, N, D, M, rescore):
+    """pbest follows the approximate fitness; gbest only moves to verified
+    improvements: its rescored fitness never increases and equals the oracle's
+    FP64 ||A g - b||^2. D <= M rescores in the Gram form (A^T A; float-float or
+    FP64 arithmetic), D > M row by row in FP64; D = 1600 holds 50 KB of
+    candidates in shared memory in the FP64 Gram kernel, past the default 48 KB
+    limit, and leaves a ragged last tile of 64 in the float-float one."""
     A, b, _ = _problem(M, D, 1, seed=11)
-    with _lsq_swarm(P, A, b, N, 5, precision) as s:
+    with _lsq_swarm(P, A, b, N, 5, precision, rescore) as s:
         prev64 = s.gbest_f64()
         prev = s.state()
         for _ in range(6):
@@ -238,8 +244,8 @@ def test_lsq_swarm_lazy_pbest_consistent(P, precision):
     _check_improvers_displacement(A, b, before, g, eager, precision)
 
 
-@pytest.mark.parametrize("precision", ["bf16", "fp8"])
-def test_lsq_acceptance_per_iteration(P, precision):
+@pytest.mark.parametrize("precision,rescore", [("bf16", "ff"), ("fp8", "ff"), ("bf16", "fp64")])
+def test_lsq_acceptance_per_iteration(P, precision, rescore):
     """Each iteration, against the oracle's FP64 fitness of every improver: the
     16 improvers with the lowest approximate keys are the rescored candidates;
     gbest's new FP64 value is the lowest of theirs when that beats the old one
@@ -250,7 +256,7 @@ def test_lsq_acceptance_per_iteration(P, precision):
     A, b, _ = _problem(M, D, 1, seed=17)
     misses = checked = 0
     worst = 0.0
-    with _lsq_swarm(P, A, b, N, 11, precision) as s:
+    with _lsq_swarm(P, A, b, N, 11, precision, rescore) as s:
         prev = s.state()
         g64_prev = s.gbest_f64()
         for _ in range(30):
@@ -282,6 +288,37 @@ def test_lsq_acceptance_per_iteration(P, precision):
     assert checked >= 20
     print("\n%s: %d iterations checked, true FP64 best outside the 16 candidates in %d, worst gap %.2e"
           % (precision, checked, misses, worst))
+
+
+@pytest.mark.parametrize("N,D,M,iters", [(2000, 96, 640, 40), (1500, 200, 300, 30), (1024, 1024, 4096, 12)])
+def test_lsq_rescore_ff_matches_fp64(P, N, D, M, iters):
+    """The float-float rescoring against the FP64 one on the same swarm: every
+    iteration both accept the same particle (so the trajectories stay equal
+    bit for bit), their values agree to 1e-12 relative, and both equal the
+    oracle's FP64 residual sum of gbest_pos to 1e-11 relative. D = 200 leaves a
+    ragged last tile (zero-padded Gram pairs); D = 1024 is 136 tiles."""
+    from tests.gpu_common import same_bits
+    A, b, _ = _problem(M, D, 1, seed=D + 3)
+    with _lsq_swarm(P, A, b, N, 13, "bf16", "ff") as s1, _lsq_swarm(P, A, b, N, 13, "bf16", "fp64") as s2:
+        moved = 0
+        g_prev = s1.gbest_f64()
+        assert abs(g_prev - s2.gbest_f64()) <= 1e-12 * g_prev
+        for _ in range(iters):
+            s1.step(1)
+            s2.step(1)
+            _, fit1, idx1, pos1 = s1.gbest()
+            _, fit2, idx2, pos2 = s2.gbest()
+            g1, g2 = s1.gbest_f64(), s2.gbest_f64()
+            assert idx1 == idx2 and same_bits(pos1, pos2)
+            assert abs(g1 - g2) <= 1e-12 * g2, (g1, g2)
+            exact = O.lsq_f64(A, b, pos1)
+            assert abs(g1 - exact) <= 1e-11 * exact and abs(g2 - exact) <= 1e-11 * exact
+            moved += int(g1 < g_prev)
+            g_prev = g1
+        st1, st2 = s1.state(), s2.state()
+    for k in ("pos", "v", "pbest_pos", "pbest_fit"):
+        assert same_bits(st1[k], st2[k]), k
+    assert moved >= 3
 
 
 def _converging_problem(M, D, seed):

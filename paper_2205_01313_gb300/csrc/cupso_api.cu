@@ -322,7 +322,8 @@ cudaError_t launch_lsq_iteration(cupso_swarm* h, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaStreamWaitEvent(L.side, L.fork, 0);
     if (e == cudaSuccess) e = lsq_launch_offsets(h->dev, L.A, L.b, L.M, L.tc.roff, L.tc.roff_stale, h->num_sms, L.side);
     if (e == cudaSuccess) e = cudaEventRecord(L.join, L.side);
-    if (e == cudaSuccess) e = lsq_launch_move_q(h->dev, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms, st);
+    if (e == cudaSuccess)
+        e = lsq_launch_move_q(h->dev, L.tc.tmMove, L.tc.Xq, L.tc.Kp, L.tc.fp8, L.tc.sx, h->num_sms, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, L.join, 0);
     if (e != cudaSuccess) return e;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1194,6 +1195,8 @@ int cupso_set_lsq(cupso_handle h, const float* A_dev, const float* b_dev, int M,
         const float sx = std::isfinite(span) && span > 0.0f ? 448.0f / span : 1.0f;
         rc = lsq_setup_tc(&L->tc, A_dev, b_dev, M, h->D, h->Np, precision == CUPSO_LSQ_FP8, sx, h->stream);
         if (rc) return rc;
+        if (!lsq_make_move_maps(L->tc.tmMove, h->dev.x, h->dev.v, h->dev.pb, h->Np, h->D))
+            return fail(CUPSO_ERR_UNSUPPORTED, "tensor maps of the move could not be encoded%s");
         if (h->D <= M && h->D <= kGramMaxD) {
             // Gram data: A^T A, A^T b (device, FP64), A^T A again as binary32
             // pairs for the float-float rescoring, and b^T b (host, from b)

@@ -77,6 +77,9 @@ cudaError_t lsq_prepare();
 cudaError_t lsq_convert(const float* src, size_t si, size_t sk, int N, int D, int Np, int Kp, bool fp8, float scale,
                         void* dst, cudaStream_t st);
 bool lsq_tc_plan(LsqTcPlan* p, void* Xq, void* Aq, bool fp8, int Np, int Mp, int Kp);
+// The three tensor maps of the TMA-fed move over arrays [D][Np] of FP32 (Np a
+// multiple of 64): boxes of 64 particles x 64 dimensions, zeros past D.
+bool lsq_make_move_maps(unsigned char (*maps)[128], const float* x, const float* v, const float* pb, int Np, int D);
 // part[k][i] (k < lsq_tc_partials) = sum of squared residuals y + off[m] of
 // particle i over residual rows 128 k .. 128 k + 127 (off = -b: the positions'
 // residuals; off = A c - b: residuals of displacements from c).
@@ -98,6 +101,9 @@ struct LsqTcState {
     float* part = nullptr;           // [Mp / 128][Np] partial sums
     unsigned int* status = nullptr;
     LsqTcPlan plan;
+    // CUtensorMaps of the swarm's pos, v and pbest_pos ([D][Np] FP32, boxes of
+    // 64 particles x 64 dimensions) for the TMA-fed move (lsq_make_move_maps)
+    alignas(64) unsigned char tmMove[3][128];
 };
 int lsq_setup_tc(LsqTcState* st, const float* A, const float* b, int M, int D, int Np, bool fp8, float sx,
                  cudaStream_t stream);
@@ -122,8 +128,11 @@ cudaError_t lsq_fp64_launch(const float* x, int ldx, int N, int D, const float* 
 cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st);
 // The same moves, writing the new positions also as the tensor-core operand
 // Xq ([Np][Kp], BF16, or FP8 e4m3 of x * sx), zero for i >= N and k >= D.
-// Requires Np and Kp multiples of 64 and Kp >= D.
-cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int num_sms, cudaStream_t st);
+// Tiles of pos, v, pbest_pos arrive by TMA through the maps of
+// lsq_make_move_maps (maps: 3 x 128 bytes). Requires Np and Kp multiples of
+// 64 and Kp >= D.
+cudaError_t lsq_launch_move_q(const SwarmDev& s, const unsigned char (*maps)[128], void* Xq, int Kp, bool fp8,
+                              float sx, int num_sms, cudaStream_t st);
 cudaError_t lsq_launch_select_exact(const SwarmDev& s, const float* fit, unsigned int* flags, int grid,
                                     cudaStream_t st);
 // Candidate lists of the selection (one of 16 keys per warp of 32 particles):

@@ -35,6 +35,7 @@
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "tma_common.cuh"
 
 namespace cupso {
 
@@ -50,36 +51,6 @@ constexpr int kEpiWarps = 8;
 constexpr int X_BYTES = BM * KB; // 16 KB
 constexpr int A_BYTES = BNH * KB; // 16 KB
 constexpr int STAGE_BYTES = X_BYTES + A_BYTES;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the completion of phase `parity`; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = global_ns();
-    for (;;) {
-        for (int k = 0; k < 32; ++k)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
 
 // Address of the same shared-memory offset in CTA `rank` of the cluster.
 __device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
@@ -601,6 +572,24 @@ size_t tc_smem() { return (size_t)STAGES * STAGE_BYTES + 1024 + 256; }
 }  // namespace
 
 bool lsq_tc_available() { return encode_fn() != nullptr; }
+
+bool lsq_make_move_maps(unsigned char (*maps)[128], const float* x, const float* v, const float* pb, int Np, int D) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn || Np % 64 != 0 || D < 1) return false;
+    const float* arrays[3] = {x, v, pb};
+    for (int a = 0; a < 3; ++a) {
+        cuuint64_t dims[2] = {(cuuint64_t)Np, (cuuint64_t)D};
+        cuuint64_t strides[1] = {(cuuint64_t)Np * sizeof(float)};
+        cuuint32_t box[2] = {64, 64};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = fn(reinterpret_cast<CUtensorMap*>(maps[a]), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<float*>(arrays[a]), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return false;
+    }
+    return true;
+}
 
 cudaError_t lsq_prepare() {
     cudaError_t e = cudaFuncSetAttribute(lsq_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem());

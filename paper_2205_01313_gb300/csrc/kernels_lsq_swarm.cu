@@ -21,8 +21,10 @@
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
 #include "stream_common.cuh"
+#include "tma_common.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace cupso {
 
@@ -79,121 +81,157 @@ __global__ void __launch_bounds__(kBlock) lsq_move_kernel(const __grid_constant_
 // lsq_offset_kernel) lands in Xq[i][k] (row-major, row length Kp): x'_k - g_k,
 // computed in FP32, rounded to BF16, or multiplied by sx and rounded to FP8
 // e4m3 with saturation (|x' - g| <= max_pos - min_pos, so sx = 448 / (max_pos -
-// min_pos) never saturates); zero for i >= N and k >= D. A CTA takes tiles of
-// 64 particles x 64 dimensions; the transposition goes through shared memory,
-// so the swarm rows and the operand rows are both written in whole segments.
+// min_pos) never saturates); zero for i >= N and k >= D.
+// One CTA per SM walks tiles of 64 particles x 64 dimensions (tile b, b +
+// gridDim.x, ...). Thread 0 keeps a ring of kMoveStages tiles in flight: per
+// tile, three 2-D tensor copies (pos, v, pbest_pos; rows past D read as zeros)
+// and one bulk copy of the tile's 64 improvement flags, all completing on the
+// stage's mbarrier; a stage is refilled as soon as every thread is done with
+// it. Thread q takes 4 particles x one dimension pair of the tile; new pos and
+// v go straight back to global memory; the operand's transposition goes
+// through shared memory, so its rows are written in whole segments.
 // Lazy pbest: a particle flagged in s.pflag improved in the previous
 // iteration, so its pbest_pos is the position loaded here; that row is written
-// back on the way.
+// back on the way. Every wait is bounded: on a timeout the CTA sets
+// kStatusTimeout, waits (bounded) for the copies it has in flight and stops.
+struct MoveMaps {
+    CUtensorMap m[3];   // pos, v, pbest_pos
+};
+constexpr int kMoveThreads = 512;
+constexpr int kMoveStages = 3;
+constexpr int kMoveBox = 64 * 64 * 4;   // one array's tile
+constexpr int kMoveStageBytes = (3 * kMoveBox + 64 + 127) / 128 * 128;
+constexpr uint32_t kMoveTx = 3 * kMoveBox + 64;
+
 template <bool FP8>
-__global__ void __launch_bounds__(kBlock) lsq_move_q_kernel(const __grid_constant__ SwarmDev s, void* __restrict__ Xq,
-                                                            int Kp, float sx) {
-    __shared__ uint32_t S[32][65];   // [dimension pair][particle]: the pair's two operand values
+__global__ void __launch_bounds__(kMoveThreads, 1) lsq_move_q_kernel(const __grid_constant__ SwarmDev s,
+                                                                     const __grid_constant__ MoveMaps maps,
+                                                                     void* __restrict__ Xq, int Kp, float sx) {
+    extern __shared__ unsigned char msm_raw[];   // kMoveStages stages, 128-byte aligned below
+    __shared__ uint32_t S[32][65];               // [dimension pair][particle]: the pair's two operand values
+    __shared__ __align__(8) uint64_t full[kMoveStages];
+    const uint32_t raw = smem_u32(msm_raw);
+    const uint32_t sbase = (raw + 127u) & ~127u;
+    unsigned char* msm = msm_raw + (sbase - raw);
     const uint32_t t_prev = __ldcg(s.t_dev);
     const uint32_t t = t_prev + 1u;
     const float* G = s.G + (size_t)(t_prev & 1u) * s.D;
     const size_t Np = (size_t)s.Np;
     const int ptiles = s.Np / 64, ntiles = ptiles * (Kp / 64);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int mine = (int)blockIdx.x < ntiles ? (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+    // tile k of this CTA into stage k % kMoveStages (thread 0)
+    auto issue = [&](int k) {
+        const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+        const int p0 = (tile % ptiles) * 64, d0 = (tile / ptiles) * 64;
+        const int st = k % kMoveStages;
+        const uint32_t bar = smem_u32(&full[st]), dst = sbase + (uint32_t)(st * kMoveStageBytes);
+        mbar_expect_tx(bar, kMoveTx);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) tma_load_2d_cta(dst + (uint32_t)(a * kMoveBox), &maps.m[a], p0, d0, bar);
+        bulk_load_cta(dst + 3u * kMoveBox, s.pflag + p0, 64u, bar);
+    };
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kMoveStages; ++st) mbar_init(smem_u32(&full[st]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+        for (int k = 0; k < mine && k < kMoveStages; ++k) issue(k);
+    }
+    __syncthreads();
+    const int q = (int)threadIdx.x, grp = q & 15, gl = q >> 4;
+    for (int k = 0; k < mine; ++k) {
+        const int st = k % kMoveStages;
+        const bool ok = mbar_wait(smem_u32(&full[st]), (uint32_t)((k / kMoveStages) & 1), s.wait_limit_ns);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(s.status, kStatusTimeout);
+                // the copies still in flight land before the CTA leaves
+                for (int kk = k; kk < mine && kk < k + kMoveStages; ++kk)
+                    mbar_wait(smem_u32(&full[kk % kMoveStages]), (uint32_t)((kk / kMoveStages) & 1), s.wait_limit_ns);
+            }
+            break;
+        }
+        const int tile = (int)blockIdx.x + k * (int)gridDim.x;
         const uint32_t p0 = (uint32_t)(tile % ptiles) * 64u;
         const int dt = tile / ptiles;
-        // 512 (4-particle group, dimension pair) items, kItems per thread; every
-        // row of all of them is loaded before any is used, so that a thread
-        // keeps 6 kItems loads in flight
-        constexpr int kItems = 16 * 32 / kBlock;
-        float4 X[kItems][2], V[kItems][2], P[kItems][2];
-        uint32_t fl[kItems];
+        const float* tx = reinterpret_cast<const float*>(msm + st * kMoveStageBytes);   // [64 dims][64 particles]
+        const float* tv = tx + 64 * 64;
+        const float* tp = tv + 64 * 64;
+        const uint32_t* tfl = reinterpret_cast<const uint32_t*>(tp + 64 * 64);          // 16 groups of 4 flag bytes
+        const int g = dt * 32 + gl;
+        const uint32_t i0 = p0 + 4u * (uint32_t)grp;
+        float xn[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+        if (2 * g < s.D) {
+            const uint32_t fl = tfl[grp];
+            uint4 r[4];
 #pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const int q = (int)threadIdx.x + it * kBlock;
-            const int g = dt * 32 + (q >> 4);
-            const uint32_t i0 = p0 + 4u * (uint32_t)(q & 15);
-            fl[it] = 0u;
-            if (2 * g < s.D) fl[it] = __ldcg(reinterpret_cast<const unsigned int*>(s.pflag) + (i0 >> 2));
+            for (int j = 0; j < 4; ++j)
+                r[j] = philox4x32_10_rk(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.rk0, s.rk1);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int d = 2 * g + h;
-                X[it][h] = V[it][h] = P[it][h] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (d < s.D) {
-                    const size_t off = (size_t)d * Np + i0;
-                    X[it][h] = ld4(s.x + off);
-                    V[it][h] = ld4(s.v + off);
-                    P[it][h] = ld4(s.pb + off);
+                if (d >= s.D) break;
+                const int row = (2 * gl + h) * 64 + 4 * grp;
+                const size_t off = (size_t)d * Np + i0;
+                float4 Xh = *reinterpret_cast<const float4*>(tx + row);
+                float4 Vh = *reinterpret_cast<const float4*>(tv + row);
+                float4 Ph = *reinterpret_cast<const float4*>(tp + row);
+                if (fl) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if ((fl >> (8 * j)) & 1u) set_lane(Ph, j, lane(Xh, j));
+                    st4(s.pb + off, Ph);
                 }
+                const float gd = __ldg(G + d);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float xj = lane(Xh, j), vj = lane(Vh, j);
+                    move_one(xj, vj, lane(Ph, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
+                    set_lane(Xh, j, xj);
+                    set_lane(Vh, j, vj);
+                    xn[h][j] = __fsub_rn(xj, gd);
+                }
+                st4(s.x + off, Xh);
+                st4(s.v + off, Vh);
             }
         }
 #pragma unroll
-        for (int it = 0; it < kItems; ++it) {
-            const int q = (int)threadIdx.x + it * kBlock;
-            const int grp = q & 15, gl = q >> 4;
-            const int g = dt * 32 + gl;
-            const uint32_t i0 = p0 + 4u * (uint32_t)grp;
-            float xn[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-            if (2 * g < s.D) {
-                uint4 r[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    r[j] = philox4x32_10_rk(make_uint4((uint32_t)g, i0 + j, t, s.swarm), s.rk0, s.rk1);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int d = 2 * g + h;
-                    if (d >= s.D) break;
-                    const size_t off = (size_t)d * Np + i0;
-                    float4 Xh = X[it][h], Vh = V[it][h], Ph = P[it][h];
-                    if (fl[it]) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if ((fl[it] >> (8 * j)) & 1u) set_lane(Ph, j, lane(Xh, j));
-                        st4(s.pb + off, Ph);
-                    }
-                    const float gd = __ldg(G + d);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        float xj = lane(Xh, j), vj = lane(Vh, j);
-                        move_one(xj, vj, lane(Ph, j), gd, u01(word(r[j], 2 * h)), u01(word(r[j], 2 * h + 1)), s);
-                        set_lane(Xh, j, xj);
-                        set_lane(Vh, j, vj);
-                        xn[h][j] = __fsub_rn(xj, gd);
-                    }
-                    st4(s.x + off, Xh);
-                    st4(s.v + off, Vh);
-                }
+        for (int j = 0; j < 4; ++j) {
+            const bool real = i0 + j < (uint32_t)s.N;
+            const float a = real ? xn[0][j] : 0.0f, b = real ? xn[1][j] : 0.0f;
+            uint32_t wq;
+            if constexpr (FP8) {
+                const __nv_fp8x2_e4m3 q2(make_float2(__fmul_rn(a, sx), __fmul_rn(b, sx)));
+                wq = (uint32_t)q2.__x;
+            } else {
+                const __nv_bfloat162 q2 = __floats2bfloat162_rn(a, b);
+                wq = *reinterpret_cast<const uint32_t*>(&q2);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bool real = i0 + j < (uint32_t)s.N;
-                const float a = real ? xn[0][j] : 0.0f, b = real ? xn[1][j] : 0.0f;
-                uint32_t wq;
-                if constexpr (FP8) {
-                    const __nv_fp8x2_e4m3 q2(make_float2(__fmul_rn(a, sx), __fmul_rn(b, sx)));
-                    wq = (uint32_t)q2.__x;
-                } else {
-                    const __nv_bfloat162 q2 = __floats2bfloat162_rn(a, b);
-                    wq = *reinterpret_cast<const uint32_t*>(&q2);
-                }
-                S[gl][4 * grp + j] = wq;
-            }
+            S[gl][4 * grp + j] = wq;
         }
-        __syncthreads();
+        __syncthreads();   // stage st read by every thread, S complete
+        if (threadIdx.x == 0 && k + kMoveStages < mine) {
+            fence_proxy_async_smem();
+            issue(k + kMoveStages);
+        }
         char* row0 = static_cast<char*>(Xq) + (size_t)p0 * Kp * (FP8 ? 1 : 2);
         if constexpr (FP8) {
             // 64 rows x 4 pieces of 16 dimensions (16 B)
-            const int c = threadIdx.x & 3, pl = threadIdx.x >> 2;
-            uint4 u;
-            u.x = (S[8 * c + 0][pl] & 0xFFFFu) | (S[8 * c + 1][pl] << 16);
-            u.y = (S[8 * c + 2][pl] & 0xFFFFu) | (S[8 * c + 3][pl] << 16);
-            u.z = (S[8 * c + 4][pl] & 0xFFFFu) | (S[8 * c + 5][pl] << 16);
-            u.w = (S[8 * c + 6][pl] & 0xFFFFu) | (S[8 * c + 7][pl] << 16);
-            *reinterpret_cast<uint4*>(row0 + (size_t)pl * Kp + dt * 64 + 16 * c) = u;
-        } else {
-            // 64 rows x 8 pieces of 8 dimensions (16 B)
-            for (int q = threadIdx.x; q < 64 * 8; q += kBlock) {
-                const int c = q & 7, pl = q >> 3;
-                const uint4 u = make_uint4(S[4 * c][pl], S[4 * c + 1][pl], S[4 * c + 2][pl], S[4 * c + 3][pl]);
-                *reinterpret_cast<uint4*>(row0 + ((size_t)pl * Kp + dt * 64 + 8 * c) * 2) = u;
+            if (threadIdx.x < 256) {
+                const int c = threadIdx.x & 3, pl = threadIdx.x >> 2;
+                uint4 u;
+                u.x = (S[8 * c + 0][pl] & 0xFFFFu) | (S[8 * c + 1][pl] << 16);
+                u.y = (S[8 * c + 2][pl] & 0xFFFFu) | (S[8 * c + 3][pl] << 16);
+                u.z = (S[8 * c + 4][pl] & 0xFFFFu) | (S[8 * c + 5][pl] << 16);
+                u.w = (S[8 * c + 6][pl] & 0xFFFFu) | (S[8 * c + 7][pl] << 16);
+                *reinterpret_cast<uint4*>(row0 + (size_t)pl * Kp + dt * 64 + 16 * c) = u;
             }
+        } else {
+            // 64 rows x 8 pieces of 8 dimensions (16 B): one per thread
+            const int c = threadIdx.x & 7, pl = threadIdx.x >> 3;
+            const uint4 u = make_uint4(S[4 * c][pl], S[4 * c + 1][pl], S[4 * c + 2][pl], S[4 * c + 3][pl]);
+            *reinterpret_cast<uint4*>(row0 + ((size_t)pl * Kp + dt * 64 + 8 * c) * 2) = u;
         }
-        __syncthreads();
+        __syncthreads();   // S free for the next tile
     }
 }
 
@@ -1086,16 +1124,23 @@ cudaError_t lsq_launch_move(const SwarmDev& s, int grid, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t lsq_launch_move_q(const SwarmDev& s, void* Xq, int Kp, bool fp8, float sx, int num_sms, cudaStream_t st) {
-    if (s.Np % 64 != 0 || Kp % 64 != 0 || Kp < s.D || num_sms < 1) return cudaErrorInvalidValue;
+cudaError_t lsq_launch_move_q(const SwarmDev& s, const unsigned char (*maps)[128], void* Xq, int Kp, bool fp8,
+                              float sx, int num_sms, cudaStream_t st) {
+    if (s.Np % 64 != 0 || Kp % 64 != 0 || Kp < s.D || num_sms < 1 || !maps ||
+        (reinterpret_cast<uintptr_t>(s.pflag) & 15) != 0)
+        return cudaErrorInvalidValue;
     const int ntiles = (s.Np / 64) * (Kp / 64);
-    // one wave of resident CTAs walks the tiles
-    int per_sm = 0;
-    const void* k = fp8 ? (const void*)lsq_move_q_kernel<true> : (const void*)lsq_move_q_kernel<false>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kBlock, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    const int grid = std::min(num_sms * per_sm, ntiles);
-    if (fp8) lsq_move_q_kernel<true><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
-    else lsq_move_q_kernel<false><<<grid, kBlock, 0, st>>>(s, Xq, Kp, sx);
+    const size_t smem = (size_t)kMoveStages * kMoveStageBytes + 128;
+    MoveMaps mm;
+    static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+    for (int a = 0; a < 3; ++a) std::memcpy(&mm.m[a], maps[a], sizeof(CUtensorMap));
+    // one CTA per SM walks the tiles
+    const int grid = std::min(num_sms, ntiles);
+    cudaError_t e = cudaFuncSetAttribute(fp8 ? (const void*)lsq_move_q_kernel<true> : (const void*)lsq_move_q_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (fp8) lsq_move_q_kernel<true><<<grid, kMoveThreads, smem, st>>>(s, mm, Xq, Kp, sx);
+    else lsq_move_q_kernel<false><<<grid, kMoveThreads, smem, st>>>(s, mm, Xq, Kp, sx);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,7 @@ SOURCES = ["cupso_api.cu", "cupso_batch.cu", "cupso_lsq.cu", "kernels_stream.cu"
            "kernels_batch.cu", "kernels_lsq.cu", "kernels_lsq_swarm.cu", "kernels_onchip.cu",
            "kernels_paper.cu", "kernels_tiled.cu", "kernels_panel.cu", "cupso_noalloc.cu"]
 HEADERS = ["cupso_device.cuh", "cupso_internal.h", "stream_common.cuh", "paper_kernels.h", "tiled_kernels.h",
-           "async_common.cuh", "pdl.cuh"]
+           "async_common.cuh", "pdl.cuh", "lsq_internal.h", "tma_common.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + [

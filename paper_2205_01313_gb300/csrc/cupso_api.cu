@@ -18,6 +18,7 @@
 #include "../../include/cupso.h"
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "lsq_internal.h"
 #include "paper_kernels.h"
 #include "tiled_kernels.h"
 

@@ -9,6 +9,7 @@
 #include "../../include/cupso.h"
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "lsq_internal.h"
 
 using namespace cupso;
 

@@ -35,6 +35,7 @@
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "lsq_internal.h"
 #include "tma_common.cuh"
 
 namespace cupso {

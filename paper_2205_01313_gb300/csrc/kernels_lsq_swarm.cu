@@ -20,6 +20,7 @@
 
 #include "cupso_device.cuh"
 #include "cupso_internal.h"
+#include "lsq_internal.h"
 #include "stream_common.cuh"
 #include "tma_common.cuh"
 

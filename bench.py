@@ -176,10 +176,10 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(workload, warmup):
+def measured_traffic(workload, first_iteration, iterations):
     """DRAM bytes per launch from the last ncu capture, if the kernel source is
-    unchanged since and the capture took a launch among the timed iterations
-    (after `warmup` untimed ones)."""
+    unchanged since and the capture took the same launch: the same first
+    iteration and number of iterations as this run's timed launch."""
     try:
         with open(TRAFFIC_FILE) as f:
             rec = json.load(f)
@@ -187,7 +187,7 @@ def measured_traffic(workload, warmup):
         return None
     if rec.get("source_sha") != kernel_source_sha() or rec.get("workload") != workload:
         return None
-    if rec.get("iteration") is not None and rec["iteration"] <= warmup:
+    if rec.get("first_iteration") != first_iteration or rec.get("iterations") != iterations:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -262,7 +262,7 @@ def run_ours(a):
     stream = torch.cuda.Stream()
     sw = P.Swarm(D, N, cfg["bounds"], cfg["w"], cfg["c1"], cfg["c2"], fid, cfg["seed"] + rank,
                  mode=a.mode, stream=stream.cuda_stream)
-    sw.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)   # one kernel per step: events bracket that launch
+    sw.set_option(P.CUPSO_OPT_GRAPH_CHUNK, 0)   # no captured graphs: the kernels run as launched
     sw.set_option(P.CUPSO_OPT_SYNC_KERNEL, P.SYNC_KERNELS[a.sync_kernel])
     info = sw.info()
     mode_used = {v: k for k, v in P.MODES.items()}[info["mode"]]
@@ -275,25 +275,31 @@ def run_ours(a):
                                               "pipelined, %d-stage ring" % info["sync_stages"]
                                               if info["sync_stages"] else "register")
 
-    for _ in range(a.warmup):
-        sw.step(1)
+    # W untimed iterations: W - 1 in one call (the timed region's launch form)
+    # and one alone (the end-to-end loop's)
+    if a.warmup > 1:
+        sw.step(a.warmup - 1)
+    sw.step(1)
     torch.cuda.synchronize()
 
+    # The K timed iterations in one cupso_step call: on the panel layout one
+    # cooperative launch runs them with a grid barrier between iterations (up
+    # to sync_iters_per_launch per launch), otherwise one launch per iteration.
     K = a.steps
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ipl = min(K, info["sync_iters_per_launch"]) if mode_used.startswith("sync (panels") else 1
+    launches = -(-K // ipl)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
     torch.cuda.synchronize()
-    for k in range(K):
-        starts[k].record(stream)
-        sw.step(1)
-        ends[k].record(stream)
+    e0.record(stream)
+    sw.step(K)
+    e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    total_ms = starts[0].elapsed_time(ends[-1])
-    per_launch_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = e0.elapsed_time(e1)
+    per_launch_ms = total_ms / launches
     total_ms = max_over_ranks(total_ms, world, device="cuda")
 
     # End to end through the public API: each step queues one iteration and
@@ -325,7 +331,7 @@ def run_ours(a):
     # the improvement fraction of exactly the timed iterations (W+1 .. W+K)
     fr = improvement_fractions(P, cfg, rank, a.warmup + K)
     p_timed = statistics.mean(fr[a.warmup:])
-    bpl = algorithmic_bytes(N, D, p_timed)
+    bpl = algorithmic_bytes(N, D, p_timed) * ipl   # per launch of ipl iterations
     achieved = bpl / (per_launch_ms / 1e3) / 1e9
     peak, peak_src = hbm_peak()
     out = {
@@ -336,21 +342,25 @@ def run_ours(a):
                    "mode": mode_used, "step": "one PSO iteration over the whole swarm",
                    "l2": "inputs larger than L2 (%.0f MB swarm state vs 129 MB L2), no flush"
                          % (3 * 4 * N * D / 1e6),
+                   "timed": "the %d iterations in one cupso_step call: %d launch(es) of %d iteration(s)"
+                            % (K, launches, ipl),
                    "grid": info["sync_grid"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": (32 + 4 * D + 255) // 256 * 256,
                 "api": "cupso_step(h, 1) + cupso_gbest_post(h, slot) per step, cupso_gbest_wait(h, slot, host "
                        "buffers) for each step's result one step later (the last before the clock stops)"},
-        "gpu_launches": K,
+        "gpu_launches": launches,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(a.workload, a.warmup),
+                     "frac": achieved / peak,
+                     "traffic": measured_traffic(a.workload, a.warmup + 1, ipl) if launches == 1 else None,
                      "kernel": kernel_name(info),
                      "algorithmic_bytes_per_launch": bpl,
                      "improved_fraction_timed": p_timed,
                      "improved_fraction_range": [min(fr[a.warmup:]), max(fr[a.warmup:])],
-                     "bytes_with_pbest_rows_per_launch": bytes_with_pbest_rows(N, D, p_timed),
-                     "frac_with_pbest_rows": bytes_with_pbest_rows(N, D, p_timed) / (per_launch_ms / 1e3) / 1e9
+                     "iterations_per_launch": ipl,
+                     "bytes_with_pbest_rows_per_launch": bytes_with_pbest_rows(N, D, p_timed) * ipl,
+                     "frac_with_pbest_rows": bytes_with_pbest_rows(N, D, p_timed) * ipl / (per_launch_ms / 1e3) / 1e9
                                              / peak,
                      "launch_ms": per_launch_ms, "peak_source": peak_src},
         "clocks": clk,

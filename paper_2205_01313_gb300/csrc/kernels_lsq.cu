@@ -192,6 +192,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     auto tile_pb = [&](int jj) { return ((int)pair + jj * (int)npairs) / mtiles; };
 
     if (threadIdx.x == 0) {
+        prefetch_tensormap(&tmX);
+        prefetch_tensormap(&tmA);
         s_fail = 0;
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) lsq_move_q_kernel(const __gri
         bulk_load_cta(dst + 3u * kMoveBox, s.pflag + p0, 64u, bar);
     };
     if (threadIdx.x == 0) {
+        for (int a = 0; a < 3; ++a) prefetch_tensormap(&maps.m[a]);
         for (int st = 0; st < kMoveStages; ++st) mbar_init(smem_u32(&full[st]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         fence_proxy_async_smem();

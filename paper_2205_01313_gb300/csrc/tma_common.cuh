@@ -58,6 +58,12 @@ __device__ __forceinline__ void bulk_load_cta(uint32_t dst, const void* src, uin
                  : "memory");
 }
 
+// Starts fetching a tensor map (a __grid_constant__ parameter) ahead of its
+// first use by a tensor copy.
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* tm) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(tm)) : "memory");
+}
+
 // Orders this thread's earlier generic-proxy accesses to shared memory before
 // later async-proxy (bulk copy) accesses to it.
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -675,6 +675,30 @@ def lsq_report(P, stream, quick):
     }
 
 
+def cublas_fp8_tflops(n=8192, reps=20):
+    """Dense FP8 e4m3 GEMM throughput of cuBLASLt (torch._scaled_mm, n x n x n,
+    BF16 output), as context for the FP8 product's fraction; None where this
+    PyTorch has no FP8 GEMM."""
+    import torch
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.tensor(1.0, device="cuda")
+        run = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)  # noqa: E731
+        for _ in range(3):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        return 2.0 * n ** 3 / (e0.elapsed_time(e1) / reps / 1e3) / 1e12
+    except (RuntimeError, AttributeError, TypeError):
+        return None
+
+
 def lsq_launches(P, stream, prec):
     """The least-squares workload in one precision: set-up, 6 iterations, then 20
     timed ones, each iteration's kernels launched directly (no captured graph),
@@ -713,6 +737,14 @@ def run_lsq(a):
         print(json.dumps(lsq_launches(P, stream, a.lsq_launches)), flush=True)
         return
     r = lsq_report(P, stream, quick=False)
+    # FP8: the peak of the fraction is the measured BF16 peak times the nominal
+    # FP8 / BF16 ratio (2); cuBLASLt's own FP8 GEMM, measured here, beside it
+    fp8_peak = 2.0 * r["roofline"]["peak"]
+    cub = cublas_fp8_tflops()
+    r["roofline"].update({"fp8_peak": fp8_peak, "fp8_frac": r["roofline"]["fp8_achieved"] / fp8_peak,
+                          "fp8_peak_source": "measured BF16 peak x 2 (nominal FP8 / BF16 ratio)",
+                          "cublas_fp8_tflops_measured": cub,
+                          "fp8_frac_of_cublas": r["roofline"]["fp8_achieved"] / cub if cub else None})
     out = {
         "metric": METRIC, "value": r["runs"]["bf16"]["pd_per_s"], "unit": UNIT, "n_gpus": 1,
         "steps": r["runs"]["bf16"]["iters_timed"], "warmup": 3, "ms_per_step": r["ms_per_iter"]["bf16"],

@@ -826,7 +826,7 @@ def run_paper(a, table):
     FP64 paths (the fused SYNC step and, where the swarm fits one CTA, the
     on-chip kernel). Each run is timed with CUDA events over exactly the
     table's iteration count after 3 warm-up iterations. The FP64 oracle is
-    timed on a bounded prefix of iterations per row and scaled, as this box's
+    timed on a bounded prefix of iterations per row and scaled, as this host's
     serial baseline. The paper's published seconds (GTX 1080 Ti, Xeon
     E3-1275 v5) are printed beside them as context."""
     import torch
@@ -881,7 +881,7 @@ def run_paper(a, table):
         row["ours_best"] = best_mode
         paper_best_gpu = min(v for k, v in cols.items() if k != "cpu")
         row["paper_best_gpu_over_ours"] = paper_best_gpu * (T / spec_iters(spec, N)) / ours[best_mode]
-        # this box's serial FP64 baseline: a bounded prefix of the same run, scaled
+        # this host's serial FP64 baseline: a bounded prefix of the same run, scaled
         k = max(1, min(T, int(2e6 // (N * D))))
         o = O.Swarm64(N, D, *S["bounds"], S["w"], S["c1"], S["c2"], S["fitness_id"], S["seed"]).init()
         t0 = time.perf_counter()

@@ -78,3 +78,37 @@ def test_reference_arm_under_torchrun_world_2():
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["steps"] == 2
     assert rec["value"] > 0 and rec["cpu_baseline"]["kind"] == "oracle"
     assert rec["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_traffic_record_only_for_the_captured_launch(tmp_path, monkeypatch):
+    """The DRAM traffic of the timed launch is reported only when the committed
+    capture took exactly that launch: the same kernel sources (hash), workload,
+    first iteration and number of iterations; anything else reads as no
+    measurement (null), never as another launch's bytes."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = {"workload": "rosenbrock_1048576x64", "source_sha": bench.kernel_source_sha(), "first_iteration": 6,
+           "iterations": 20, "dram_bytes_per_launch": 123456789}
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(path))
+    assert bench.measured_traffic("rosenbrock_1048576x64", 6, 20) == 123456789
+    assert bench.measured_traffic("rosenbrock_1048576x64", 7, 20) is None      # another first iteration
+    assert bench.measured_traffic("rosenbrock_1048576x64", 6, 1) is None       # another launch form
+    assert bench.measured_traffic("rastrigin_65536x128", 6, 20) is None        # another workload
+    path.write_text(json.dumps(dict(rec, source_sha="0" * 16)))
+    assert bench.measured_traffic("rosenbrock_1048576x64", 6, 20) is None      # sources changed since
+    path.write_text("not json")
+    assert bench.measured_traffic("rosenbrock_1048576x64", 6, 20) is None
+
+
+def test_committed_traffic_record_matches_the_sources():
+    """The committed record is the capture of the current kernel sources, for
+    the timed launch of the default command (--steps 20 --warmup 5)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(bench.TRAFFIC_FILE) as f:
+        rec = json.load(f)
+    assert rec["source_sha"] == bench.kernel_source_sha()
+    assert (rec["first_iteration"], rec["iterations"]) == (6, 20)
+    assert bench.measured_traffic(rec["workload"], 6, 20) == rec["dram_bytes_per_launch"]

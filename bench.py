@@ -192,6 +192,16 @@ def measured_traffic(workload, first_iteration, iterations):
     return rec.get("dram_bytes_per_launch")
 
 
+def workload_config(name, cfg, world):
+    """The line's `config`, the same in both arms: the workload and its shape.
+    What ran it (kernel, grid, launches) goes under `run`."""
+    N, D = cfg["N"], cfg["D"]
+    return {"workload": name, "fitness": workloads.FITNESS_NAMES[cfg["fitness_id"]], "N": N, "D": D,
+            "step": "one PSO iteration over the whole swarm",
+            "l2": "inputs larger than L2 (%.0f MB swarm state vs 129 MB L2), no flush" % (3 * 4 * N * D / 1e6),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def kernel_name(info):
     if info["sync_tile"]:
         return "sync_tiled_kernel"
@@ -338,14 +348,10 @@ def run_ours(a):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": a.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": a.workload, "fitness": workloads.FITNESS_NAMES[fid], "N": N, "D": D,
-                   "mode": mode_used, "step": "one PSO iteration over the whole swarm",
-                   "l2": "inputs larger than L2 (%.0f MB swarm state vs 129 MB L2), no flush"
-                         % (3 * 4 * N * D / 1e6),
-                   "timed": "the %d iterations in one cupso_step call: %d launch(es) of %d iteration(s)"
-                            % (K, launches, ipl),
-                   "grid": info["sync_grid"],
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(a.workload, cfg, world),
+        "run": {"mode": mode_used, "grid": info["sync_grid"],
+                "timed": "the %d iterations in one cupso_step call: %d launch(es) of %d iteration(s)"
+                         % (K, launches, ipl)},
         "e2e": {"value": work / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": (32 + 4 * D + 255) // 256 * 256,
                 "api": "cupso_step(h, 1) + cupso_gbest_post(h, slot) per step, cupso_gbest_wait(h, slot, host "
@@ -453,8 +459,8 @@ def run_reference(a):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": a.workload, "fitness": workloads.FITNESS_NAMES[cfg["fitness_id"]], "N": cfg["N"],
-                   "D": cfg["D"], "mode": "oracle (serial synchronous PSO, Alg. 1)"},
+        "config": workload_config(a.workload, cfg, world),
+        "run": {"mode": "oracle (serial synchronous PSO, Alg. 1)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

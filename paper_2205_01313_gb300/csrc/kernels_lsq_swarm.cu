@@ -792,9 +792,10 @@ __device__ __forceinline__ void ff_acc(float& hi, float& lo, float p, float e) {
 // its binary64 rate. Each entry Gm_rc is held as gh + gl (gh = Gm_rc rounded
 // to binary32, gl = the rest, rounded): x_r gh = p + e exactly (e by one fma),
 // p enters the running hi by TwoSum, e and x_r gl the running lo. Per column c
-// of a tile the sum over its rows runs in float-float, is multiplied by x_c
-// the same way, and the columns of a candidate are added in float-float in a
-// fixed order before one conversion to FP64. The diagonal and linear terms
+// and quarter of a tile's rows the sum runs in float-float, is multiplied by
+// x_c the same way, and a candidate's pieces are added in float-float in a
+// fixed order (a reduce-scatter over each warp's lanes, then the warps in
+// order) before one conversion to FP64. The diagonal and linear terms
 // x_r (Gm_rr x_r - 2 c_r) stay in FP64 (D per candidate). Relative to the sum
 // of the terms' magnitudes the result is within a few units of 2^-44, beside
 // the FP64 Gram form's own cancellation error, which near a minimum dominates

@@ -352,3 +352,29 @@ def test_lsq_converging_regime(P, seed):
     for prec in ("bf16", "fp8"):
         assert rel[prec] <= 1e-3, prec
         assert abs(final[prec] - final["fp64"]) <= 1e-3 * final["fp64"], prec
+
+
+def test_lsq_rescore_option_switch(P):
+    """CUPSO_OPT_LSQ_RESCORE takes 0 or 1 (anything else is refused), before or
+    after cupso_set_lsq; switched between iterations (the captured graphs are
+    rebuilt), every accepted gbest still equals the oracle's FP64 residual sum
+    of gbest_pos, and the trajectory equals a swarm that rescored in FP64 all
+    along (both rescorings accept the same particles here)."""
+    from tests.gpu_common import same_bits
+    N, D, M = 1500, 96, 400
+    A, b, _ = _problem(M, D, 1, seed=31)
+    with _lsq_swarm(P, A, b, N, 9, "bf16", "ff") as s1, _lsq_swarm(P, A, b, N, 9, "bf16", "fp64") as s2:
+        for bad in (2, -1):
+            with pytest.raises(P.CupsoError):
+                s1.set_option(P.CUPSO_OPT_LSQ_RESCORE, bad)
+        for k in range(4):
+            s1.set_option(P.CUPSO_OPT_LSQ_RESCORE, k & 1)
+            s1.step(17)           # a captured graph of 16 and one more
+            s2.step(17)
+            _, fit, idx, pos = s1.gbest()
+            g64 = s1.gbest_f64()
+            exact = O.lsq_f64(A, b, pos)
+            assert abs(g64 - exact) <= 1e-9 * exact
+        st1, st2 = s1.state(), s2.state()
+    for key in ("pos", "v", "pbest_pos", "pbest_fit"):
+        assert same_bits(st1[key], st2[key]), key
